@@ -1,0 +1,165 @@
+"""FP64 CPU oracle for the partial-wave-analysis likelihood (Berger, arXiv:1108.5882, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` are the only callers.  The oracle shares no code with the CUDA library and never
+imports it.  The arithmetic lives in plain C (``pwa_oracle.c``, FP64, single-threaded); this
+module compiles it with gcc on first use and marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+  amplitudes   -- A_a(Omega) of Eq. 1 under the fixed-width unit-peak Breit-Wigner reading
+  normint      -- Psi_ab, the inner bracket of Eq. 3 (MC sum over accepted events / N_gen)
+  nll_grad     -- -lnL of Eq. 3 (extended form, footnote 2) and its gradient in V
+  nll_double_sum -- Eq. 3 in its printed K^2 double-sum form, long double (pin only)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = [os.path.join(_HERE, f) for f in ("pwa_oracle.c", "pwa_oracle_fit.c")]
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64 = ctypes.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, strict IEEE FP64)."""
+    srcs = [s for s in _SRC if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_amplitudes.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _i64, _fp, _i64,
+                                           _dp, _dp, _dp]
+            lib.orc_amplitudes.restype = None
+            lib.orc_normint.argtypes = [ctypes.c_int, _i64, _fp, _i64, _fp, ctypes.c_double, _dp]
+            lib.orc_normint.restype = None
+            lib.orc_nll_grad.argtypes = [ctypes.c_int, _i64, _fp, _i64, ctypes.c_int, _dp, _dp,
+                                         ctypes.c_double, _dp, _dp, _dp, _dp]
+            lib.orc_nll_grad.restype = ctypes.c_int
+            lib.orc_nll_double_sum.argtypes = [ctypes.c_int, _i64, _fp, _i64, _dp, _dp,
+                                               ctypes.c_double]
+            lib.orc_nll_double_sum.restype = ctypes.c_double
+            lib.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_double]
+            lib.orc_legendre.restype = ctypes.c_double
+            _register_fit(lib)
+            _lib = lib
+    return _lib
+
+
+def _register_fit(lib):
+    if hasattr(lib, "orc_philox4x32"):
+        lib.orc_philox4x32.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32)]
+        lib.orc_philox4x32.restype = None
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _c64_as_f32(A):
+    """complex64 [K][ld] -> contiguous float32 view [K][2*ld] (interleaved re, im)."""
+    A = np.ascontiguousarray(A, dtype=np.complex64)
+    return A.view(np.float32)
+
+
+def legendre(J: int, x: float) -> float:
+    return _load().orc_legendre(int(J), float(x))
+
+
+def amplitudes(J, lam, M, W, kin, derivs: bool = False):
+    """A_a(Omega_i), complex128 [K][n] (plus dA/dM, dA/dGamma if ``derivs``).
+
+    kin: float32 [3][n] (m, cos theta, phi).  J, lam: int per wave; M, W: float64 per wave."""
+    lib = _load()
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    kin = np.ascontiguousarray(kin, dtype=np.float32)
+    K = J.shape[0]
+    n = kin.shape[1]
+    A = np.zeros((K, n), dtype=np.complex128)
+    dM = np.zeros((K, n), dtype=np.complex128) if derivs else None
+    dW = np.zeros((K, n), dtype=np.complex128) if derivs else None
+    lib.orc_amplitudes(K, _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), n,
+                       _ptr(kin, _fp), n, _ptr(A, _dp), _ptr(dM, _dp), _ptr(dW, _dp))
+    return (A, dM, dW) if derivs else A
+
+
+def normint(A, w=None, n_gen=None):
+    """Psi (complex128 [K][K]) from complex64 MC amplitudes A [K][n]; w optional float32 [n]."""
+    lib = _load()
+    K, n = A.shape
+    Af = _c64_as_f32(A)
+    wf = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    if n_gen is None:
+        n_gen = float(n)
+    Psi = np.zeros((K, K), dtype=np.complex128)
+    lib.orc_normint(K, n, _ptr(Af, _fp), n, _ptr(wf, _fp), float(n_gen), _ptr(Psi, _dp))
+    return Psi
+
+
+def nll_grad(A, V, Psi, n_factor=None, with_cond: bool = False):
+    """(-lnL [P], grad [P][2K] as (Re g, Im g) pairs) for complex64 A [K][n], V [P][K]
+    (any complex dtype, promoted to complex128) and Psi complex128 [K][K].
+
+    With ``with_cond`` also returns the condition scales (cond_f [P], cond_g [P][K]) the
+    parity tolerances are measured against, and the count of sets with I_i <= 0."""
+    lib = _load()
+    K, n = A.shape
+    Af = _c64_as_f32(A)
+    V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.complex128)
+    P = V.shape[0]
+    assert V.shape[1] == K
+    Psi = np.ascontiguousarray(Psi, dtype=np.complex128)
+    if n_factor is None:
+        n_factor = float(n)
+    nll = np.zeros(P, dtype=np.float64)
+    grad = np.zeros((P, 2 * K), dtype=np.float64)
+    cf = np.zeros(P, dtype=np.float64)
+    cg = np.zeros((P, K), dtype=np.float64)
+    bad = lib.orc_nll_grad(K, n, _ptr(Af, _fp), n, P, _ptr(V, _dp), _ptr(Psi, _dp),
+                           float(n_factor), _ptr(nll, _dp), _ptr(grad, _dp), _ptr(cf, _dp),
+                           _ptr(cg, _dp))
+    if with_cond:
+        return nll, grad, cf, cg, bad
+    return nll, grad
+
+
+def nll_double_sum(A, V, Psi, n_factor=None) -> float:
+    """Eq. 3 as printed (K^2 double sum per event), long double; tiny inputs only."""
+    lib = _load()
+    K, n = A.shape
+    Af = _c64_as_f32(A)
+    V = np.ascontiguousarray(V, dtype=np.complex128).reshape(K)
+    Psi = np.ascontiguousarray(Psi, dtype=np.complex128)
+    if n_factor is None:
+        n_factor = float(n)
+    return lib.orc_nll_double_sum(K, n, _ptr(Af, _fp), n, _ptr(V, _dp), _ptr(Psi, _dp),
+                                  float(n_factor))

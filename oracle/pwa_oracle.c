@@ -1,0 +1,231 @@
+/*
+ * pwa_oracle.c -- plain, single-threaded FP64 CPU oracle for the partial-wave-analysis
+ * likelihood of Berger, "Partial Wave Analysis using Graphics Cards" (arXiv:1108.5882).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls this file;
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark do.  It shares
+ * no header, helper, table or constant with the CUDA library.
+ *
+ * What is computed, and where the paper defines it:
+ *   - coherent intensity I(Omega) = |sum_a V_a A_a(Omega)|^2                     (Sec. 2, Eq. 1)
+ *   - MC normalisation Psi_ab = (1/N_gen) sum_{j in acc} w_j A_a(j) conj(A_b(j)) (Sec. 2, Eq. 3,
+ *     inner bracket of the second term; acceptance/weights from the text around Eq. 2)
+ *   - -lnL fed to the minimiser (Sec. 2, footnote 2), extended form
+ *       f(V) = -sum_i ln I_i + n_factor * sum_ab V_a conj(V_b) Psi_ab
+ *     and its gradient g_c = dF/dRe V_c + i dF/dIm V_c = 2 dF/dconj(V_c)
+ *   - the double-sum form of Eq. 3 in long double (used only to pin the O(K) form above)
+ *   - the amplitude model A_a = BW_a(m) P_J(cos th) exp(i lambda phi) and its derivatives
+ *     in the resonance mass and width (the paper gives no amplitude formula; the reading is
+ *     the fixed-width, unit-peak relativistic Breit-Wigner with ordinary Legendre P_J).
+ *
+ * Everything is the textbook definition evaluated in double precision, in the order the
+ * definition states, with Neumaier-compensated accumulation of the long event sums.
+ *
+ * Parity pins: every function here is pinned by tests against closed forms, identities,
+ * library routines or brute force (see tests/test_oracle_*.py).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ---------- compensated summation (Neumaier) ---------------------------------------- */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum* a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else                       a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double nsum_get(const nsum* a) { return a->s + a->c; }
+
+/* ---------- amplitude model ----------------------------------------------------------- */
+
+/* Fixed-width relativistic Breit-Wigner, normalised to unit modulus at the peak:
+ * BW(m) = M*Gamma / (M^2 - m^2 - i M Gamma).  At m = M it equals i, and |BW| <= 1. */
+cplx orc_bw(double m, double M, double W) {
+    cplx den = (M * M - m * m) - I * (M * W);
+    return (M * W) / den;
+}
+
+/* d BW / d M and d BW / d Gamma by the quotient rule, written out unsimplified. */
+void orc_bw_deriv(double m, double M, double W, cplx* dM, cplx* dW) {
+    cplx num = M * W;
+    cplx den = (M * M - m * m) - I * (M * W);
+    cplx dnum_dM = W, dden_dM = 2.0 * M - I * W;
+    cplx dnum_dW = M, dden_dW = -I * M;
+    *dM = (dnum_dM * den - num * dden_dM) / (den * den);
+    *dW = (dnum_dW * den - num * dden_dW) / (den * den);
+}
+
+/* Ordinary Legendre polynomial P_J(x) by Bonnet's recurrence
+ * (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1}. */
+double orc_legendre(int J, double x) {
+    if (J == 0) return 1.0;
+    double pm = 1.0, p = x;
+    for (int n = 1; n < J; ++n) {
+        double pn = ((2.0 * n + 1.0) * x * p - n * pm) / (n + 1.0);
+        pm = p;
+        p = pn;
+    }
+    return p;
+}
+
+/* A_a(Omega_i) for K waves over n events.  kin is float32 SoA [3][ld]: m, cos(theta), phi.
+ * A, dAdM, dAdW are complex double [K][n] (dAdM/dAdW may be NULL). */
+void orc_amplitudes(int K, const int* J, const int* lam, const double* M, const double* W,
+                    int64_t n, const float* kin, int64_t ld,
+                    double* A, double* dAdM, double* dAdW) {
+    cplx* Ac = (cplx*)A;
+    cplx* dM = (cplx*)dAdM;
+    cplx* dW = (cplx*)dAdW;
+    for (int a = 0; a < K; ++a) {
+        for (int64_t i = 0; i < n; ++i) {
+            double m = kin[i], ct = kin[ld + i], ph = kin[2 * ld + i];
+            cplx ang = orc_legendre(J[a], ct) * cexp(I * (lam[a] * ph));
+            Ac[(int64_t)a * n + i] = orc_bw(m, M[a], W[a]) * ang;
+            if (dM || dW) {
+                cplx bm, bw;
+                orc_bw_deriv(m, M[a], W[a], &bm, &bw);
+                if (dM) dM[(int64_t)a * n + i] = bm * ang;
+                if (dW) dW[(int64_t)a * n + i] = bw * ang;
+            }
+        }
+    }
+}
+
+/* ---------- MC normalisation integral -------------------------------------------------- */
+
+/* Psi_ab = (1/n_gen) sum_j w_j A_a(j) conj(A_b(j)); A is complex64 interleaved [K][ld]
+ * (the same array the GPU consumes, promoted to double).  w may be NULL (all ones).
+ * Psi is complex double [K][K], full matrix. */
+void orc_normint(int K, int64_t n, const float* A, int64_t ld, const float* w, double n_gen,
+                 double* Psi) {
+    cplx* out = (cplx*)Psi;
+    for (int a = 0; a < K; ++a) {
+        for (int b = 0; b < K; ++b) {
+            nsum re = {0, 0}, im = {0, 0};
+            for (int64_t j = 0; j < n; ++j) {
+                cplx Aa = A[2 * ((int64_t)a * ld + j)] + I * A[2 * ((int64_t)a * ld + j) + 1];
+                cplx Ab = A[2 * ((int64_t)b * ld + j)] + I * A[2 * ((int64_t)b * ld + j) + 1];
+                double wj = w ? (double)w[j] : 1.0;
+                cplx t = wj * Aa * conj(Ab);
+                nsum_add(&re, creal(t));
+                nsum_add(&im, cimag(t));
+            }
+            out[a * K + b] = (nsum_get(&re) + I * nsum_get(&im)) / n_gen;
+        }
+    }
+}
+
+/* ---------- negative log-likelihood and gradient --------------------------------------- */
+
+/* f(V) and g(V) for P parameter sets.  A: complex64 interleaved [K][ld]; V: complex double
+ * [P][K]; Psi: complex double [K][K].  Outputs nll[P], grad[P][2K] = (Re g_c, Im g_c).
+ * cond_f[P] = max(|f|, sum_i |ln I_i|, n_factor*|S|) and cond_g[P][K] =
+ * 2 sum_i |A_ic||u_i|/I_i + 2 n_factor sum_a |Psi_ac||V_a| are the scales the parity
+ * tolerances are taken relative to (either may be NULL).
+ * Returns the number of parameter sets with a non-positive or non-finite intensity at some
+ * event; those get nll = +inf and a zero gradient. */
+int orc_nll_grad(int K, int64_t n, const float* A, int64_t ld, int P, const double* Vd,
+                 const double* Psid, double n_factor, double* nll, double* grad,
+                 double* cond_f, double* cond_g) {
+    const cplx* V = (const cplx*)Vd;
+    const cplx* Psi = (const cplx*)Psid;
+    int bad_sets = 0;
+    cplx* Ai = (cplx*)malloc(sizeof(cplx) * (size_t)K);
+    nsum* gre = (nsum*)malloc(sizeof(nsum) * (size_t)K);
+    nsum* gim = (nsum*)malloc(sizeof(nsum) * (size_t)K);
+    double* gsc = (double*)malloc(sizeof(double) * (size_t)K);
+    for (int p = 0; p < P; ++p) {
+        const cplx* Vp = V + (int64_t)p * K;
+        nsum lnsum = {0, 0};
+        double lnabs = 0.0;
+        int bad = 0;
+        for (int c = 0; c < K; ++c) { gre[c].s = gre[c].c = gim[c].s = gim[c].c = 0.0; gsc[c] = 0.0; }
+        for (int64_t i = 0; i < n; ++i) {
+            cplx u = 0.0;
+            for (int a = 0; a < K; ++a) {
+                Ai[a] = A[2 * ((int64_t)a * ld + i)] + I * A[2 * ((int64_t)a * ld + i) + 1];
+                u += Vp[a] * Ai[a];
+            }
+            double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
+            if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; continue; }
+            double l = log(Ii);
+            nsum_add(&lnsum, l);
+            lnabs += fabs(l);
+            /* d(-ln I_i)/d conj(V_c) = -conj(A_ic) u_i / I_i; g = 2 * that */
+            for (int c = 0; c < K; ++c) {
+                cplx t = conj(Ai[c]) * u / Ii;
+                nsum_add(&gre[c], -2.0 * creal(t));
+                nsum_add(&gim[c], -2.0 * cimag(t));
+                gsc[c] += 2.0 * cabs(Ai[c]) * cabs(u) / Ii;
+            }
+        }
+        /* normalisation term S = sum_ab V_a conj(V_b) Psi_ab and its gradient 2 n sum_a Psi_ac V_a */
+        cplx S = 0.0;
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) S += Vp[a] * conj(Vp[b]) * Psi[a * K + b];
+        double f = -nsum_get(&lnsum) + n_factor * creal(S);
+        for (int c = 0; c < K; ++c) {
+            cplx nt = 0.0;
+            double nts = 0.0;
+            for (int a = 0; a < K; ++a) {
+                nt += Psi[a * K + c] * Vp[a];
+                nts += cabs(Psi[a * K + c]) * cabs(Vp[a]);
+            }
+            double gr = nsum_get(&gre[c]) + 2.0 * n_factor * creal(nt);
+            double gi = nsum_get(&gim[c]) + 2.0 * n_factor * cimag(nt);
+            grad[(int64_t)p * 2 * K + 2 * c] = bad ? 0.0 : gr;
+            grad[(int64_t)p * 2 * K + 2 * c + 1] = bad ? 0.0 : gi;
+            if (cond_g) cond_g[(int64_t)p * K + c] = gsc[c] + 2.0 * fabs(n_factor) * nts;
+        }
+        nll[p] = bad ? INFINITY : f;
+        if (cond_f) {
+            double cf = fabs(f);
+            if (lnabs > cf) cf = lnabs;
+            if (fabs(n_factor * creal(S)) > cf) cf = fabs(n_factor * creal(S));
+            cond_f[p] = cf;
+        }
+        bad_sets += bad;
+    }
+    free(Ai); free(gre); free(gim); free(gsc);
+    return bad_sets;
+}
+
+/* Eq. 3 exactly as printed: ln L = sum_i ln( sum_a sum_a' V_a conj(V_a') A_a conj(A_a') )
+ *   - sum_a sum_a' V_a conj(V_a') Psi_aa'.  Returns -ln L * (with n_factor on the second term)
+ * accumulated in long double, O(K^2) per event.  Used only on tiny inputs to pin the O(K)
+ * form |sum_a V_a A_a|^2 of Eq. 1. */
+double orc_nll_double_sum(int K, int64_t n, const float* A, int64_t ld, const double* Vd,
+                          const double* Psid, double n_factor) {
+    long double lnsum = 0.0L;
+    for (int64_t i = 0; i < n; ++i) {
+        long double re = 0.0L;
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) {
+                long double var = Vd[2 * a], vai = Vd[2 * a + 1];
+                long double vbr = Vd[2 * b], vbi = -Vd[2 * b + 1];
+                long double aar = A[2 * ((int64_t)a * ld + i)], aai = A[2 * ((int64_t)a * ld + i) + 1];
+                long double abr = A[2 * ((int64_t)b * ld + i)], abi = -A[2 * ((int64_t)b * ld + i) + 1];
+                /* (va * conj vb) * (Aa * conj Ab), real part (the imaginary parts cancel in the sum) */
+                long double pr = var * vbr - vai * vbi, pi = var * vbi + vai * vbr;
+                long double qr = aar * abr - aai * abi, qi = aar * abi + aai * abr;
+                re += pr * qr - pi * qi;
+            }
+        lnsum += logl(re);
+    }
+    long double norm = 0.0L;
+    for (int a = 0; a < K; ++a)
+        for (int b = 0; b < K; ++b) {
+            long double var = Vd[2 * a], vai = Vd[2 * a + 1];
+            long double vbr = Vd[2 * b], vbi = -Vd[2 * b + 1];
+            long double pr = var * vbr - vai * vbi, pi = var * vbi + vai * vbr;
+            long double sr = Psid[2 * (a * K + b)], si = Psid[2 * (a * K + b) + 1];
+            norm += pr * sr - pi * si;
+        }
+    return (double)(-lnsum + (long double)n_factor * norm);
+}

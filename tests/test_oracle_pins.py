@@ -1,0 +1,330 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties one oracle function to something other than itself: a closed form derived by
+hand, a library routine, an exact identity of Eq. 1-3, brute force on tiny inputs, or a finite
+difference.  A dropped term, a wrong sign, a missing conjugate or a transposed Psi fails at
+least one of them (see the comment on each test).
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.special import eval_legendre
+
+import oracle
+from paper_1108_5882_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_A(K, n, seed):
+    g = np.random.default_rng(seed)
+    return (g.normal(size=(K, n)) + 1j * g.normal(size=(K, n))).astype(np.complex64)
+
+
+def _rand_V(K, seed, P=None):
+    g = np.random.default_rng(seed)
+    shape = (K,) if P is None else (P, K)
+    return (g.uniform(0.2, 2, size=shape) * np.exp(1j * g.uniform(0, 2 * np.pi, size=shape)))
+
+
+# ---------------------------------------------------------------- amplitude model ---------
+
+def test_legendre_matches_scipy():
+    # the Bonnet recurrence against scipy's Legendre polynomials (library routine)
+    for J in range(0, 9):
+        for x in np.linspace(-1, 1, 17):
+            assert abs(oracle.legendre(J, x) - eval_legendre(J, x)) < 1e-14
+
+
+def test_breit_wigner_rationalised_and_unit_peak():
+    # BW(m) = M G / (M^2 - m^2 - i M G) = M G (M^2 - m^2 + i M G) / ((M^2-m^2)^2 + M^2 G^2):
+    # the rationalised form fixes the sign of Im and the modulus; BW(M) = i (unit peak).
+    M, G = 1.7, 0.12
+    kin = inputs.kinematics(2000, 5, 0)
+    A = oracle.amplitudes([0], [0], [M], [G], kin)[0]
+    m = kin[0].astype(np.float64)
+    d = (M * M - m * m) ** 2 + (M * G) ** 2
+    ref = M * G * ((M * M - m * m) + 1j * M * G) / d
+    assert np.max(np.abs(A - ref)) < 1e-14
+    assert np.all(np.abs(A) <= 1 + 1e-15)
+    kin_pk = np.array([[M], [0.3], [1.0]], dtype=np.float32)
+    Apk = oracle.amplitudes([0], [0], [float(np.float32(M))], [G], kin_pk)[0, 0]
+    assert abs(Apk - 1j) < 1e-12
+
+
+def test_amplitude_composition():
+    # A = BW(m) * P_J(cos th) * exp(i lambda phi), composed from independent pieces
+    ws = inputs.wave_set_spread(12, 3)
+    kin = inputs.kinematics(500, 3, 1)
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin)
+    m, ct, ph = (kin[k].astype(np.float64) for k in range(3))
+    for a in range(ws.K):
+        M, G = ws.M[a], ws.W[a]
+        bw = M * G * ((M * M - m * m) + 1j * M * G) / ((M * M - m * m) ** 2 + (M * G) ** 2)
+        ref = bw * eval_legendre(int(ws.J[a]), ct) * np.exp(1j * ws.lam[a] * ph)
+        assert np.max(np.abs(A[a] - ref)) < 1e-13
+
+
+def test_amplitude_derivatives_closed_form_and_fd():
+    # dBW/dM = -G (M^2 + m^2) / D^2, dBW/dG = M (M^2 - m^2) / D^2 with D = M^2 - m^2 - i M G
+    # (derived by hand), and central finite differences of the oracle's own amplitudes.
+    ws = inputs.wave_set_spread(6, 9)
+    kin = inputs.kinematics(400, 9, 1)
+    A, dM, dW = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin, derivs=True)
+    m, ct, ph = (kin[k].astype(np.float64) for k in range(3))
+    for a in range(ws.K):
+        M, G = ws.M[a], ws.W[a]
+        D = M * M - m * m - 1j * M * G
+        ang = eval_legendre(int(ws.J[a]), ct) * np.exp(1j * ws.lam[a] * ph)
+        assert np.max(np.abs(dM[a] - (-G * (M * M + m * m) / D ** 2) * ang)) < 1e-11
+        assert np.max(np.abs(dW[a] - (M * (M * M - m * m) / D ** 2) * ang)) < 1e-11
+    h = 1e-6
+    for a in range(ws.K):
+        Mp, Mm = ws.M.copy(), ws.M.copy()
+        Mp[a] += h
+        Mm[a] -= h
+        fd = (oracle.amplitudes(ws.J, ws.lam, Mp, ws.W, kin)[a]
+              - oracle.amplitudes(ws.J, ws.lam, Mm, ws.W, kin)[a]) / (2 * h)
+        assert np.max(np.abs(fd - dM[a])) < 1e-5 * max(1.0, np.max(np.abs(dM[a])))
+        Wp, Wm = ws.W.copy(), ws.W.copy()
+        Wp[a] += h
+        Wm[a] -= h
+        fd = (oracle.amplitudes(ws.J, ws.lam, ws.M, Wp, kin)[a]
+              - oracle.amplitudes(ws.J, ws.lam, ws.M, Wm, kin)[a]) / (2 * h)
+        assert np.max(np.abs(fd - dW[a])) < 1e-5 * max(1.0, np.max(np.abs(dW[a])))
+
+
+# ---------------------------------------------------------------- normalisation integral --
+
+def test_normint_is_gram_matrix():
+    # Psi = A A^H / N_gen (numpy matmul as the library routine); Hermitian; PSD;
+    # diag = <|A_a|^2>; V^T Psi V* = <|sum_a V_a A_a|^2>_MC.  A transposed or unconjugated
+    # Psi fails the matmul and the quadratic-form checks.
+    A = _rand_A(7, 3000, 1)
+    Psi = oracle.normint(A)
+    Ad = A.astype(np.complex128)
+    ref = Ad @ Ad.conj().T / A.shape[1]
+    assert np.max(np.abs(Psi - ref)) < 1e-13 * np.max(np.abs(ref))
+    assert np.max(np.abs(Psi - Psi.conj().T)) < 1e-15 * np.max(np.abs(Psi))
+    ev = np.linalg.eigvalsh(Psi)
+    assert ev.min() >= -1e-12 * np.trace(Psi).real
+    assert np.allclose(np.diag(Psi).real, np.mean(np.abs(Ad) ** 2, axis=1), rtol=1e-13)
+    V = _rand_V(7, 2)
+    S = np.real(V @ Psi @ V.conj())
+    assert abs(S - np.mean(np.abs(V @ Ad) ** 2)) < 1e-12 * S
+
+
+def test_normint_weights_and_acceptance():
+    # weight 0 == event removed with N_gen unchanged; all-ones mask == no mask (Eq. 2-3 text)
+    A = _rand_A(5, 1000, 3)
+    w = np.ones(1000, dtype=np.float32)
+    assert np.max(np.abs(oracle.normint(A, w) - oracle.normint(A))) < 1e-15
+    w[::3] = 0
+    keep = w > 0
+    P1 = oracle.normint(A, w, n_gen=1000)
+    P2 = oracle.normint(np.ascontiguousarray(A[:, keep]), n_gen=1000)
+    assert np.max(np.abs(P1 - P2)) < 1e-14
+    # real weights scale the per-event contribution linearly
+    g = np.random.default_rng(4).uniform(0, 2, 1000).astype(np.float32)
+    ref = (A.astype(np.complex128) * g) @ A.astype(np.complex128).conj().T / 1000
+    assert np.max(np.abs(oracle.normint(A, g) - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- likelihood --------------
+
+def test_single_wave_constant_amplitude_closed_form():
+    # K=1, A_i = c for every event: I = |V|^2 |c|^2, Psi = |c|^2, so
+    # f = -N ln(|V|^2 |c|^2) + N |V|^2 |c|^2 and g = 2 dF/dconj V = -2N V/|V|^2 + 2N |c|^2 V.
+    N = 257
+    c = np.complex64(0.7 - 0.4j)
+    A = np.full((1, N), c, dtype=np.complex64)
+    Psi = oracle.normint(A)
+    for V in (0.3 + 0.9j, -1.2 + 0.1j, 2.0 + 0.0j):
+        f, g = oracle.nll_grad(A, np.array([[V]]), Psi)
+        c2 = abs(complex(c)) ** 2
+        v2 = abs(V) ** 2
+        assert abs(f[0] - (-N * math.log(v2 * c2) + N * v2 * c2)) < 1e-12 * N
+        gref = -2 * N * V / v2 + 2 * N * c2 * V
+        assert abs(complex(g[0, 0], g[0, 1]) - gref) < 1e-12 * N
+
+
+def test_single_wave_minimum_closed_form():
+    # K=1: f(V) = -sum ln|A_i|^2 - N ln|V|^2 + N |V|^2 Psi_11; minimum at |V|^2 = 1/Psi_11 with
+    # f_min = -sum ln|A_i|^2 + N ln Psi_11 + N, and zero gradient there.
+    A = _rand_A(1, 5000, 7)
+    N = A.shape[1]
+    Psi = oracle.normint(_rand_A(1, 20000, 8))
+    p11 = Psi[0, 0].real
+    V = np.exp(0.37j) / math.sqrt(p11)
+    f, g = oracle.nll_grad(A, np.array([[V]]), Psi)
+    fmin = -np.sum(np.log(np.abs(A[0].astype(np.complex128)) ** 2)) + N * math.log(p11) + N
+    assert abs(f[0] - fmin) < 1e-11 * abs(fmin)
+    assert np.max(np.abs(g)) < 1e-9 * N
+    for s in (0.9, 1.1):
+        assert oracle.nll_grad(A, np.array([[s * V]]), Psi)[0][0] > f[0]
+
+
+def test_eq3_double_sum_equals_modulus_form():
+    # Eq. 3 as printed (K^2 double sum, long double) == the O(K) form |sum V A|^2 of Eq. 1
+    for K, n, seed in ((1, 3, 1), (2, 4, 2), (3, 5, 3), (3, 2, 4)):
+        A = _rand_A(K, n, seed)
+        V = _rand_V(K, seed + 10)
+        Psi = oracle.normint(_rand_A(K, 50, seed + 20))
+        f, _ = oracle.nll_grad(A, V[None, :], Psi, n_factor=float(n))
+        f2 = oracle.nll_double_sum(A, V, Psi, n_factor=float(n))
+        assert abs(f[0] - f2) < 1e-13 * max(1.0, abs(f2))
+
+
+def test_brute_force_exact_rational():
+    # tiny input: the data term summed exactly in rational arithmetic from the float inputs,
+    # the logs taken in double, normalisation term exact; compared to the oracle.
+    K, n = 3, 4
+    A = _rand_A(K, n, 11)
+    V = _rand_V(K, 12)
+    Psi = oracle.normint(_rand_A(K, 20, 13))
+
+    def fr(x):
+        return Fraction(float(x))
+
+    lnsum = 0.0
+    for i in range(n):
+        re = Fraction(0)
+        im = Fraction(0)
+        for a in range(K):
+            vr, vi = fr(V[a].real), fr(V[a].imag)
+            ar, ai = fr(A[a, i].real), fr(A[a, i].imag)
+            re += vr * ar - vi * ai
+            im += vr * ai + vi * ar
+        lnsum += math.log(float(re * re + im * im))
+    S = Fraction(0)
+    for a in range(K):
+        for b in range(K):
+            vr = fr(V[a].real) * fr(V[b].real) + fr(V[a].imag) * fr(V[b].imag)
+            vi = fr(V[a].imag) * fr(V[b].real) - fr(V[a].real) * fr(V[b].imag)
+            S += vr * fr(Psi[a, b].real) - vi * fr(Psi[a, b].imag)
+    fref = -lnsum + n * float(S)
+    f, _ = oracle.nll_grad(A, V[None, :], Psi)
+    assert abs(f[0] - fref) < 1e-13 * max(1.0, abs(fref))
+
+
+def test_phase_invariance_and_equivariance():
+    # f(e^{i phi} V) = f(V) (Eq. 1 sees only |sum V A|); g(e^{i phi} V) = e^{i phi} g(V)
+    A = _rand_A(6, 2000, 21)
+    Psi = oracle.normint(_rand_A(6, 8000, 22))
+    V = _rand_V(6, 23)
+    f0, g0 = oracle.nll_grad(A, V[None, :], Psi)
+    gc0 = g0[0, 0::2] + 1j * g0[0, 1::2]
+    for phi in (0.4, 2.0, -2.9):
+        f1, g1 = oracle.nll_grad(A, (np.exp(1j * phi) * V)[None, :], Psi)
+        assert abs(f1[0] - f0[0]) < 1e-12 * abs(f0[0])
+        gc1 = g1[0, 0::2] + 1j * g1[0, 1::2]
+        assert np.max(np.abs(gc1 - np.exp(1j * phi) * gc0)) < 1e-10 * np.max(np.abs(gc0))
+
+
+def test_euler_and_phase_identities():
+    # Re(sum_c conj(V_c) g_c) = -2N + 2N S(V)  (f is -N ln|V|^2 + N |V|^2 S along rays)
+    # Im(sum_c conj(V_c) g_c) = 0               (phase invariance)
+    # A dropped factor 2, a wrong N or a missing conjugate breaks one of the two.
+    A = _rand_A(5, 3000, 31)
+    N = A.shape[1]
+    Psi = oracle.normint(_rand_A(5, 9000, 32))
+    for s in range(4):
+        V = _rand_V(5, 33 + s)
+        _, g = oracle.nll_grad(A, V[None, :], Psi)
+        gc = g[0, 0::2] + 1j * g[0, 1::2]
+        z = np.sum(np.conj(V) * gc)
+        S = np.real(V @ Psi @ V.conj())
+        assert abs(z.real - (-2 * N + 2 * N * S)) < 1e-10 * N * max(1.0, S)
+        assert abs(z.imag) < 1e-10 * N * max(1.0, S)
+
+
+def test_gradient_finite_differences():
+    # central differences of f in each real coordinate Re V_c, Im V_c
+    A = _rand_A(4, 1500, 41)
+    Psi = oracle.normint(_rand_A(4, 6000, 42))
+    V = _rand_V(4, 43)
+    _, g = oracle.nll_grad(A, V[None, :], Psi)
+    for c in range(4):
+        for part, unit in ((0, 1.0), (1, 1j)):
+            h = 1e-6 * max(1.0, abs(V[c]))
+            Vp, Vm = V.copy(), V.copy()
+            Vp[c] += unit * h
+            Vm[c] -= unit * h
+            fd = (oracle.nll_grad(A, Vp[None, :], Psi)[0][0]
+                  - oracle.nll_grad(A, Vm[None, :], Psi)[0][0]) / (2 * h)
+            assert abs(fd - g[0, 2 * c + part]) < 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+def test_batched_sets_are_independent():
+    # P parameter sets in one call == P separate calls (no cross-talk between sets)
+    A = _rand_A(3, 700, 51)
+    Psi = oracle.normint(_rand_A(3, 900, 52))
+    V = _rand_V(3, 53, P=5)
+    f, g = oracle.nll_grad(A, V, Psi)
+    for p in range(5):
+        f1, g1 = oracle.nll_grad(A, V[p:p + 1], Psi)
+        assert f1[0] == f[p] and np.array_equal(g1[0], g[p])
+
+
+def test_paper_normalisation_mapping():
+    # Eq. 3 has no N on the normalisation term; the extended form has it.  They agree up to a
+    # reparametrisation: f_paper(sqrt(N) V) = f_ext(V) - N ln N.
+    A = _rand_A(4, 2500, 61)
+    N = A.shape[1]
+    Psi = oracle.normint(_rand_A(4, 5000, 62))
+    V = _rand_V(4, 63)
+    f_ext, _ = oracle.nll_grad(A, V[None, :], Psi, n_factor=N)
+    f_pap, _ = oracle.nll_grad(A, (math.sqrt(N) * V)[None, :], Psi, n_factor=1.0)
+    assert abs(f_pap[0] - (f_ext[0] - N * math.log(N))) < 1e-10 * abs(f_ext[0])
+
+
+def test_zero_intensity_is_flagged():
+    # an event with I_i = 0 gives f = +inf for that set (reading: -ln 0 = +inf)
+    A = _rand_A(3, 100, 71)
+    A[:, 17] = 0
+    Psi = oracle.normint(_rand_A(3, 300, 72))
+    f, g, cf, cg, bad = oracle.nll_grad(A, _rand_V(3, 73, P=2), Psi, with_cond=True)
+    assert bad == 2 and np.all(np.isinf(f)) and np.all(g == 0)
+
+
+def test_condition_scales_bound_the_terms():
+    # the tolerance denominators are at least the magnitudes they are built from
+    A = _rand_A(4, 800, 81)
+    Psi = oracle.normint(_rand_A(4, 1600, 82))
+    V = _rand_V(4, 83)
+    f, g, cf, cg, bad = oracle.nll_grad(A, V[None, :], Psi, with_cond=True)
+    assert cf[0] >= abs(f[0])
+    gc = np.abs(g[0, 0::2] + 1j * g[0, 1::2])
+    assert np.all(cg[0] >= gc * (1 - 1e-12))
+
+
+# ---------------------------------------------------------------- the paper's one number --
+
+def test_table_storage_matches_paper():
+    # Sec. 2: the per-event K x K lookup table takes ~1.5 GB per million events at 20 waves.
+    with open(os.path.join(GOLDEN, "table_storage.json")) as fh:
+        gold = json.load(fh)
+    K, n, bytes_per_real = gold["waves"], gold["events"], gold["bytes_per_real"]
+    size = K * K * bytes_per_real * n
+    assert abs(size / 2 ** 30 - gold["paper_gb"]) < gold["tolerance_gb"]
+
+
+def test_tree_sum_beats_sequential_fp32_sum():
+    # Sec. 2 precision remark: a sequential single-precision loop sum of ln I drifts at 1e6
+    # terms while a pairwise (tree) sum stays close to the FP64 sum.  Demonstration.
+    g = np.random.default_rng(91)
+    x = np.log(g.uniform(0.05, 3.0, size=1_000_000)).astype(np.float32)
+    exact = math.fsum(x.astype(np.float64))
+    seq = np.cumsum(x, dtype=np.float32)[-1]  # strictly sequential accumulation
+    tree = x.copy()
+    while tree.shape[0] > 1:
+        if tree.shape[0] % 2:
+            tree = np.append(tree, np.float32(0))
+        tree = (tree[0::2] + tree[1::2]).astype(np.float32)
+    scale = np.sum(np.abs(x.astype(np.float64)))
+    assert abs(float(tree[0]) - exact) < 1e-6 * scale
+    assert abs(float(seq) - exact) > 10 * abs(float(tree[0]) - exact)
