@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the PWA likelihood hot path on GB300 (one JSON line on rank 0).
+
+Workload (default "scale"): K=16 waves (J in {0,2,4} x lambda in {0,1}, masses spread over
+1.3-2.8 GeV), N_data = 1e6 events drawn on the GPU by accept-reject from I under a seeded V,
+N_MC = 5e6 flat phase-space events, complex64 amplitudes.  Amplitudes and Psi are computed once
+(masses and widths fixed: Sec. 2 of the paper, the bracket and per-event terms can be
+pre-calculated), then one step is one fit-iteration evaluation of -lnL and its gradient at a
+new V (the data-event sum, the normalisation term and the deterministic grid reduction: one
+launch of the streaming kernel).
+
+Metric: event x parameter-set NLL+grad evaluations per second = N_data * P / step time.
+  value     device time of the steps (CUDA events on the launching stream), inputs resident in
+            HBM, L2 flushed (a 512 MiB read) before every step, outside the events.
+  e2e       the same metric through the C ABI from HOST buffers: each step copies the data and MC
+            kinematics from pinned host memory, recomputes amplitudes and Psi, evaluates -lnL
+            and its gradient, and reads nll and the gradient back.
+  roofline  the dominant kernel (k_nll_stream) against the measured HBM copy bandwidth:
+            algorithmic bytes per launch = N_data * K * 8 (each complex64 amplitude read once).
+  cpu_baseline  the FP64 oracle (single-threaded C) on a bounded sample of the same workload.
+
+--impl reference times the oracle as the reference arm on this workload.
+Under torchrun (N > 1) every rank evaluates its own replica (independent fits, no collective
+on the data path): weak scaling, value = all ranks' units / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "event x param-set NLL+grad evals/s"
+UNIT = "event-evals/s"
+
+WORKLOADS = {
+    # name: (K, N_data, N_MC, P, seed)
+    "plain": (4, 10_000, 50_000, 1, 11085883),
+    "scale": (16, 1_000_000, 5_000_000, 1, 11085884),
+    "multistart": (32, 2_000_000, 10_000_000, 256, 11085885),
+}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Polls SM clock and clock-event reasons through NVML (read-only queries) while running."""
+
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+    def __init__(self, device_index: int, period_s: float = 0.002):
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        self.ok = False
+        self.period = period_s
+        self._stop = threading.Event()
+        try:
+            import torch
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            p = torch.cuda.get_device_properties(device_index)
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0".encode()
+            self.dev = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.dev)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx)) == 0:  # 1 = SM clock
+                self.max_mhz = int(mx.value)
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        get_reasons = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self._stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(int(clk.value))
+            if get_reasons(self.dev, ctypes.byref(rs)) == 0:
+                self.reasons |= int(rs.value)
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"]}
+        names = [v for k, v in self.REASONS.items() if self.reasons & k]
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz, "reasons": names,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- ranks
+def dist_init(ngpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- workload
+def setup_workload(name, h, rank):
+    """Generate the synthetic workload on the device with the library's own kernels."""
+    import torch
+
+    from paper_1108_5882_gb300 import inputs, pwa
+    K, N, NMC, P, seed = WORKLOADS[name]
+    seed = seed + 1000 * rank
+    ws = inputs.wave_set_plain(seed) if name == "plain" else inputs.wave_set_spread(K, seed)
+    waves = pwa.waves_from(ws)
+    V_true = inputs.production_amplitudes(K, seed)
+    C = pwa.pwa_envelope(waves, V_true)
+    # data: accept-reject on the device (Philox candidates, candidate-ordered output)
+    kin = torch.zeros((3, N), dtype=torch.float32, device="cuda")
+    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    Vd = torch.from_numpy(V_true).cuda()
+    got, cand0, chunk = 0, 0, 1 << 25
+    while got < N:
+        tmp = torch.zeros((3, N - got), dtype=torch.float32, device="cuda")
+        h.pwa_generate(waves, Vd, seed, 0, cand0, chunk, C, tmp, N - got, na)
+        k = min(int(na.item()), N - got)
+        kin[:, got:got + k] = tmp[:, :k]
+        got += k
+        cand0 += chunk
+    kin_mc_h = inputs.kinematics(NMC, seed, 5)
+    kin_mc = torch.from_numpy(kin_mc_h).cuda()
+    A = torch.zeros((K, N), dtype=torch.complex64, device="cuda")
+    A_mc = torch.zeros((K, NMC), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(waves, kin, N, A)
+    h.pwa_amplitudes(waves, kin_mc, NMC, A_mc)
+    Psi = torch.zeros((K, K), dtype=torch.complex128, device="cuda")
+    h.pwa_normint(A_mc, NMC, Psi)
+    torch.cuda.synchronize()
+    # parameter sets visited by the steps: perturbations of the truth (a fit's iterates)
+    g = np.random.default_rng(seed)
+    n_sets = 64
+    Vs = []
+    for s in range(n_sets):
+        if P == 1:
+            pert = V_true * (1 + 0.05 * (g.normal(size=K) + 1j * g.normal(size=K)))
+            Vs.append(pert.astype(np.complex64)[None, :])
+        else:
+            Vs.append(inputs.starts(P, K, seed + s))
+    Vs = torch.from_numpy(np.stack(Vs)).cuda()
+    return dict(K=K, N=N, NMC=NMC, P=P, seed=seed, waves=waves, kin=kin, kin_mc=kin_mc, kin_mc_h=kin_mc_h,
+                A=A, A_mc=A_mc, Psi=Psi, Vs=Vs, ws=ws, V_true=V_true)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1108_5882_gb300 import build, pwa
+    if rank == 0 or world > 1:
+        build.build()
+    torch.cuda.set_device(local)
+    h = pwa.Handle(local)
+    wl = setup_workload(args.workload, h, rank)
+    K, N, P = wl["K"], wl["N"], wl["P"]
+    nll = torch.zeros(P, dtype=torch.float64, device="cuda")
+    grad = torch.zeros((P, 2 * K), dtype=torch.float64, device="cuda")
+    h.pwa_reserve(K, N, P)
+    stream = torch.cuda.current_stream()
+    # L2 flush: READ a 512 MiB buffer (> 129 MB L2) so that L2 holds clean lines of another buffer;
+    # a write-flush would leave ~126 MB of dirty lines whose write-back competes with the step
+    flush = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def l2_flush():
+        torch.sum(flush, dim=0, out=flush_out)
+
+    nsets = wl["Vs"].shape[0]
+
+    def step(i):
+        h.pwa_nll_grad(wl["A"], N, wl["Vs"][i % nsets], wl["Psi"], float(N), nll, grad)
+
+    for i in range(args.warmup):
+        l2_flush()
+        step(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    with sampler:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            l2_flush()
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = tot_ms / args.steps
+    value = world * N * P * args.steps / (tot_ms * 1e-3)
+    kernel_ms = sum(step_ms) / len(step_ms)  # one launch of the streaming kernel per step
+    ok = h.pwa_sync_status()
+
+    # ---- end to end from host buffers through the C ABI
+    kin_h = wl["kin"].cpu().pin_memory()
+    kin_mc_h = torch.from_numpy(wl["kin_mc_h"]).pin_memory()
+    kin_d = torch.empty_like(wl["kin"])
+    kin_mc_d = torch.empty_like(wl["kin_mc"])
+    V_h = wl["Vs"][0].cpu().pin_memory()
+    V_d = torch.empty_like(wl["Vs"][0])
+    nll_h = torch.empty(P, dtype=torch.float64).pin_memory()
+    grad_h = torch.empty((P, 2 * K), dtype=torch.float64).pin_memory()
+    A, A_mc, Psi = torch.empty_like(wl["A"]), torch.empty_like(wl["A_mc"]), torch.empty_like(wl["Psi"])
+    NMC = wl["NMC"]
+
+    def e2e_step():
+        kin_d.copy_(kin_h, non_blocking=True)
+        kin_mc_d.copy_(kin_mc_h, non_blocking=True)
+        V_d.copy_(V_h, non_blocking=True)
+        h.pwa_amplitudes(wl["waves"], kin_d, N, A)
+        h.pwa_amplitudes(wl["waves"], kin_mc_d, NMC, A_mc)
+        h.pwa_normint(A_mc, NMC, Psi)
+        h.pwa_nll_grad(A, N, V_d, Psi, float(N), nll, grad)
+        nll_h.copy_(nll, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    n_e2e = max(3, min(20, args.steps))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e, world)
+    h2d = kin_h.numel() * 4 + kin_mc_h.numel() * 4 + V_h.numel() * 8
+    d2h = nll_h.numel() * 8 + grad_h.numel() * 8
+
+    peak, peak_kind = measured_peaks()
+    alg_bytes = N * K * 8 + P * K * 8 + K * K * 16
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    launches = args.steps  # one k_nll_stream launch per step (P = 1)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (accept-reject from I on the GPU; flat MC)",
+        "config": {"workload": f"{args.workload}: K={K}, N_data={N}, N_MC={wl['NMC']}, P={P}, "
+                               "one -lnL+gradient evaluation per step, amplitudes and Psi precomputed",
+                   "K": K, "N_data": N, "N_MC": wl["NMC"], "P": P, "l2": "flushed before every step (512 MiB read)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * N * P / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "pinned H2D of data+MC kinematics, amplitudes(data, MC), Psi, -lnL+grad, D2H of nll+grad"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_nll_stream<16,true>", "bytes_per_launch": alg_bytes,
+                     "kernel_us": kernel_ms * 1e3, "peak_kind": f"{peak_kind} (copy bandwidth)"},
+        "clocks": sampler.summary(),
+        "status": pwa.status_string(ok), "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    h.close()
+    return res
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(wl_name, n_sample, rank=0):
+    """A bounded sample of the workload for the oracle: first n_sample events (oracle amplitudes
+    of the same flat/accept-reject recipe are not needed for timing; the oracle consumes
+    complex64 amplitudes exactly like the GPU path)."""
+    import oracle
+    from paper_1108_5882_gb300 import inputs
+    K, N, NMC, P, seed = WORKLOADS[wl_name]
+    ws = inputs.wave_set_plain(seed) if wl_name == "plain" else inputs.wave_set_spread(K, seed)
+    V_true = inputs.production_amplitudes(K, seed)
+    kin = inputs.kinematics(n_sample, seed, 4)
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin).astype(np.complex64)
+    kin_mc = inputs.kinematics(min(n_sample, 100_000), seed, 5)
+    Psi = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
+    if P == 1:
+        V = V_true[None, :]
+    else:
+        V = inputs.starts(min(P, 4), K, seed)
+    return A, V, Psi, N, P
+
+
+def cpu_baseline(wl, seconds):
+    import oracle
+    name = [k for k, v in WORKLOADS.items() if v[0] == wl["K"] and v[1] == wl["N"]][0]
+    n_s = 250_000 if wl["P"] == 1 else 50_000
+    A, V, Psi, N, P = oracle_sample(name, n_s)
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.nll_grad(A, V, Psi, n_factor=float(N))
+        evals += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": A.shape[1] * V.shape[0] * evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{evals} FP64 -lnL+gradient evaluations of the first {A.shape[1]} events x {V.shape[0]} "
+                      f"parameter set(s) of the workload (K={A.shape[0]}), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    K, N, NMC, P, seed = WORKLOADS[args.workload]
+    n_s = 100_000 if P == 1 else 20_000
+    A, V, Psi, _, _ = oracle_sample(args.workload, n_s)
+    for _ in range(args.warmup):
+        oracle.nll_grad(A, V, Psi, n_factor=float(N))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.nll_grad(A, V, Psi, n_factor=float(N))
+    dt = time.perf_counter() - t0
+    value = A.shape[1] * V.shape[0] * args.steps / dt
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"each step: FP64 -lnL+gradient of the first {A.shape[1]} events x {V.shape[0]} set(s)"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{args.workload}: K={K}, N_data={N}, P={P} (oracle on a "
+                                                        f"bounded sample of {A.shape[1]} events)",
+                                             "K": K, "N_data": N, "P": P},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        res = run_reference(args, world, rank)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    world, rank, local = dist_init(args.gpus)
+    res = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

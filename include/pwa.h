@@ -1,0 +1,178 @@
+/*
+ * pwa.h -- C ABI of the GB300 partial-wave-analysis library (libpwa.so).
+ *
+ * The library evaluates the unbinned extended negative log-likelihood of a coherent
+ * partial-wave model (Berger, "Partial Wave Analysis using Graphics Cards", arXiv:1108.5882,
+ * Sec. 2, Eqs. 1-3) and its analytic gradient in the complex production amplitudes V, the
+ * per-event decay amplitudes A_a(Omega), and the Monte-Carlo normalisation integral Psi.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Complex numbers are stored as interleaved (re, im) pairs: "complex float" = 2 floats
+ *    (8 bytes), "complex double" = 2 doubles (16 bytes).
+ *  - Amplitude arrays are wave-major structure-of-arrays: A[a][i] for wave a < K and event
+ *    i < n lives at complex offset a*ld + i, i.e. float offset 2*(a*ld + i).  ld (the leading
+ *    dimension, in complex elements) must be even and >= n, and the array must be 16-byte
+ *    aligned: the kernels stream two events per 16-byte load.
+ *  - Kinematics arrays are float SoA [3][ld]: m_KK (GeV), cos(theta), phi (rad).
+ *  - Every array argument is DEVICE memory owned by the caller unless marked "host".  The
+ *    library only borrows it for the duration of the stream-ordered call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *    asynchronous on that stream: outputs are valid once the stream reaches the call.
+ *  - Arguments are validated on the host before anything is launched; a rejected call returns
+ *    PWA_ERR_INVALID_ARG, launches nothing, leaves the outputs untouched and records a message
+ *    retrievable with pwa_last_error().
+ *  - Problems found on the device (an event with intensity <= 0 or not finite) cannot be
+ *    returned synchronously: the affected parameter set gets nll = +inf, and a sticky status
+ *    word in the handle is set; pwa_sync_status() reads and clears it.
+ *  - A handle owns a device workspace (block partial sums, completion counters).  Calls that
+ *    share a handle must be ordered on one stream; use one handle per concurrent stream.
+ *  - There is no CPU fallback: without a CUDA device pwa_create() fails with
+ *    PWA_ERR_NO_DEVICE.
+ */
+#ifndef PWA_H
+#define PWA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PWA_API __attribute__((visibility("default")))
+#else
+#define PWA_API
+#endif
+
+#define PWA_ABI_VERSION 1
+#define PWA_MAX_WAVES 64
+
+typedef enum pwa_status {
+    PWA_OK = 0,
+    PWA_ERR_INVALID_ARG = -1,
+    PWA_ERR_NO_DEVICE = -2,
+    PWA_ERR_CUDA = -3,
+    PWA_ERR_NONFINITE = -4,   /* some event had I_i <= 0 or a non-finite intensity */
+    PWA_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    PWA_ERR_WORKSPACE = -6,   /* workspace allocation failed */
+    PWA_NOT_CONVERGED = 1     /* warning from the fitters */
+} pwa_status;
+
+typedef struct pwa_handle pwa_handle;
+
+/* One partial wave: A_a(Omega) = BW(m; mass, width) * P_J(cos theta) * exp(i lambda phi).
+ * The paper leaves the amplitude model to the analysis (Sec. 2 names only "the complex decay
+ * amplitude"); this library uses the fixed-width relativistic Breit-Wigner normalised to unit
+ * modulus at the peak, BW(m) = M G / (M^2 - m^2 - i M G), and the ordinary Legendre
+ * polynomial P_J.  Constraints: 0 <= J <= 8, |lambda| <= 8, mass > 0, width > 0. */
+typedef struct pwa_wave {
+    int J;
+    int lambda;
+    double mass;
+    double width;
+} pwa_wave;
+
+/* ABI version of the loaded library (PWA_ABI_VERSION at build time). */
+PWA_API int pwa_abi_version(void);
+
+/* Human-readable name of a pwa_status value.  Never NULL. */
+PWA_API const char* pwa_status_string(int status);
+
+/* Create a handle bound to CUDA device `device`.  Fails with PWA_ERR_NO_DEVICE when no
+ * device is visible and PWA_ERR_INVALID_ARG for a bad index.  *h is NULL on failure. */
+PWA_API pwa_status pwa_create(pwa_handle** h, int device);
+
+/* Release the handle and its workspace (synchronises the device first).  NULL is a no-op. */
+PWA_API void pwa_destroy(pwa_handle* h);
+
+/* Message describing the last failed call on this handle ("" if none).  Owned by the handle;
+ * valid until the next call on it. h may be NULL (returns the last create() error). */
+PWA_API const char* pwa_last_error(const pwa_handle* h);
+
+/* Bytes of device workspace a pwa_nll / pwa_nll_grad call with these sizes uses. */
+PWA_API size_t pwa_workspace_size(const pwa_handle* h, int K, int64_t n, int P);
+
+/* Grow the workspace to fit calls up to (K, n, P) now, so that later calls allocate nothing
+ * (required before capturing those calls into a CUDA graph). */
+PWA_API pwa_status pwa_reserve(pwa_handle* h, int K, int64_t n, int P);
+
+/* Synchronise `stream`, then read and clear the device status word: PWA_OK, or
+ * PWA_ERR_NONFINITE if any evaluation since the last check met I_i <= 0 / non-finite. */
+PWA_API pwa_status pwa_sync_status(pwa_handle* h, void* stream);
+
+/* Decay amplitudes A_a(Omega_i) (Sec. 2, Eq. 1; "facilities for amplitude calculation",
+ * Sec. 3) for K waves over n events, computed in single precision (Sec. 2 precision remark).
+ *   waves  host array [K]
+ *   kin    float [3][ld]            m_KK, cos(theta), phi
+ *   A      complex float [K][ld]    output; columns n..ld-1 are set to zero
+ *   dA_dM, dA_dW   complex float [K][ld] or NULL: derivatives of A_a in the mass and width
+ *                  of wave a (for fits in which masses and widths float, Sec. 2)
+ * 1 <= K <= PWA_MAX_WAVES, n >= 0, ld >= n, ld even, kin and outputs 16-byte aligned. */
+PWA_API pwa_status pwa_amplitudes(pwa_handle* h, const pwa_wave* waves, int K, const float* kin,
+                          int64_t n, int64_t ld, float* A, float* dA_dM, float* dA_dW,
+                          void* stream);
+
+/* Monte-Carlo normalisation integral (Sec. 2, Eq. 3, inner bracket of the second term):
+ *   Psi_ab = (1/n_gen) * sum_{j < n_mc} w_j A_a(j) conj(A_b(j))
+ * summed in single precision per thread with compensated (double-single) carries, and
+ * finalised in double precision.
+ *   A_mc   complex float [K][ld]
+ *   w      float [n_mc] or NULL: 1/0 acceptance flags or event weights (non-uniform MC,
+ *          Sec. 2 footnote 1); NULL means w_j = 1 for every event
+ *   n_gen  number of generated MC events (> 0, finite), may exceed n_mc (acceptance)
+ *   Psi    complex double [K][K] output (full Hermitian matrix) */
+PWA_API pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t n_mc, int64_t ld,
+                       const float* w, double n_gen, double* Psi, void* stream);
+
+/* Extended negative log-likelihood (Sec. 2, Eq. 3 and footnote 2) for P parameter sets:
+ *   nll[p] = -sum_{i<n} ln |sum_a V[p][a] A_a(i)|^2 + n_factor * sum_ab V[p][a] conj(V[p][b]) Psi_ab
+ *   A      complex float [K][ld]    data amplitudes
+ *   V      complex float [P][K]     production amplitudes
+ *   Psi    complex double [K][K]    normalisation integral (pwa_normint)
+ *   n_factor  the factor on the normalisation term (the number of data events for the
+ *             extended likelihood; 1.0 gives Eq. 3 exactly as printed)
+ *   nll    double [P] output (+inf for a set that met I_i <= 0 or a non-finite intensity)
+ * Event sums run in single precision per thread, then double-single across threads and
+ * blocks in a fixed order (deterministic: identical inputs give identical bits). */
+PWA_API pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V,
+                   int P, const double* Psi, double n_factor, double* nll, void* stream);
+
+/* As pwa_nll, plus the gradient in the real coordinates of V:
+ *   grad[p][2c] = d nll[p] / d Re V[p][c],  grad[p][2c+1] = d nll[p] / d Im V[p][c]
+ * i.e. (Re, Im) of g_c = 2 d nll / d conj(V_c)
+ *                      = -2 sum_i conj(A_c(i)) u_i / |u_i|^2 + 2 n_factor sum_a Psi_ac V_a,
+ * u_i = sum_a V_a A_a(i).   grad: double [P][2K] output (zero for a non-finite set). */
+PWA_API pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld,
+                        const float* V, int P, const double* Psi, double n_factor, double* nll,
+                        double* grad, void* stream);
+
+/* Bound C >= max over the flat phase space of I(Omega) = |sum_a V_a A_a(Omega)|^2 (Eq. 1)
+ * for m in [m_lo, m_hi], used as the accept-reject envelope of pwa_generate.  HOST function
+ * (no device work): V is a HOST complex float [K] array.  On each of n_intervals equal
+ * m-intervals |BW_a| is maximal at m = M_a when M_a lies inside, else at the interval end
+ * nearer M_a, and |P_J| <= 1, |exp(i lambda phi)| = 1; C is the largest interval value of
+ * (sum_a |V_a| max|BW_a|)^2.  Returns a negative value for invalid arguments. */
+PWA_API double pwa_envelope(const pwa_wave* waves, int K, const float* V, double m_lo, double m_hi,
+                    int n_intervals);
+
+/* Toy events drawn by accept-reject from I(Omega) (Eq. 1) on the flat phase space
+ * m_KK in [0.99, 3.0), cos(theta) in [-1, 1), phi in [0, 2 pi).
+ * Candidate j (cand0 <= j < cand0 + n_cand) takes its phase-space point and accept uniform
+ * from Philox4x32-10 (Salmon et al., SC'11) with counter (j_lo, j_hi, stream_id, 0) and key
+ * (seed_lo, seed_hi); it is accepted iff u * envelope < I(Omega_j) (I in single precision).
+ *   V           complex float [K] (device)
+ *   kin         float [3][ld_out] output: accepted events in candidate order (first max_out)
+ *   n_accepted  int64 (device) output: number accepted in the range (may exceed max_out)
+ * The result is deterministic: independent of the launch geometry. */
+PWA_API pwa_status pwa_generate(pwa_handle* h, const pwa_wave* waves, int K, const float* V, uint64_t seed,
+                        uint32_t stream_id, int64_t cand0, int64_t n_cand, double envelope,
+                        float* kin, int64_t ld_out, int64_t max_out, int64_t* n_accepted,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PWA_H */

@@ -22,7 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SRC = [os.path.join(_HERE, f) for f in ("pwa_oracle.c", "pwa_oracle_fit.c")]
+_SRC = [os.path.join(_HERE, f) for f in ("pwa_oracle.c", "pwa_oracle_gen.c", "pwa_oracle_fit.c")]
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -72,10 +72,14 @@ def _load():
 
 
 def _register_fit(lib):
-    if hasattr(lib, "orc_philox4x32"):
-        lib.orc_philox4x32.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
-                                       ctypes.POINTER(ctypes.c_uint32)]
-        lib.orc_philox4x32.restype = None
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.orc_philox4x32.argtypes = [u32p, u32p, u32p]
+    lib.orc_philox4x32.restype = None
+    lib.orc_envelope.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.orc_envelope.restype = ctypes.c_double
+    lib.orc_generate.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_uint64, ctypes.c_uint32, _i64,
+                                 _i64, ctypes.c_double, _fp, _i64, _i64, _dp]
+    lib.orc_generate.restype = ctypes.c_int64
 
 
 def _ptr(a, t):
@@ -163,3 +167,41 @@ def nll_double_sum(A, V, Psi, n_factor=None) -> float:
         n_factor = float(n)
     return lib.orc_nll_double_sum(K, n, _ptr(Af, _fp), n, _ptr(V, _dp), _ptr(Psi, _dp),
                                   float(n_factor))
+
+
+# ------------------------------------------------------------------ toy generator -------------
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of one 128-bit counter under a 64-bit key -> 4 uint32."""
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32(c, k, o)
+    return [int(x) for x in o]
+
+
+def envelope(M, W, V, m_lo=0.99, m_hi=3.0, n_int=4096) -> float:
+    """Rigorous bound C >= max I(Omega) over the flat phase space (see pwa_oracle_gen.c)."""
+    lib = _load()
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    return lib.orc_envelope(M.shape[0], _ptr(M, _dp), _ptr(W, _dp), _ptr(V, _dp), m_lo, m_hi, n_int)
+
+
+def generate(J, lam, M, W, V, seed, stream, cand0, n_cand, C, max_out):
+    """Accept-reject toys: returns (kin float32 [3][n_out], n_accepted, max I/C)."""
+    lib = _load()
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    kin = np.zeros((3, max(int(max_out), 1)), dtype=np.float32)
+    mr = np.zeros(1, dtype=np.float64)
+    na = lib.orc_generate(J.shape[0], _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), _ptr(V, _dp),
+                          int(seed), int(stream), int(cand0), int(n_cand), float(C), _ptr(kin, _fp),
+                          kin.shape[1], int(max_out), _ptr(mr, _dp))
+    n_out = min(int(na), int(max_out))
+    return np.ascontiguousarray(kin[:, :n_out]), int(na), float(mr[0])

@@ -1,0 +1,349 @@
+// C ABI of libpwa.so: handle lifetime, argument validation, workspace management and
+// dispatch to the kernels.  Every entry point validates its arguments on the host before
+// launching anything; there is no CPU fallback path.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "pwa_internal.cuh"
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_create_err;
+
+pwa_status fail(pwa_handle* h, pwa_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_err = buf;
+    }
+    return st;
+}
+
+pwa_status cuda_fail(pwa_handle* h, cudaError_t e, const char* what) {
+    return fail(h, PWA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Make the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+pwa_status ensure_workspace(pwa_handle* h, size_t bytes, int P) {
+    if (bytes > h->ws_bytes) {
+        if (h->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->ws);
+            h->ws = nullptr;
+            h->ws_bytes = 0;
+        }
+        size_t want = bytes + bytes / 4;
+        cudaError_t e = cudaMalloc(&h->ws, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PWA_ERR_WORKSPACE, "workspace allocation of %zu bytes failed: %s", want,
+                        cudaGetErrorString(e));
+        }
+        h->ws_bytes = want;
+    }
+    if (P > h->bad_cap) {
+        if (h->bad) {
+            cudaDeviceSynchronize();
+            cudaFree(h->bad);
+            h->bad = nullptr;
+            h->bad_cap = 0;
+        }
+        int cap = P < 1024 ? 1024 : P;
+        cudaError_t e = cudaMalloc(&h->bad, sizeof(int) * (size_t)cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PWA_ERR_WORKSPACE, "flag allocation failed: %s", cudaGetErrorString(e));
+        }
+        e = cudaMemset(h->bad, 0, sizeof(int) * (size_t)cap);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
+        h->bad_cap = cap;
+    }
+    return PWA_OK;
+}
+
+pwa_status check_amp_layout(pwa_handle* h, int K, int64_t n, int64_t ld) {
+    if (K < 1 || K > PWA_MAX_WAVES)
+        return fail(h, PWA_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, PWA_MAX_WAVES);
+    if (n < 0) return fail(h, PWA_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (ld < n) return fail(h, PWA_ERR_INVALID_ARG, "ld = %lld < n = %lld", (long long)ld, (long long)n);
+    if (ld & 1) return fail(h, PWA_ERR_INVALID_ARG, "ld = %lld must be even", (long long)ld);
+    if ((int64_t)K * ld > ((int64_t)1 << 40))
+        return fail(h, PWA_ERR_INVALID_ARG, "K * ld = %lld too large", (long long)((int64_t)K * ld));
+    return PWA_OK;
+}
+
+pwa_status fill_waves(pwa_handle* h, const pwa_wave* waves, int K, pwa::WaveTable* wt) {
+    wt->K = K;
+    for (int a = 0; a < K; ++a) {
+        const pwa_wave& w = waves[a];
+        if (w.J < 0 || w.J > 8 || w.lambda < -8 || w.lambda > 8)
+            return fail(h, PWA_ERR_INVALID_ARG, "wave %d: J = %d or lambda = %d out of range", a, w.J, w.lambda);
+        if (!(w.mass > 0.0) || !(w.width > 0.0) || !std::isfinite(w.mass) || !std::isfinite(w.width))
+            return fail(h, PWA_ERR_INVALID_ARG, "wave %d: mass and width must be finite and > 0", a);
+        wt->J[a] = w.J;
+        wt->lam[a] = w.lambda;
+        wt->Mhi[a] = (float)w.mass;
+        wt->Mlo[a] = (float)(w.mass - (double)wt->Mhi[a]);
+        wt->W[a] = (float)w.width;
+        wt->MW[a] = (float)(w.mass * w.width);
+    }
+    return PWA_OK;
+}
+
+pwa_status nll_common(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V, int P,
+                      const double* Psi, double n_factor, double* nll, double* grad, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    if (P < 1 || P > (1 << 24)) return fail(h, PWA_ERR_INVALID_ARG, "P = %d outside [1, 2^24]", P);
+    if ((n > 0 && !A) || !V || !Psi || !nll)
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array argument (A, V, Psi and nll are required)");
+    if (n > 0 && !aligned16(A)) return fail(h, PWA_ERR_INVALID_ARG, "A is not 16-byte aligned");
+    if (!aligned16(Psi)) return fail(h, PWA_ERR_INVALID_ARG, "Psi is not 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) != 0) return fail(h, PWA_ERR_INVALID_ARG, "V is not 8-byte aligned");
+    if (!std::isfinite(n_factor)) return fail(h, PWA_ERR_INVALID_ARG, "n_factor is not finite");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::nll_workspace(K, n, P, h->sm_count), P);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_nll(reinterpret_cast<const float2*>(A), K, n, ld, reinterpret_cast<const float2*>(V),
+                                    P, reinterpret_cast<const double2*>(Psi), n_factor, nll, grad, h->ws, h->ws_bytes,
+                                    h->counters, h->bad, h->status, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "nll launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pwa_abi_version(void) { return PWA_ABI_VERSION; }
+
+const char* pwa_status_string(int s) {
+    switch (s) {
+        case PWA_OK: return "PWA_OK";
+        case PWA_ERR_INVALID_ARG: return "PWA_ERR_INVALID_ARG";
+        case PWA_ERR_NO_DEVICE: return "PWA_ERR_NO_DEVICE";
+        case PWA_ERR_CUDA: return "PWA_ERR_CUDA";
+        case PWA_ERR_NONFINITE: return "PWA_ERR_NONFINITE";
+        case PWA_ERR_TIMEOUT: return "PWA_ERR_TIMEOUT";
+        case PWA_ERR_WORKSPACE: return "PWA_ERR_WORKSPACE";
+        case PWA_NOT_CONVERGED: return "PWA_NOT_CONVERGED";
+        default: return "PWA_UNKNOWN_STATUS";
+    }
+}
+
+pwa_status pwa_create(pwa_handle** out, int device) {
+    if (!out) return PWA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(nullptr, PWA_ERR_NO_DEVICE, "no CUDA device: %s",
+                    e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0");
+    }
+    if (device < 0 || device >= count)
+        return fail(nullptr, PWA_ERR_INVALID_ARG, "device %d outside [0, %d)", device, count);
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(nullptr, PWA_ERR_CUDA, "cannot select device %d", device);
+    pwa_handle* h = new pwa_handle();
+    h->device = device;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (h->sm_count <= 0) h->sm_count = 1;
+    e = cudaMalloc(&h->counters, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        pwa_status st = fail(nullptr, PWA_ERR_CUDA, "handle allocation: %s", cudaGetErrorString(e));
+        pwa_destroy(h);
+        return st;
+    }
+    *out = h;
+    return PWA_OK;
+}
+
+void pwa_destroy(pwa_handle* h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->counters) cudaFree(h->counters);
+    if (h->status) cudaFree(h->status);
+    if (h->bad) cudaFree(h->bad);
+    delete h;
+}
+
+const char* pwa_last_error(const pwa_handle* h) {
+    if (h) return h->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_create_err.c_str();
+}
+
+size_t pwa_workspace_size(const pwa_handle* h, int K, int64_t n, int P) {
+    if (!h || K < 1 || K > PWA_MAX_WAVES || n < 0 || P < 1) return 0;
+    size_t a = pwa::nll_workspace(K, n, P, h->sm_count);
+    size_t b = pwa::normint_workspace(K, h->sm_count);
+    return a > b ? a : b;
+}
+
+pwa_status pwa_reserve(pwa_handle* h, int K, int64_t n, int P) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (K < 1 || K > PWA_MAX_WAVES || n < 0 || P < 1)
+        return fail(h, PWA_ERR_INVALID_ARG, "bad sizes K=%d n=%lld P=%d", K, (long long)n, P);
+    DeviceGuard dg(h->device);
+    return ensure_workspace(h, pwa_workspace_size(h, K, n, P), P);
+}
+
+pwa_status pwa_sync_status(pwa_handle* h, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    int s = 0;
+    e = cudaMemcpy(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (s) {
+        e = cudaMemset(h->status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+        return fail(h, PWA_ERR_NONFINITE, "an evaluation met an event with intensity <= 0 or not finite");
+    }
+    return PWA_OK;
+}
+
+pwa_status pwa_amplitudes(pwa_handle* h, const pwa_wave* waves, int K, const float* kin, int64_t n,
+                          int64_t ld, float* A, float* dA_dM, float* dA_dW, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    if (!waves) return fail(h, PWA_ERR_INVALID_ARG, "waves is NULL");
+    if (ld > 0 && (!A || (n > 0 && !kin)))
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL kinematics or amplitude array");
+    if ((dA_dM == nullptr) != (dA_dW == nullptr))
+        return fail(h, PWA_ERR_INVALID_ARG, "dA_dM and dA_dW must be both given or both NULL");
+    if ((A && !aligned16(A)) || (kin && !aligned16(kin)) || (dA_dM && !aligned16(dA_dM)) ||
+        (dA_dW && !aligned16(dA_dW)))
+        return fail(h, PWA_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+    pwa::WaveTable wt;
+    st = fill_waves(h, waves, K, &wt);
+    if (st != PWA_OK) return st;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = pwa::launch_amplitudes(wt, kin, n, ld, reinterpret_cast<float2*>(A),
+                                           reinterpret_cast<float2*>(dA_dM), reinterpret_cast<float2*>(dA_dW),
+                                           h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "amplitude launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t n_mc, int64_t ld, const float* w,
+                       double n_gen, double* Psi, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n_mc, ld);
+    if (st != PWA_OK) return st;
+    if ((n_mc > 0 && !A_mc) || !Psi) return fail(h, PWA_ERR_INVALID_ARG, "NULL A_mc or Psi");
+    if (n_mc > 0 && !aligned16(A_mc)) return fail(h, PWA_ERR_INVALID_ARG, "A_mc is not 16-byte aligned");
+    if (!aligned16(Psi)) return fail(h, PWA_ERR_INVALID_ARG, "Psi is not 16-byte aligned");
+    if (w && (reinterpret_cast<uintptr_t>(w) & 3u)) return fail(h, PWA_ERR_INVALID_ARG, "w is not 4-byte aligned");
+    if (!(n_gen > 0.0) || !std::isfinite(n_gen))
+        return fail(h, PWA_ERR_INVALID_ARG, "n_gen must be finite and > 0");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::normint_workspace(K, h->sm_count), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_normint(reinterpret_cast<const float2*>(A_mc), K, n_mc, ld, w, n_gen,
+                                        reinterpret_cast<double2*>(Psi), h->ws, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "normint launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V, int P,
+                   const double* Psi, double n_factor, double* nll, void* stream) {
+    return nll_common(h, A, K, n, ld, V, P, Psi, n_factor, nll, nullptr, stream);
+}
+
+pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V, int P,
+                        const double* Psi, double n_factor, double* nll, double* grad, void* stream) {
+    if (h && !grad) return fail(h, PWA_ERR_INVALID_ARG, "grad is NULL");
+    return nll_common(h, A, K, n, ld, V, P, Psi, n_factor, nll, grad, stream);
+}
+
+double pwa_envelope(const pwa_wave* waves, int K, const float* V, double m_lo, double m_hi, int n_intervals) {
+    if (!waves || !V || K < 1 || K > PWA_MAX_WAVES || !(m_hi > m_lo) || n_intervals < 1) return -1.0;
+    double best = 0.0;
+    for (int k = 0; k < n_intervals; ++k) {
+        const double a0 = m_lo + (m_hi - m_lo) * k / n_intervals;
+        const double a1 = m_lo + (m_hi - m_lo) * (k + 1) / n_intervals;
+        double s = 0.0;
+        for (int a = 0; a < K; ++a) {
+            const double M = waves[a].mass, W = waves[a].width;
+            if (!(M > 0.0) || !(W > 0.0)) return -1.0;
+            // |BW|^2 = (M W)^2 / ((M^2 - m^2)^2 + (M W)^2) rises below M and falls above it
+            const double mm = M < a0 ? a0 : (M > a1 ? a1 : M);
+            const double d = M * M - mm * mm;
+            s += std::hypot((double)V[2 * a], (double)V[2 * a + 1]) * (M * W / std::sqrt(d * d + M * M * W * W));
+        }
+        if (s * s > best) best = s * s;
+    }
+    return best;
+}
+
+pwa_status pwa_generate(pwa_handle* h, const pwa_wave* waves, int K, const float* V, uint64_t seed,
+                        uint32_t stream_id, int64_t cand0, int64_t n_cand, double envelope, float* kin,
+                        int64_t ld_out, int64_t max_out, int64_t* n_accepted, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (!waves || !V || !n_accepted || (max_out > 0 && !kin))
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL argument (waves, V, n_accepted, kin)");
+    if (K < 1 || K > PWA_MAX_WAVES) return fail(h, PWA_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, PWA_MAX_WAVES);
+    if (cand0 < 0 || n_cand < 0 || max_out < 0 || ld_out < max_out)
+        return fail(h, PWA_ERR_INVALID_ARG, "bad sizes: cand0, n_cand, max_out >= 0 and ld_out >= max_out required");
+    if (n_cand > ((int64_t)1 << 40)) return fail(h, PWA_ERR_INVALID_ARG, "n_cand too large");
+    if (!(envelope > 0.0) || !std::isfinite(envelope) || envelope > 3.0e38)
+        return fail(h, PWA_ERR_INVALID_ARG, "envelope must be finite and > 0");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) || (reinterpret_cast<uintptr_t>(n_accepted) & 7u))
+        return fail(h, PWA_ERR_INVALID_ARG, "V must be 8-byte aligned, n_accepted 8-byte aligned");
+    pwa::WaveTable wt;
+    pwa_status st = fill_waves(h, waves, K, &wt);
+    if (st != PWA_OK) return st;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::generate_workspace(n_cand), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_generate(wt, reinterpret_cast<const float2*>(V), seed, stream_id, cand0, n_cand,
+                                         envelope, kin, ld_out, max_out, reinterpret_cast<long long*>(n_accepted),
+                                         h->ws, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "generate launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,758 @@
+// Extended negative log-likelihood and its gradient in V (Sec. 2, Eq. 3 and footnote 2):
+//
+//   f(V)  = -sum_i ln I_i + n_f * S(V),     I_i = |u_i|^2,  u_i = sum_a V_a A_a(i),
+//   S(V)  = sum_ab V_a conj(V_b) Psi_ab,
+//   g_c   = dF/dRe V_c + i dF/dIm V_c = -2 sum_i conj(A_c(i)) u_i / I_i + 2 n_f sum_a Psi_ac V_a.
+//
+// The per-event K x K table of Sec. 2 (A_a conj(A_a') precomputed per event) is not built:
+// the double sum over (a, a') of Eq. 3 equals |u_i|^2 of Eq. 1, which costs 2K reals and
+// 8K flops per event instead of K^2 of each, so the data sum streams A once per evaluation.
+//
+// Two kernels:
+//  * k_nll_stream  (one parameter set): HBM-bound stream over A (8K bytes per event).  Each
+//    thread takes two events per 16-byte load per wave, holds V in shared memory, and keeps
+//    FP32 gradient partials in registers.  Warp partials are combined by a reduce-scatter
+//    (31 shuffles for 32 values), blocks write double-single partials, and the last block to
+//    finish (completion counter) sums the partials in block order and adds the FP64
+//    normalisation term: one launch per evaluation, deterministic.
+//  * k_nll_batched (P > 1 parameter sets, multi-start): the event x wave x start complex
+//    contraction U = A V^T, W = U / |U|^2, G = A^H W on FP32 FMA pipes, tiled through shared
+//    memory (an A tile of E events feeds both contractions), with per-start compensated
+//    sums of ln I.  k_nll_finalize then sums the chunk partials per start in order and adds
+//    the normalisation term in FP64.
+//
+// Sec. 2 precision remark: amplitudes in single precision, the final sum in double
+// precision with a tree-like summation order; here every long sum is carried as a
+// double-single pair and combined along a fixed tree (thread -> warp -> block -> grid).
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "pwa_internal.cuh"
+
+namespace pwa {
+
+namespace {
+
+// ======================================================================= one parameter set
+template <int KMAX, bool GRAD, bool HOLD>
+__global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
+    const float2* __restrict__ A, int K, int64_t n, int64_t ld, const float2* __restrict__ V,
+    const double2* __restrict__ Psi, double nfac, float2* __restrict__ part, unsigned* __restrict__ counter,
+    int* __restrict__ badw, int* __restrict__ status, double* __restrict__ nll, double* __restrict__ grad) {
+    constexpr bool EV2 = KMAX <= 16;   // two events per thread and iteration (16-byte loads)
+    // HOLD: keep the event's amplitudes in registers for the gradient pass; otherwise reload
+    // them (L1 hits: the same lines were just read) to free registers for more warps
+    constexpr int NG = 2 * KMAX;
+    constexpr int ROUNDS = (NG + 31) / 32;
+    constexpr int NW = PWA_THREADS / 32;
+    __shared__ float2 sV[KMAX];
+    __shared__ float sred[NW][ROUNDS * 32];
+    __shared__ ff slred[NW];
+    __shared__ int sLast;
+    __shared__ ff sfin[PWA_THREADS];
+    __shared__ double sval[1 + NG];
+    __shared__ double2 sT[KMAX];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < KMAX) sV[tid] = tid < K ? V[tid] : make_float2(0.f, 0.f);
+    __syncthreads();
+
+    float g[NG];
+#pragma unroll
+    for (int v = 0; v < NG; ++v) g[v] = 0.f;
+    ff lacc = ff_zero();
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * PWA_THREADS;
+
+    if (EV2) {
+        const float4* A4 = reinterpret_cast<const float4*>(A);
+        const int64_t ld2 = ld >> 1;
+        const int64_t npairs = (n + 1) >> 1;
+        for (int64_t q = (int64_t)blockIdx.x * PWA_THREADS + tid; q < npairs; q += stride) {
+            float4 a[KMAX];
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c) a[c] = (c < K) ? __ldg(A4 + c * ld2 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool has1 = 2 * q + 1 < n;
+            if (!has1) {  // odd n: the pair's second slot is padding, whatever it holds
+#pragma unroll
+                for (int c = 0; c < KMAX; ++c) a[c].z = a[c].w = 0.f;
+            }
+            float u0r = 0.f, u0i = 0.f, u1r = 0.f, u1i = 0.f;
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c) {
+                const float2 v = sV[c];
+                u0r += v.x * a[c].x - v.y * a[c].y;
+                u0i += v.x * a[c].y + v.y * a[c].x;
+                u1r += v.x * a[c].z - v.y * a[c].w;
+                u1i += v.x * a[c].w + v.y * a[c].z;
+            }
+            const float I0 = u0r * u0r + u0i * u0i;
+            const float I1 = u1r * u1r + u1i * u1i;
+            float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f;
+            if (intensity_ok(I0)) {
+                lacc = ff_add_f(lacc, logf(I0));
+                const float r = 1.f / I0;
+                w0r = u0r * r;
+                w0i = u0i * r;
+            } else {
+                bad = true;
+            }
+            if (has1) {
+                if (intensity_ok(I1)) {
+                    lacc = ff_add_f(lacc, logf(I1));
+                    const float r = 1.f / I1;
+                    w1r = u1r * r;
+                    w1i = u1i * r;
+                } else {
+                    bad = true;
+                }
+            }
+            if (GRAD) {
+#pragma unroll
+                for (int c = 0; c < KMAX; ++c) {
+                    float4 x = a[c];
+                    if (!HOLD) {
+                        x = (c < K) ? __ldg(A4 + c * ld2 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (!has1) x.z = x.w = 0.f;
+                    }
+                    g[2 * c] += x.x * w0r + x.y * w0i + x.z * w1r + x.w * w1i;
+                    g[2 * c + 1] += x.x * w0i - x.y * w0r + x.z * w1i - x.w * w1r;
+                }
+            }
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * PWA_THREADS + tid; i < n; i += stride) {
+            float2 a[HOLD ? KMAX : 1];
+            float ur = 0.f, ui = 0.f;
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c) {
+                const float2 x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
+                if (HOLD) a[c] = x;
+                const float2 v = sV[c];
+                ur += v.x * x.x - v.y * x.y;
+                ui += v.x * x.y + v.y * x.x;
+            }
+            const float I0 = ur * ur + ui * ui;
+            float wr = 0.f, wi = 0.f;
+            if (intensity_ok(I0)) {
+                lacc = ff_add_f(lacc, logf(I0));
+                const float r = 1.f / I0;
+                wr = ur * r;
+                wi = ui * r;
+            } else {
+                bad = true;
+            }
+            if (GRAD) {
+#pragma unroll
+                for (int c = 0; c < KMAX; ++c) {
+                    float2 x;
+                    if (HOLD) x = a[c];
+                    else x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
+                    g[2 * c] += x.x * wr + x.y * wi;
+                    g[2 * c + 1] += x.x * wi - x.y * wr;
+                }
+            }
+        }
+    }
+
+    // ---- warp: reduce-scatter of the gradient partials, butterfly of the ln I pair
+    if (GRAD) {
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (32 * r + j < NG) x[j] = g[32 * r + j];
+                else x[j] = 0.f;
+            }
+            warp_transpose_reduce32(x);
+            sred[warp][32 * r + lane] = x[0];
+        }
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) lacc = ff_add(lacc, ff_shfl_xor(lacc, m));
+    if (lane == 0) slred[warp] = lacc;
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+
+    // ---- block: fixed-order double-single sum over warps -> block partial
+    const int NV = 1 + 2 * K;
+    float2* bp = part + (int64_t)blockIdx.x * NV;
+    if (tid == 0) {
+        ff s = ff_zero();
+        for (int w = 0; w < NW; ++w) s = ff_add(s, slred[w]);
+        bp[0] = make_float2(s.hi, s.lo);
+    }
+    if (GRAD && tid < 2 * K) {
+        ff s = ff_zero();
+        for (int w = 0; w < NW; ++w) s = ff_add_f(s, sred[w][tid]);
+        bp[1 + tid] = make_float2(s.hi, s.lo);
+    }
+    if (any_bad && tid == 0) atomicOr(badw, 1);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sLast = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!sLast) return;
+
+    // ---- last block: sum the block partials in block order (double-single), finalise in FP64
+    __threadfence();
+    const int NVu = GRAD ? NV : 1;
+    const int nch = PWA_THREADS / NVu;
+    if (tid < nch * NVu) {
+        const int v = tid % NVu, ch = tid / NVu;
+        // blocks ch, ch + nch, ch + 2 nch, ... in increasing order
+        const int cnt = ((int)gridDim.x - ch + nch - 1) / nch;
+        sfin[tid] = ff_sum_strided(part, (int64_t)ch * NV + v, (int64_t)nch * NV, cnt);
+    }
+    __syncthreads();
+    if (tid < NVu) {
+        ff s = ff_zero();
+        for (int ch = 0; ch < nch; ++ch) s = ff_add(s, sfin[ch * NVu + tid]);
+        sval[tid] = ff_to_double(s);
+    }
+    // t_c = sum_a Psi_ac V_a  (FP64, K^2 complex multiply-adds)
+    if (tid < K) {
+        double tr = 0.0, ti = 0.0;
+        for (int a = 0; a < K; ++a) {
+            const double2 p = Psi[a * K + tid];
+            const double vr = sV[a].x, vi = sV[a].y;
+            tr += p.x * vr - p.y * vi;
+            ti += p.x * vi + p.y * vr;
+        }
+        sT[tid] = make_double2(tr, ti);
+    }
+    if (tid == 0) sLast = __ldcg(badw) != 0;  // reuse: now the non-finite flag of this evaluation
+    __syncthreads();
+    const bool isbad = sLast != 0;
+    if (tid == 0) {
+        // S = sum_c conj(V_c) t_c  (real by Hermiticity of Psi)
+        double S = 0.0;
+        for (int c = 0; c < K; ++c) S += (double)sV[c].x * sT[c].x + (double)sV[c].y * sT[c].y;
+        nll[0] = isbad ? INFINITY : (-sval[0] + nfac * S);
+        if (isbad) atomicOr(status, 1);
+        *badw = 0;
+        *counter = 0u;
+    }
+    if (GRAD && tid < K) {
+        grad[2 * tid] = isbad ? 0.0 : (-2.0 * sval[1 + 2 * tid] + 2.0 * nfac * sT[tid].x);
+        grad[2 * tid + 1] = isbad ? 0.0 : (-2.0 * sval[2 + 2 * tid] + 2.0 * nfac * sT[tid].y);
+    }
+}
+
+// ======================================================================= P parameter sets
+template <int KMAX, int E, int PB>
+struct BatchedCfg {
+    static constexpr int EA = E + 2;             // padded row stride of sA (float2, even -> 16-B rows)
+    static constexpr int EW = E + 2;             // padded row stride of sW ([PB][EW])
+    static constexpr int TE = E / 16;            // GEMM1 events per thread (pairs of 2)
+    static constexpr int TP = PB / 16;           // GEMM1 starts per thread (pairs of 2)
+    static constexpr int TA = KMAX < 16 ? KMAX : 16;
+    static constexpr int TPG = PWA_THREADS / TA;
+    static constexpr int KA = KMAX / TA;         // GEMM2 waves per thread
+    static constexpr int PP = PB / TPG;          // GEMM2 starts per thread
+    static constexpr int LD4 = KMAX * E / 2 / PWA_THREADS;  // float4 tile loads per thread
+    static constexpr int FLUSH = (128 + E - 1) / E;          // tiles between flushes of G
+    static constexpr size_t SMEM = sizeof(float2) * (KMAX * PB + KMAX * EA + PB * EW) +
+                                   sizeof(float4) * KMAX * PB + sizeof(ff) * PB + sizeof(int) * PB;
+    static_assert(TE >= 2 && TP >= 2 && PP >= 1 && KA >= 1, "tile shape");
+    static_assert(KMAX * E / 2 % PWA_THREADS == 0, "tile loader");
+};
+
+template <int KMAX, int E, int PB>
+__global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
+    const float2* __restrict__ A, int K, int64_t n, int64_t ld, const float2* __restrict__ V, int P,
+    int64_t ev_per_chunk, float2* __restrict__ part, int* __restrict__ bad, int with_grad) {
+    using C = BatchedCfg<KMAX, E, PB>;
+    extern __shared__ float4 smem[];
+    float2* sV = reinterpret_cast<float2*>(smem);  // [KMAX][PB]
+    float2* sA = sV + KMAX * PB;                    // [KMAX][EA]
+    float2* sW = sA + KMAX * C::EA;                 // [PB][EW]
+    float4* sG = reinterpret_cast<float4*>(sW + PB * C::EW);  // [KMAX][PB] complex double-single
+    ff* sL = reinterpret_cast<ff*>(sG + KMAX * PB);            // [PB]
+    int* sBad = reinterpret_cast<int*>(sL + PB);               // [PB]
+
+    const int tid = threadIdx.x;
+    const int chunk = blockIdx.x;
+    const int p0 = blockIdx.y * PB;
+    const int NV = 1 + 2 * K;
+
+    for (int idx = tid; idx < KMAX * PB; idx += PWA_THREADS) {
+        const int a = idx / PB, p = idx % PB;
+        sV[idx] = (a < K && p0 + p < P) ? V[(int64_t)(p0 + p) * K + a] : make_float2(0.f, 0.f);
+        sG[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int p = tid; p < PB; p += PWA_THREADS) {
+        sL[p] = ff_zero();
+        sBad[p] = 0;
+    }
+
+    const int64_t e_begin = (int64_t)chunk * ev_per_chunk;
+    int64_t e_end = e_begin + ev_per_chunk;
+    if (e_end > n) e_end = n;
+
+    // GEMM1 coordinates: events 2*te + {0,1} + 32*r, starts 2*tp + {0,1} + 32*s
+    const int te = tid % 16, tp = tid / 16;
+    // GEMM2 coordinates: waves ta + TA*k, starts tg + TPG*s
+    const int ta = tid % C::TA, tg = tid / C::TA;
+
+    float4 pre[C::LD4];
+    auto load_tile = [&](int64_t e0) {
+#pragma unroll
+        for (int j = 0; j < C::LD4; ++j) {
+            const int idx = tid + PWA_THREADS * j;
+            const int a = idx / (E / 2), c4 = idx % (E / 2);
+            const int64_t e = e0 + 2 * c4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a < K && e < e_end) {
+                v = __ldg(reinterpret_cast<const float4*>(A + a * ld + e));
+                if (e + 1 >= e_end) { v.z = 0.f; v.w = 0.f; }
+            }
+            pre[j] = v;
+        }
+    };
+
+    ff lsum[C::TP];
+#pragma unroll
+    for (int s = 0; s < C::TP; ++s) lsum[s] = ff_zero();
+    float gacc[C::KA][C::PP][2];
+#pragma unroll
+    for (int k = 0; k < C::KA; ++k)
+#pragma unroll
+        for (int s = 0; s < C::PP; ++s) gacc[k][s][0] = gacc[k][s][1] = 0.f;
+    int since_flush = 0;
+
+    auto flush_g = [&]() {
+#pragma unroll
+        for (int k = 0; k < C::KA; ++k)
+#pragma unroll
+            for (int s = 0; s < C::PP; ++s) {
+                float4* dst = sG + (ta + C::TA * k) * PB + (tg + C::TPG * s);
+                float4 cur = *dst;
+                ff re = ff_add_f(ff{cur.x, cur.y}, gacc[k][s][0]);
+                ff im = ff_add_f(ff{cur.z, cur.w}, gacc[k][s][1]);
+                *dst = make_float4(re.hi, re.lo, im.hi, im.lo);
+                gacc[k][s][0] = gacc[k][s][1] = 0.f;
+            }
+    };
+
+    if (e_begin < e_end) load_tile(e_begin);
+    for (int64_t e0 = e_begin; e0 < e_end; e0 += E) {
+        __syncthreads();  // previous GEMM2 done with sA / sW
+#pragma unroll
+        for (int j = 0; j < C::LD4; ++j) {
+            const int idx = tid + PWA_THREADS * j;
+            const int a = idx / (E / 2), c4 = idx % (E / 2);
+            *reinterpret_cast<float4*>(sA + a * C::EA + 2 * c4) = pre[j];
+        }
+        __syncthreads();
+        if (e0 + E < e_end) load_tile(e0 + E);  // prefetch next tile into registers
+
+        // ---- GEMM1: U[e][p] = sum_a A[a][e] V[p][a]
+        float u[C::TE][C::TP][2];
+#pragma unroll
+        for (int r = 0; r < C::TE; ++r)
+#pragma unroll
+            for (int s = 0; s < C::TP; ++s) u[r][s][0] = u[r][s][1] = 0.f;
+#pragma unroll 2
+        for (int a = 0; a < K; ++a) {
+            float4 av[C::TE / 2], vv[C::TP / 2];
+#pragma unroll
+            for (int r = 0; r < C::TE / 2; ++r) av[r] = *reinterpret_cast<const float4*>(sA + a * C::EA + 2 * te + 32 * r);
+#pragma unroll
+            for (int s = 0; s < C::TP / 2; ++s) vv[s] = *reinterpret_cast<const float4*>(sV + a * PB + 2 * tp + 32 * s);
+#pragma unroll
+            for (int r = 0; r < C::TE / 2; ++r)
+#pragma unroll
+                for (int s = 0; s < C::TP / 2; ++s) {
+                    // events (2r: av.x,av.y) (2r+1: av.z,av.w); starts (2s: vv.x,vv.y) (2s+1: vv.z,vv.w)
+                    u[2 * r][2 * s][0] += av[r].x * vv[s].x - av[r].y * vv[s].y;
+                    u[2 * r][2 * s][1] += av[r].x * vv[s].y + av[r].y * vv[s].x;
+                    u[2 * r][2 * s + 1][0] += av[r].x * vv[s].z - av[r].y * vv[s].w;
+                    u[2 * r][2 * s + 1][1] += av[r].x * vv[s].w + av[r].y * vv[s].z;
+                    u[2 * r + 1][2 * s][0] += av[r].z * vv[s].x - av[r].w * vv[s].y;
+                    u[2 * r + 1][2 * s][1] += av[r].z * vv[s].y + av[r].w * vv[s].x;
+                    u[2 * r + 1][2 * s + 1][0] += av[r].z * vv[s].z - av[r].w * vv[s].w;
+                    u[2 * r + 1][2 * s + 1][1] += av[r].z * vv[s].w + av[r].w * vv[s].z;
+                }
+        }
+        // ---- epilogue: I = |U|^2, ln I, W = U / I  -> sW[p][e]
+#pragma unroll
+        for (int s = 0; s < C::TP; ++s) {
+            const int p = 2 * tp + (s & 1) + 32 * (s >> 1);
+            const bool pv = p0 + p < P;
+            float lpart = 0.f;
+#pragma unroll
+            for (int r = 0; r < C::TE; r += 2) {
+                const int e = 2 * te + 32 * (r >> 1);
+                float w[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float ur = u[r + h][s][0], ui = u[r + h][s][1];
+                    const float I = ur * ur + ui * ui;
+                    float wr = 0.f, wi = 0.f;
+                    if (pv && e0 + e + h < e_end) {
+                        if (intensity_ok(I)) {
+                            lpart += logf(I);
+                            const float rc = 1.f / I;
+                            wr = ur * rc;
+                            wi = ui * rc;
+                        } else {
+                            sBad[p] = 1;
+                        }
+                    }
+                    w[2 * h] = wr;
+                    w[2 * h + 1] = wi;
+                }
+                *reinterpret_cast<float4*>(sW + p * C::EW + e) = make_float4(w[0], w[1], w[2], w[3]);
+            }
+            lsum[s] = ff_add_f(lsum[s], lpart);
+        }
+        __syncthreads();
+        // ---- GEMM2: G[a][p] += sum_e conj(A[a][e]) W[p][e]
+        if (with_grad) {
+#pragma unroll 4
+            for (int e = 0; e < E; e += 2) {
+                float4 av[C::KA], wv[C::PP];
+#pragma unroll
+                for (int k = 0; k < C::KA; ++k) av[k] = *reinterpret_cast<const float4*>(sA + (ta + C::TA * k) * C::EA + e);
+#pragma unroll
+                for (int s = 0; s < C::PP; ++s) wv[s] = *reinterpret_cast<const float4*>(sW + (tg + C::TPG * s) * C::EW + e);
+#pragma unroll
+                for (int k = 0; k < C::KA; ++k)
+#pragma unroll
+                    for (int s = 0; s < C::PP; ++s) {
+                        gacc[k][s][0] += av[k].x * wv[s].x + av[k].y * wv[s].y + av[k].z * wv[s].z + av[k].w * wv[s].w;
+                        gacc[k][s][1] += av[k].x * wv[s].y - av[k].y * wv[s].x + av[k].z * wv[s].w - av[k].w * wv[s].z;
+                    }
+            }
+            if (++since_flush == C::FLUSH) {
+                since_flush = 0;
+                flush_g();
+            }
+        }
+    }
+    if (with_grad) flush_g();
+    // ln I: reduce the 16 GEMM1 event groups (lanes te = 0..15 of a half warp) per start
+#pragma unroll
+    for (int s = 0; s < C::TP; ++s) {
+        ff v = lsum[s];
+#pragma unroll
+        for (int m = 8; m > 0; m >>= 1) v = ff_add(v, ff_shfl_xor(v, m));
+        if (te == 0) sL[2 * tp + (s & 1) + 32 * (s >> 1)] = v;
+    }
+    __syncthreads();
+    // ---- block result -> part[chunk][p][v]  (v = 0: sum ln I; 1+2a, 2+2a: Re, Im of G[a])
+    const int np = (P - p0) < PB ? (P - p0) : PB;
+    const int NVu = with_grad ? NV : 1;
+    for (int idx = tid; idx < np * NVu; idx += PWA_THREADS) {
+        const int p = idx / NVu, v = idx % NVu;
+        float2 out;
+        if (v == 0) {
+            out = make_float2(sL[p].hi, sL[p].lo);
+        } else {
+            const float4 gv = sG[((v - 1) >> 1) * PB + p];
+            out = ((v - 1) & 1) ? make_float2(gv.z, gv.w) : make_float2(gv.x, gv.y);
+        }
+        part[((int64_t)chunk * P + p0 + p) * NV + v] = out;
+    }
+    for (int p = tid; p < np; p += PWA_THREADS)
+        if (sBad[p]) bad[p0 + p] = 1;
+}
+
+// Per parameter set: sum the chunk partials in chunk order, add the FP64 normalisation term.
+__global__ void __launch_bounds__(PWA_THREADS) k_nll_finalize(
+    const float2* __restrict__ part, int nchunk, int K, int P, const float2* __restrict__ V,
+    const double2* __restrict__ Psi, double nfac, int* __restrict__ bad, int* __restrict__ status,
+    double* __restrict__ nll, double* __restrict__ grad, int with_grad) {
+    __shared__ double sval[1 + 2 * PWA_MAX_WAVES];
+    __shared__ double2 sT[PWA_MAX_WAVES];
+    __shared__ double2 sVd[PWA_MAX_WAVES];
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int NV = 1 + 2 * K;
+    const int NVu = with_grad ? NV : 1;
+    if (tid < K) {
+        const float2 v = V[(int64_t)p * K + tid];
+        sVd[tid] = make_double2(v.x, v.y);
+    }
+    if (tid < NVu) sval[tid] = ff_to_double(ff_sum_strided(part, (int64_t)p * NV + tid, (int64_t)P * NV, nchunk));
+    __syncthreads();
+    if (tid < K) {
+        double tr = 0.0, ti = 0.0;
+        for (int a = 0; a < K; ++a) {
+            const double2 ps = Psi[a * K + tid];
+            tr += ps.x * sVd[a].x - ps.y * sVd[a].y;
+            ti += ps.x * sVd[a].y + ps.y * sVd[a].x;
+        }
+        sT[tid] = make_double2(tr, ti);
+    }
+    __syncthreads();
+    const bool isbad = bad[p] != 0;
+    if (tid == 0) {
+        double S = 0.0;
+        for (int c = 0; c < K; ++c) S += sVd[c].x * sT[c].x + sVd[c].y * sT[c].y;
+        nll[p] = isbad ? INFINITY : (-sval[0] + nfac * S);
+        if (isbad) atomicOr(status, 1);
+    }
+    if (with_grad && tid < K) {
+        grad[(int64_t)p * 2 * K + 2 * tid] = isbad ? 0.0 : (-2.0 * sval[1 + 2 * tid] + 2.0 * nfac * sT[tid].x);
+        grad[(int64_t)p * 2 * K + 2 * tid + 1] = isbad ? 0.0 : (-2.0 * sval[2 + 2 * tid] + 2.0 * nfac * sT[tid].y);
+    }
+    __syncthreads();
+    if (tid == 0) bad[p] = 0;
+}
+
+// ----------------------------------------------------------------------- launch helpers
+int kmax_stream(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64; }
+int kmax_batched(int K) { return K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64; }
+
+template <int KMAX, bool GRAD, bool HOLD>
+int stream_occupancy() {
+    static int occ = -1;
+    if (occ < 0) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nll_stream<KMAX, GRAD, HOLD>, PWA_THREADS, 0);
+        occ = o > 0 ? o : 1;
+    }
+    return occ;
+}
+
+int64_t stream_grid(int64_t n, int sm_count, int occ) {
+    const int64_t npairs = (n + 1) / 2;
+    int64_t g = (npairs + PWA_THREADS - 1) / PWA_THREADS;
+    const int64_t cap = (int64_t)sm_count * occ;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return g;
+}
+
+// Register-holding variant by default for K <= 32; PWA_STREAM_HOLD=0/1 overrides (tuning).
+inline int stream_hold_override() {
+    static int v = -2;
+    if (v == -2) {
+        const char* e = getenv("PWA_STREAM_HOLD");
+        v = e ? atoi(e) : -1;
+    }
+    return v;
+}
+
+template <int KMAX, bool GRAD, bool HOLD>
+cudaError_t stream_launch_v(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                            double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
+                            int* badw, int* status, int sm_count, cudaStream_t st) {
+    const int64_t g = stream_grid(KMAX <= 16 ? n : 2 * n, sm_count, stream_occupancy<KMAX, GRAD, HOLD>());
+    if ((size_t)g * (1 + 2 * (size_t)K) * sizeof(float2) > ws_bytes) return cudaErrorInvalidValue;
+    k_nll_stream<KMAX, GRAD, HOLD><<<(unsigned)g, PWA_THREADS, 0, st>>>(A, K, n, ld, V, Psi, nfac, (float2*)ws,
+                                                                       counter, badw, status, nll, grad);
+    return cudaGetLastError();
+}
+
+template <int KMAX, bool GRAD>
+cudaError_t stream_launch(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                          double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
+                          int* badw, int* status, int sm_count, cudaStream_t st) {
+    const int ov = stream_hold_override();
+    const bool hold = ov >= 0 ? ov != 0 : KMAX <= 32;
+    if (hold)
+        return stream_launch_v<KMAX, GRAD, true>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw,
+                                                 status, sm_count, st);
+    return stream_launch_v<KMAX, GRAD, false>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw,
+                                              status, sm_count, st);
+}
+
+template <bool GRAD>
+cudaError_t stream_dispatch(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                            double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
+                            int* badw, int* status, int sm_count, cudaStream_t st) {
+    switch (kmax_stream(K)) {
+        case 4: return stream_launch<4, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        case 8: return stream_launch<8, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        case 16: return stream_launch<16, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        case 32: return stream_launch<32, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        case 48: return stream_launch<48, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        default: return stream_launch<64, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+    }
+}
+
+// batched tile shapes (E events x PB starts per block tile)
+struct Shape {
+    int E, PB;
+};
+const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}};
+constexpr int kNumShapes = 3;
+
+template <int KMAX, int E, int PB>
+bool shape_feasible() {
+    return BatchedCfg<KMAX, E, PB>::SMEM <= 113 * 1024;
+}
+
+void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int* nchunk, int64_t* ev_per_chunk) {
+    const int ntp = (P + PB - 1) / PB;
+    int64_t target = ((int64_t)sm_count * 2) / ntp;
+    if (target < 1) target = 1;
+    int64_t tiles = (n + E - 1) / E;
+    if (tiles < 1) tiles = 1;
+    if (target > tiles) target = tiles;
+    const int64_t tpc = (tiles + target - 1) / target;
+    *ev_per_chunk = tpc * E;
+    int64_t nc = (n + *ev_per_chunk - 1) / *ev_per_chunk;
+    *nchunk = (int)(nc < 1 ? 1 : nc);
+}
+
+template <int KMAX, int E, int PB>
+cudaError_t batched_launch_shape(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
+                                 size_t ws_bytes, int* bad, int with_grad, int sm_count, cudaStream_t st, int* nchunk_out) {
+    using C = BatchedCfg<KMAX, E, PB>;
+    auto kern = k_nll_batched<KMAX, E, PB>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    int nchunk;
+    int64_t epc;
+    batched_geometry(n, P, PB, E, sm_count, &nchunk, &epc);
+    if ((size_t)nchunk * (size_t)P * (1 + 2 * (size_t)K) * sizeof(float2) > ws_bytes) return cudaErrorInvalidValue;
+    dim3 grid(nchunk, (P + PB - 1) / PB);
+    kern<<<grid, PWA_THREADS, C::SMEM, st>>>(A, K, n, ld, V, P, epc, (float2*)ws, bad, with_grad);
+    *nchunk_out = nchunk;
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+cudaError_t batched_launch(int shape, const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
+                           size_t ws_bytes, int* bad, int with_grad, int sm_count, cudaStream_t st, int* nchunk) {
+    switch (shape) {
+        case 0: return batched_launch_shape<KMAX, 64, 64>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 1: return batched_launch_shape<KMAX, 64, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        default: return batched_launch_shape<KMAX, 128, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+    }
+}
+
+template <int KMAX>
+bool batched_shape_ok(int shape) {
+    switch (shape) {
+        case 0: return shape_feasible<KMAX, 64, 64>();
+        case 1: return shape_feasible<KMAX, 64, 32>();
+        default: return shape_feasible<KMAX, 128, 32>();
+    }
+}
+
+bool shape_ok(int kmax, int shape) {
+    switch (kmax) {
+        case 8: return batched_shape_ok<8>(shape);
+        case 16: return batched_shape_ok<16>(shape);
+        case 32: return batched_shape_ok<32>(shape);
+        case 48: return batched_shape_ok<48>(shape);
+        default: return batched_shape_ok<64>(shape);
+    }
+}
+
+cudaError_t batched_dispatch(int shape, const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
+                             void* ws, size_t ws_bytes, int* bad, int with_grad, int sm_count, cudaStream_t st, int* nchunk) {
+    switch (kmax_batched(K)) {
+        case 8: return batched_launch<8>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 16: return batched_launch<16>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 32: return batched_launch<32>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 48: return batched_launch<48>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        default: return batched_launch<64>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+    }
+}
+
+// ---- autotuner: per (KMAX, P bucket, n bucket) time every feasible shape once, keep the fastest
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+int bucket_log2(int64_t x) {
+    int b = 0;
+    while (x > 1) { x >>= 1; ++b; }
+    return b;
+}
+
+int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const float2* V, void* ws, size_t ws_bytes, int* bad,
+                 int with_grad, int sm_count, cudaStream_t st) {
+    const int kmax = kmax_batched(K);
+    const char* env = getenv("PWA_BATCHED_SHAPE");
+    if (env) {
+        int s = atoi(env);
+        if (s >= 0 && s < kNumShapes && shape_ok(kmax, s)) return s;
+    }
+    const auto key = std::make_tuple(kmax, bucket_log2(P), bucket_log2(n));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    int fallback = shape_ok(kmax, 0) ? 0 : 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    const char* tune = getenv("PWA_TUNE");
+    if (cs != cudaStreamCaptureStatusNone || (tune && tune[0] == '0') || n < 4096) return fallback;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = fallback;
+    float best_ms = 1e30f;
+    for (int s = 0; s < kNumShapes; ++s) {
+        if (!shape_ok(kmax, s)) continue;
+        int nc;
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, st);
+            ok = batched_dispatch(s, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, &nc) == cudaSuccess;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;  // first launch is a warm-up
+        }
+        if (ok && tot < best_ms) {
+            best_ms = tot;
+            best = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // clear the non-finite flags the trial launches may have set
+    cudaMemsetAsync(bad, 0, sizeof(int) * (size_t)P, st);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
+}
+
+}  // namespace
+
+size_t nll_workspace(int K, int64_t n, int P, int sm_count) {
+    const size_t NV = 1 + 2 * (size_t)K;
+    if (P == 1) return sizeof(float2) * NV * (size_t)sm_count * 8;
+    // batched: the (E = 64, PB = 64) geometry has the most chunks of all shapes
+    int nchunk;
+    int64_t epc;
+    batched_geometry(n, P, 64, 64, sm_count, &nchunk, &epc);
+    return sizeof(float2) * NV * (size_t)P * (size_t)nchunk;
+}
+
+cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
+                       const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st) {
+    if (P == 1) {
+        // counter[0]: completion ticket, counter[1]: non-finite flag of this evaluation
+        int* badw = reinterpret_cast<int*>(counter + 1);
+        if (grad)
+            return stream_dispatch<true>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status, sm_count, st);
+        return stream_dispatch<false>(A, K, n, ld, V, Psi, nfac, nll, nullptr, ws, ws_bytes, counter, badw, status, sm_count, st);
+    }
+    const int with_grad = grad != nullptr;
+    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, with_grad, sm_count, st);
+    int nchunk = 1;
+    cudaError_t e = batched_dispatch(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, &nchunk);
+    if (e != cudaSuccess) return e;
+    k_nll_finalize<<<P, PWA_THREADS, 0, st>>>((const float2*)ws, nchunk, K, P, V, Psi, nfac, bad, status, nll, grad,
+                                              with_grad);
+    return cudaGetLastError();
+}
+
+}  // namespace pwa

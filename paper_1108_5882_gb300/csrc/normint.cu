@@ -1,0 +1,235 @@
+// Monte-Carlo normalisation integral Psi_ab = (1/N_gen) sum_j w_j A_a(j) conj(A_b(j)).
+//
+// Paper: Sec. 2, Eq. 3 (inner bracket of the second term: sum over accepted MC events divided
+// by the number generated; footnote 1 for weighted, non-uniform MC).  With masses and widths
+// fixed the bracket is computed once per fit (Sec. 2).
+//
+// This is a Hermitian rank-N update Psi = A diag(w) A^H / N_gen with K <= 64 and N ~ 1e7,
+// so the work is a reduction over events, not a GEMM with reuse in the output: the kernel
+// streams event tiles of E = 64 events through shared memory and gives each thread a 4 x 4
+// block of the upper triangle of Psi and an event phase.  Per event a thread issues 8 shared
+// loads for 16 complex multiply-adds (64 FFMA).
+//
+// Accumulation: FP32 per thread over a window of at most ~32 events, then folded into a
+// per-thread double-single accumulator held in shared memory (v-major, conflict-free); the
+// phases and then the blocks are combined in a fixed order, and the final division and the
+// Hermitian completion are done in FP64.
+#include "pwa_internal.cuh"
+
+namespace pwa {
+
+namespace {
+
+constexpr int NI_E = 64;  // events per tile
+
+struct NiShape {
+    int KB;      // 4x4 tile rows
+    int NT;      // upper-triangle tiles
+    int nph;     // event phases per block
+    int flush;   // tiles between flushes
+};
+
+__host__ __device__ inline NiShape ni_shape(int KMAX) {
+    NiShape s;
+    s.KB = KMAX / 4;
+    s.NT = s.KB * (s.KB + 1) / 2;
+    s.nph = PWA_THREADS / s.NT;
+    if (s.nph < 1) s.nph = 1;
+    int ev_per_tile = (NI_E + s.nph - 1) / s.nph;
+    s.flush = (32 + ev_per_tile - 1) / ev_per_tile;
+    return s;
+}
+
+// block partial layout: part[block][KMAX*KMAX] of complex ff = 4 floats (re.hi, re.lo, im.hi, im.lo)
+template <int KMAX, bool WEIGHTED>
+__global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restrict__ A, int K, int64_t n,
+                                                         int64_t ld, const float* __restrict__ w,
+                                                         int64_t ev_per_block, float4* __restrict__ part) {
+    constexpr NiShape S = {KMAX / 4, (KMAX / 4) * (KMAX / 4 + 1) / 2,
+                           (PWA_THREADS / ((KMAX / 4) * (KMAX / 4 + 1) / 2)) > 0
+                               ? PWA_THREADS / ((KMAX / 4) * (KMAX / 4 + 1) / 2)
+                               : 1,
+                           0};
+    constexpr int NT = S.NT;
+    constexpr int NPH = S.nph;
+    constexpr int EPT = (NI_E + NPH - 1) / NPH;
+    constexpr int FLUSH = (32 + EPT - 1) / EPT;
+    extern __shared__ float4 smem4[];
+    float2* sA = reinterpret_cast<float2*>(smem4);  // [KMAX][NI_E + 1]
+    float* sw = reinterpret_cast<float*>(sA + KMAX * (NI_E + 1));  // [NI_E]
+    float* sacc = sw + NI_E;  // [64][PWA_THREADS]: 16 complex ff per thread, v-major
+
+    const int tid = threadIdx.x;
+    const bool active = tid < NT * NPH;
+    const int t = tid % NT;
+    const int ph = tid / NT;
+    // tile t -> (ti, tj) with ti <= tj, row-major over the upper triangle
+    int ti = 0, tj = 0;
+    {
+        int r = t, row = 0, len = S.KB;
+        while (r >= len) { r -= len; ++row; --len; }
+        ti = row;
+        tj = row + r;
+    }
+    for (int v = 0; v < 64; ++v) sacc[v * PWA_THREADS + tid] = 0.f;
+
+    const int64_t e_begin = (int64_t)blockIdx.x * ev_per_block;
+    int64_t e_end = e_begin + ev_per_block;
+    if (e_end > n) e_end = n;
+
+    float acc[32];
+#pragma unroll
+    for (int v = 0; v < 32; ++v) acc[v] = 0.f;
+    int since_flush = 0;
+
+    for (int64_t e0 = e_begin; e0 < e_end; e0 += NI_E) {
+        __syncthreads();
+        // stage the tile: KMAX rows x 64 events (float2), zero beyond n or K
+        for (int idx = tid; idx < KMAX * NI_E; idx += PWA_THREADS) {
+            const int a = idx / NI_E, e = idx % NI_E;
+            float2 v = make_float2(0.f, 0.f);
+            if (a < K && e0 + e < e_end) v = __ldg(A + a * ld + e0 + e);
+            sA[a * (NI_E + 1) + e] = v;
+        }
+        if (WEIGHTED)
+            for (int e = tid; e < NI_E; e += PWA_THREADS) sw[e] = (e0 + e < e_end) ? __ldg(w + e0 + e) : 0.f;
+        __syncthreads();
+        if (active) {
+            for (int e = ph; e < NI_E; e += NPH) {
+                float2 xa[4], xb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    xa[r] = sA[(4 * ti + r) * (NI_E + 1) + e];
+                    xb[r] = sA[(4 * tj + r) * (NI_E + 1) + e];
+                }
+                if (WEIGHTED) {
+                    const float we = sw[e];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) { xa[r].x *= we; xa[r].y *= we; }
+                }
+                // acc[(r*4+c)*2 + {0,1}] += xa[r] * conj(xb[c])
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        acc[(r * 4 + c) * 2 + 0] += xa[r].x * xb[c].x + xa[r].y * xb[c].y;
+                        acc[(r * 4 + c) * 2 + 1] += xa[r].y * xb[c].x - xa[r].x * xb[c].y;
+                    }
+            }
+        }
+        if (++since_flush == FLUSH) {
+            since_flush = 0;
+#pragma unroll
+            for (int v = 0; v < 32; ++v) {
+                ff a = {sacc[(2 * v) * PWA_THREADS + tid], sacc[(2 * v + 1) * PWA_THREADS + tid]};
+                a = ff_add_f(a, acc[v]);
+                sacc[(2 * v) * PWA_THREADS + tid] = a.hi;
+                sacc[(2 * v + 1) * PWA_THREADS + tid] = a.lo;
+                acc[v] = 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 32; ++v) {
+        ff a = {sacc[(2 * v) * PWA_THREADS + tid], sacc[(2 * v + 1) * PWA_THREADS + tid]};
+        a = ff_add_f(a, acc[v]);
+        sacc[(2 * v) * PWA_THREADS + tid] = a.hi;
+        sacc[(2 * v + 1) * PWA_THREADS + tid] = a.lo;
+    }
+    __syncthreads();
+    // combine the phases of each tile in order and write the block partial (upper tiles only;
+    // lower tiles of the KMAX x KMAX partial are left unwritten and never read)
+    float4* bp = part + (int64_t)blockIdx.x * KMAX * KMAX;
+    for (int o = tid; o < NT * 16; o += PWA_THREADS) {
+        const int tt = o / 16, q = o % 16;
+        ff re = ff_zero(), im = ff_zero();
+        for (int p = 0; p < NPH; ++p) {
+            const int th = p * NT + tt;
+            re = ff_add(re, ff{sacc[(4 * q) * PWA_THREADS + th], sacc[(4 * q + 1) * PWA_THREADS + th]});
+            im = ff_add(im, ff{sacc[(4 * q + 2) * PWA_THREADS + th], sacc[(4 * q + 3) * PWA_THREADS + th]});
+        }
+        int r2 = tt, row = 0, len = S.KB;
+        while (r2 >= len) { r2 -= len; ++row; --len; }
+        const int a = 4 * row + q / 4, b = 4 * (row + r2) + q % 4;
+        bp[a * KMAX + b] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+
+// Sum the block partials in block order and finalise Psi in FP64 (full Hermitian matrix).
+template <int KMAX>
+__global__ void __launch_bounds__(PWA_THREADS) k_normint_final(const float4* __restrict__ part, int nblocks,
+                                                               int K, double inv_ngen, double2* __restrict__ Psi) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < K * K; o += gridDim.x * blockDim.x) {
+        const int a = o / K, b = o % K;
+        if (a > b) continue;
+        // block partials in block order, 16 independent loads in flight
+        ff re = ff_zero(), im = ff_zero();
+        for (int b0 = 0; b0 < nblocks; b0 += 16) {
+            float4 v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                v[j] = (b0 + j < nblocks) ? part[(int64_t)(b0 + j) * KMAX * KMAX + a * KMAX + b]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                re = ff_add(re, ff{v[j].x, v[j].y});
+                im = ff_add(im, ff{v[j].z, v[j].w});
+            }
+        }
+        const double r = ff_to_double(re) * inv_ngen, i = ff_to_double(im) * inv_ngen;
+        Psi[a * K + b] = make_double2(r, a == b ? 0.0 : i);
+        if (a != b) Psi[b * K + a] = make_double2(r, -i);
+    }
+}
+
+template <int KMAX>
+size_t ni_smem() {
+    return sizeof(float2) * KMAX * (NI_E + 1) + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
+}
+
+template <int KMAX>
+cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float* w, double n_gen,
+                      double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+    const size_t smem = ni_smem<KMAX>();
+    auto kw = k_normint<KMAX, true>;
+    auto ku = k_normint<KMAX, false>;
+    cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t tiles = (n + NI_E - 1) / NI_E;
+    int64_t nb = (int64_t)sm_count * 2;
+    if (nb > tiles) nb = tiles;
+    if (nb < 1) nb = 1;
+    const int64_t tiles_per_block = (tiles + nb - 1) / nb;
+    const int64_t ev_per_block = tiles_per_block * NI_E;
+    nb = ev_per_block > 0 ? (n + ev_per_block - 1) / ev_per_block : 1;
+    if (nb < 1) nb = 1;
+    float4* part = reinterpret_cast<float4*>(ws);
+    if (w)
+        kw<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, w, ev_per_block, part);
+    else
+        ku<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, nullptr, ev_per_block, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_normint_final<KMAX><<<(K * K + PWA_THREADS - 1) / PWA_THREADS, PWA_THREADS, 0, st>>>(part, (int)nb, K,
+                                                                                       1.0 / n_gen, Psi);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t normint_workspace(int K, int sm_count) {
+    int KMAX = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64;
+    return sizeof(float4) * (size_t)KMAX * KMAX * (size_t)sm_count * 2;
+}
+
+cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const float* w,
+                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+    if (K <= 4) return ni_launch<4>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+    if (K <= 8) return ni_launch<8>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+    if (K <= 16) return ni_launch<16>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+    if (K <= 32) return ni_launch<32>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+    if (K <= 48) return ni_launch<48>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+    return ni_launch<64>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
+}
+
+}  // namespace pwa

@@ -1,0 +1,144 @@
+// Internal declarations shared by the translation units of libpwa.so (not installed).
+//
+// Numerics used throughout: per-event arithmetic in FP32 (the paper's Sec. 2 precision
+// remark: single precision suffices for the individual amplitude), per-thread FP32
+// accumulation over a bounded window of events, and every longer sum carried as a
+// double-single ("ff") pair (hi + lo, Knuth's TwoSum and Dekker's Fast2Sum), combined across
+// warps and blocks in a fixed order so results are bitwise reproducible.  FP64 is used only
+// for the O(K^2) normalisation term: GB300 runs FP64 at a small fraction of its FP32 rate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/pwa.h"
+
+#define PWA_THREADS 256
+
+struct pwa_handle {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    void* ws = nullptr;          // workspace: block partials
+    size_t ws_bytes = 0;
+    unsigned* counters = nullptr;  // completion counters (zero between calls)
+    int* status = nullptr;         // sticky device status word (bit 0: non-finite intensity)
+    int* bad = nullptr;            // per-parameter-set non-finite flags [bad_cap]
+    int bad_cap = 0;
+};
+
+namespace pwa {
+
+// ---------------------------------------------------------------- double-single sums ----
+struct ff {
+    float hi, lo;
+};
+
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+    return {s, e};
+}
+// Fast2Sum (Dekker), valid for |a| >= |b|.
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    float e = __fadd_rn(s.lo, a.lo);
+    return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_zero() { return {0.f, 0.f}; }
+__device__ __forceinline__ ff ff_shfl_xor(ff a, int m) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+// ---------------------------------------------------------------- warp reductions -------
+// Reduce-scatter of 32 per-lane values across the warp: on return x[0] of lane l holds the
+// warp-wide sum of value l.  31 shuffles instead of 32 x 5 for a butterfly per value.  Each
+// level halves the live values: lanes with bit LVL set keep the upper half and send the lower.
+template <int LVL>
+__device__ __forceinline__ void transpose_reduce_level(float (&x)[32], int lane) {
+    constexpr int HALF = 1 << LVL;
+    const bool upper = (lane >> LVL) & 1;
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+        const float lo = x[j], hi = x[j + HALF];
+        const float send = upper ? lo : hi;
+        const float keep = upper ? hi : lo;
+        x[j] = keep + __shfl_xor_sync(0xffffffffu, send, HALF);
+    }
+    if constexpr (LVL > 0) transpose_reduce_level<LVL - 1>(x, lane);
+}
+__device__ __forceinline__ void warp_transpose_reduce32(float (&x)[32]) {
+    transpose_reduce_level<4>(x, threadIdx.x & 31);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// Fixed-order double-single sum of x[first], x[first + step], ... (count terms) with UNR
+// independent loads in flight per batch (the partials live in L2: a dependent load chain
+// would cost one L2 round trip per term).  Loads bypass L1 (written by other blocks).
+template <int UNR = 16>
+__device__ __forceinline__ ff ff_sum_strided(const float2* __restrict__ x, int64_t first, int64_t step, int count) {
+    ff s = ff_zero();
+    for (int j0 = 0; j0 < count; j0 += UNR) {
+        float2 v[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) v[j] = (j0 + j < count) ? __ldcg(x + first + (int64_t)(j0 + j) * step) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) s = ff_add(s, ff{v[j].x, v[j].y});
+    }
+    return s;
+}
+
+// Non-finite or non-positive intensity test (the likelihood needs ln I_i).
+__device__ __forceinline__ bool intensity_ok(float I) { return I > 0.f && I < INFINITY; }
+
+// ---------------------------------------------------------------- launchers --------------
+// All launchers validate nothing: the C ABI layer has done it.  They return the CUDA launch
+// error (cudaSuccess on success).
+struct WaveTable {
+    int K;
+    int J[PWA_MAX_WAVES];
+    int lam[PWA_MAX_WAVES];
+    float Mhi[PWA_MAX_WAVES], Mlo[PWA_MAX_WAVES];
+    float W[PWA_MAX_WAVES];
+    float MW[PWA_MAX_WAVES];
+};
+
+cudaError_t launch_amplitudes(const WaveTable& wt, const float* kin, int64_t n, int64_t ld,
+                              float2* A, float2* dAdM, float2* dAdW, int sm_count,
+                              cudaStream_t st);
+
+size_t normint_workspace(int K, int sm_count);
+cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const float* w,
+                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st);
+
+size_t nll_workspace(int K, int64_t n, int P, int sm_count);
+cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
+                       const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
+
+size_t generate_workspace(int64_t n_cand);
+cudaError_t launch_generate(const WaveTable& wt, const float2* V, uint64_t seed, uint32_t stream, int64_t cand0,
+                            int64_t n_cand, double envelope, float* kin, int64_t ld_out, int64_t max_out,
+                            long long* n_acc, void* ws, cudaStream_t st);
+
+}  // namespace pwa

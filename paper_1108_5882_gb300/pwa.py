@@ -1,0 +1,248 @@
+"""Thin Python binding of libpwa.so: the C ABI of include/pwa.h with the same names.
+
+Only argument marshalling happens here (torch tensors -> device pointers, the current CUDA
+stream -> void*); every step of the computation runs in the library's CUDA kernels.  There is
+no fallback: if libpwa.so is missing or no GPU is visible the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpwa.so")
+
+PWA_OK = 0
+PWA_ERR_INVALID_ARG = -1
+PWA_ERR_NO_DEVICE = -2
+PWA_ERR_CUDA = -3
+PWA_ERR_NONFINITE = -4
+PWA_ERR_TIMEOUT = -5
+PWA_ERR_WORKSPACE = -6
+PWA_NOT_CONVERGED = 1
+
+
+class PWAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class pwa_wave(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int), ("lambda_", ctypes.c_int), ("mass", ctypes.c_double),
+                ("width", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libpwa.so (built by paper_1108_5882_gb300.build).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libpwa.so not built ({p}); run paper_1108_5882_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        S = ctypes.c_int
+        lib.pwa_abi_version.restype = ctypes.c_int
+        lib.pwa_status_string.argtypes = [ctypes.c_int]
+        lib.pwa_status_string.restype = ctypes.c_char_p
+        lib.pwa_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        lib.pwa_create.restype = S
+        lib.pwa_destroy.argtypes = [_vp]
+        lib.pwa_destroy.restype = None
+        lib.pwa_last_error.argtypes = [_vp]
+        lib.pwa_last_error.restype = ctypes.c_char_p
+        lib.pwa_workspace_size.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int]
+        lib.pwa_workspace_size.restype = ctypes.c_size_t
+        lib.pwa_reserve.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int]
+        lib.pwa_reserve.restype = S
+        lib.pwa_sync_status.argtypes = [_vp, _vp]
+        lib.pwa_sync_status.restype = S
+        lib.pwa_amplitudes.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, _i64, _i64, _vp, _vp,
+                                       _vp, _vp]
+        lib.pwa_amplitudes.restype = S
+        lib.pwa_normint.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_double, _vp, _vp]
+        lib.pwa_normint.restype = S
+        lib.pwa_nll.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int, _vp, ctypes.c_double, _vp,
+                                _vp]
+        lib.pwa_nll.restype = S
+        lib.pwa_nll_grad.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int, _vp,
+                                     ctypes.c_double, _vp, _vp, _vp]
+        lib.pwa_nll_grad.restype = S
+        _register_optional(lib)
+        _lib = lib
+        return lib
+
+
+def _register_optional(lib):
+    """Entry points added after the first ABI version (bound when present)."""
+    S = ctypes.c_int
+    lib.pwa_envelope.argtypes = [ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int]
+    lib.pwa_envelope.restype = ctypes.c_double
+    if hasattr(lib, "pwa_generate"):
+        lib.pwa_generate.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_uint64,
+                                     ctypes.c_uint32, _i64, _i64, ctypes.c_double, _vp, _i64, _i64, _vp, _vp]
+        lib.pwa_generate.restype = S
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().pwa_status_string(int(s)).decode()
+    except ImportError:
+        return f"status {s}"
+
+
+def _stream_ptr(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_cuda(t, name, dtype):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Handle:
+    """Owns a pwa_handle (device workspace, status word) bound to one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = load()
+        if device is None:
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.pwa_create(ctypes.byref(h), int(device))
+        if st != PWA_OK:
+            raise PWAError(st, self.lib.pwa_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pwa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != PWA_OK:
+            raise PWAError(st, self.lib.pwa_last_error(self.h).decode())
+
+    # ------------------------------------------------------------------ entry points
+    def pwa_workspace_size(self, K, n, P):
+        return int(self.lib.pwa_workspace_size(self.h, int(K), int(n), int(P)))
+
+    def pwa_reserve(self, K, n, P):
+        self._chk(self.lib.pwa_reserve(self.h, int(K), int(n), int(P)))
+
+    def pwa_sync_status(self, stream=None):
+        return int(self.lib.pwa_sync_status(self.h, _stream_ptr(stream)))
+
+    def pwa_amplitudes(self, waves, kin, n, A, dA_dM=None, dA_dW=None, stream=None):
+        """waves: list of (J, lambda, mass, width); kin float32 [3][ld]; A complex64 [K][ld]."""
+        K = len(waves)
+        arr = (pwa_wave * K)(*[pwa_wave(int(j), int(l), float(m), float(w)) for (j, l, m, w) in waves])
+        _check_cuda(kin, "kin", torch.float32)
+        _check_cuda(A, "A", torch.complex64)
+        _check_cuda(dA_dM, "dA_dM", torch.complex64)
+        _check_cuda(dA_dW, "dA_dW", torch.complex64)
+        ld = A.shape[1]
+        if kin.shape[1] != ld:
+            raise ValueError("kin and A must share the leading dimension")
+        self._chk(self.lib.pwa_amplitudes(self.h, arr, K, _ptr(kin), int(n), int(ld), _ptr(A), _ptr(dA_dM),
+                                          _ptr(dA_dW), _stream_ptr(stream)))
+
+    def pwa_normint(self, A_mc, n_mc, Psi, w=None, n_gen=None, stream=None):
+        """A_mc complex64 [K][ld]; Psi complex128 [K][K] output; w float32 [n_mc] or None."""
+        _check_cuda(A_mc, "A_mc", torch.complex64)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(w, "w", torch.float32)
+        K, ld = A_mc.shape
+        n_gen = float(n_mc if n_gen is None else n_gen)
+        self._chk(self.lib.pwa_normint(self.h, _ptr(A_mc), K, int(n_mc), int(ld), _ptr(w), n_gen, _ptr(Psi),
+                                       _stream_ptr(stream)))
+
+    def pwa_nll(self, A, n, V, Psi, n_factor, nll, stream=None):
+        _check_cuda(A, "A", torch.complex64)
+        _check_cuda(V, "V", torch.complex64)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(nll, "nll", torch.float64)
+        K, ld = A.shape
+        P = V.shape[0]
+        self._chk(self.lib.pwa_nll(self.h, _ptr(A), K, int(n), int(ld), _ptr(V), P, _ptr(Psi), float(n_factor),
+                                   _ptr(nll), _stream_ptr(stream)))
+
+    def pwa_nll_grad(self, A, n, V, Psi, n_factor, nll, grad, stream=None):
+        """A complex64 [K][ld], V complex64 [P][K], Psi complex128 [K][K];
+        nll float64 [P], grad float64 [P][2K] outputs."""
+        _check_cuda(A, "A", torch.complex64)
+        _check_cuda(V, "V", torch.complex64)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(nll, "nll", torch.float64)
+        _check_cuda(grad, "grad", torch.float64)
+        K, ld = A.shape
+        P = V.shape[0]
+        self._chk(self.lib.pwa_nll_grad(self.h, _ptr(A), K, int(n), int(ld), _ptr(V), P, _ptr(Psi),
+                                        float(n_factor), _ptr(nll), _ptr(grad), _stream_ptr(stream)))
+
+
+def _wave_array(waves):
+    K = len(waves)
+    return (pwa_wave * K)(*[pwa_wave(int(j), int(l), float(m), float(w)) for (j, l, m, w) in waves])
+
+
+def pwa_envelope(waves, V, m_lo=0.99, m_hi=3.0, n_intervals=4096) -> float:
+    """Host bound C >= max I over the phase space; V: complex64 array-like [K] on the host."""
+    import numpy as np
+    lib = load()
+    Vh = np.ascontiguousarray(np.asarray(V, dtype=np.complex64)).view(np.float32)
+    c = lib.pwa_envelope(_wave_array(waves), len(waves), Vh.ctypes.data_as(ctypes.c_void_p), float(m_lo),
+                         float(m_hi), int(n_intervals))
+    if c < 0:
+        raise ValueError("pwa_envelope: invalid arguments")
+    return float(c)
+
+
+def _gen(self, waves, V, seed, stream_id, cand0, n_cand, envelope, kin, max_out, n_acc, stream=None):
+    """kin float32 [3][ld_out] output; n_acc int64 [1] device output."""
+    _check_cuda(V, "V", torch.complex64)
+    _check_cuda(kin, "kin", torch.float32)
+    _check_cuda(n_acc, "n_accepted", torch.int64)
+    self._chk(self.lib.pwa_generate(self.h, _wave_array(waves), len(waves), _ptr(V), int(seed), int(stream_id),
+                                    int(cand0), int(n_cand), float(envelope), _ptr(kin), int(kin.shape[1]),
+                                    int(max_out), _ptr(n_acc), _stream_ptr(stream)))
+
+
+Handle.pwa_generate = _gen
+
+
+def waves_from(ws) -> list[tuple[int, int, float, float]]:
+    """inputs.WaveSet -> list of (J, lambda, mass, width)."""
+    return [(int(ws.J[a]), int(ws.lam[a]), float(ws.M[a]), float(ws.W[a])) for a in range(ws.K)]

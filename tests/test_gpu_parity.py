@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (the reading of the benchmark spec's bounds, with condition-aware denominators):
+  -lnL:        |f_gpu - f_ref| <= 1e-5 * max(|f_ref|, sum_i |ln I_i|, n |S|)
+  gradient:    |g_gpu - g_ref| <= 1e-4 * (2 sum_i |A_ic||u_i|/I_i + 2 n sum_a |Psi_ac||V_a|)
+               per real component
+  amplitudes:  |A_gpu - A_ref| <= 4e-6 (|A| <= 1: unit-peak Breit-Wigner, |P_J| <= 1)
+  dA/dM, dA/dG: per wave |err| <= 2e-5 * max_i |dA_ref|
+  Psi:         |Psi_gpu - Psi_ref|_ab <= 1e-5 * sqrt(Psi_aa Psi_bb)
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1108_5882_gb300 import inputs
+from problems import make_problem, padded
+
+pytestmark = pytest.mark.gpu
+
+SEED = inputs.SEED_BASE
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_1108_5882_gb300 import build, pwa
+    build.build()
+    return pwa.Handle(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_nll_grad(h, A, n, V, Psi, n_factor=None, grad=True):
+    from paper_1108_5882_gb300 import pwa  # noqa: F401
+    K, ld = A.shape
+    P = V.shape[0]
+    n_factor = float(n if n_factor is None else n_factor)
+    nll = torch.zeros(P, dtype=torch.float64, device="cuda")
+    g = torch.zeros(P, 2 * K, dtype=torch.float64, device="cuda")
+    if grad:
+        h.pwa_nll_grad(dev(A), n, dev(V), dev(Psi), n_factor, nll, g)
+    else:
+        h.pwa_nll(dev(A), n, dev(V), dev(Psi), n_factor, nll)
+    torch.cuda.synchronize()
+    return nll.cpu().numpy(), g.cpu().numpy()
+
+
+def check_nll(f_gpu, g_gpu, A, V, Psi, n_factor=None, check_grad=True):
+    f_ref, g_ref, cf, cg, bad = oracle.nll_grad(A, V, Psi, n_factor=n_factor, with_cond=True)
+    assert bad == 0
+    err_f = np.abs(f_gpu - f_ref) / cf
+    assert np.all(err_f <= 1e-5), (err_f.max(), f_gpu, f_ref)
+    if check_grad:
+        scale = np.repeat(cg, 2, axis=1)
+        err_g = np.abs(g_gpu - g_ref) / scale
+        assert np.all(err_g <= 1e-4), err_g.max()
+    return f_ref, g_ref
+
+
+# ------------------------------------------------------------------- amplitudes ---------
+
+@pytest.mark.parametrize("K,n,ld", [(4, 10_000, 10_000), (16, 4099, 4352), (7, 1, 2), (48, 3001, 3002)])
+def test_amplitudes_parity(h, K, n, ld):
+    ws = inputs.wave_set_plain(SEED + 1) if K == 4 else inputs.wave_set_spread(K, SEED + K)
+    kin = inputs.kinematics(n, SEED + K, 6)
+    from paper_1108_5882_gb300 import pwa
+    A = torch.full((K, ld), complex(7, 7), dtype=torch.complex64, device="cuda")
+    dM = torch.zeros((K, ld), dtype=torch.complex64, device="cuda")
+    dW = torch.zeros((K, ld), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(pwa.waves_from(ws), dev(padded(kin, ld)), n, A, dM, dW)
+    Ag, dMg, dWg = (x.cpu().numpy() for x in (A, dM, dW))
+    Ar, dMr, dWr = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin, derivs=True)
+    assert np.max(np.abs(Ag[:, :n] - Ar)) <= 4e-6
+    assert np.all(Ag[:, n:] == 0)  # padding columns zeroed
+    for a in range(K):
+        assert np.max(np.abs(dMg[a, :n] - dMr[a])) <= 2e-5 * np.max(np.abs(dMr[a]))
+        assert np.max(np.abs(dWg[a, :n] - dWr[a])) <= 2e-5 * np.max(np.abs(dWr[a]))
+
+
+def test_amplitudes_peak_and_all_spins(h):
+    # every (J, lambda) the kernel supports, at the resonance peak and elsewhere
+    from paper_1108_5882_gb300 import pwa
+    waves = [(J, lam, 1.0 + 0.1 * J + 0.01 * (lam + 8), 0.05 + 0.01 * J) for J in range(9) for lam in (-8, -3, 0, 1, 8)]
+    waves = waves[:64]
+    K = len(waves)
+    n = 2048
+    kin = inputs.kinematics(n, SEED, 8)
+    A = torch.zeros((K, n), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(waves, dev(kin), n, A)
+    J = [w[0] for w in waves]
+    lam = [w[1] for w in waves]
+    M = [w[2] for w in waves]
+    W = [w[3] for w in waves]
+    Ar = oracle.amplitudes(J, lam, M, W, kin)
+    assert np.max(np.abs(A.cpu().numpy() - Ar)) <= 4e-6
+
+
+# ------------------------------------------------------------------- normalisation ------
+
+@pytest.mark.parametrize("K,n_mc,weighted", [(4, 50_000, False), (16, 30_001, False), (32, 9_999, True),
+                                             (5, 1, False), (48, 7_000, True), (64, 3_000, False)])
+def test_normint_parity(h, K, n_mc, weighted):
+    g = np.random.default_rng(K + n_mc)
+    A = (g.normal(size=(K, n_mc)) + 1j * g.normal(size=(K, n_mc))).astype(np.complex64)
+    ld = n_mc + (n_mc % 2) + 2
+    w = g.uniform(0, 2, n_mc).astype(np.float32) if weighted else None
+    if weighted:
+        w[::7] = 0.0
+    Psi = torch.zeros((K, K), dtype=torch.complex128, device="cuda")
+    h.pwa_normint(dev(padded(A, ld, fill=np.complex64(np.nan))), n_mc, Psi, w=None if w is None else dev(w),
+                  n_gen=1.5 * n_mc)
+    ref = oracle.normint(A, w, n_gen=1.5 * n_mc)
+    got = Psi.cpu().numpy()
+    d = np.sqrt(np.outer(np.diag(ref).real, np.diag(ref).real))
+    assert np.all(np.abs(got - ref) <= 1e-5 * d + 1e-300)
+    assert np.array_equal(got, got.conj().T)
+
+
+def test_normint_on_amplitudes_of_the_plain_workload(h):
+    p = make_problem(4, 100, 50_000, SEED + 1, accept_reject=False, plain=True)
+    Psi = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
+    h.pwa_normint(dev(p.A_mc), p.A_mc.shape[1], Psi)
+    d = np.sqrt(np.outer(np.diag(p.Psi).real, np.diag(p.Psi).real))
+    assert np.all(np.abs(Psi.cpu().numpy() - p.Psi) <= 1e-5 * d)
+
+
+# ------------------------------------------------------------------- likelihood ---------
+
+@pytest.mark.parametrize("K", [1, 3, 4, 8, 13, 16, 24, 32, 48, 64])
+def test_nll_grad_single_set(h, K):
+    # several tiles of the stream kernel plus a ragged (odd) tail
+    n = 20_001
+    p = make_problem(K, n, 4 * n, SEED + 100 + K, accept_reject=(K <= 16))
+    V = p.V_true[None, :]
+    ld = n + 1
+    f, g = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi)
+    check_nll(f, g, p.A, V, p.Psi)
+    f2, _ = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi, grad=False)
+    assert f2[0] == f[0] or abs(f2[0] - f[0]) <= 1e-12 * abs(f[0])
+
+
+def test_plain_workload_at_random_starts(h):
+    # plain workload: K=4, N_data=1e4, N_MC=5e4, data by accept-reject, one set per launch
+    p = make_problem(4, 10_000, 50_000, SEED + 1, plain=True)
+    for V in inputs.starts(8, 4, SEED + 1):
+        f, g = gpu_nll_grad(h, p.A, p.n, V[None, :], p.Psi)
+        check_nll(f, g, p.A, V[None, :], p.Psi)
+
+
+@pytest.mark.parametrize("K,P", [(4, 2), (8, 33), (16, 64), (16, 100), (32, 7), (32, 256), (48, 40), (64, 65)])
+def test_nll_grad_batched(h, K, P):
+    n = 6_337
+    p = make_problem(K, n, 2 * n, SEED + 200 + K, accept_reject=False)
+    V = inputs.starts(P, K, SEED + P)
+    V[0] = p.V_true
+    f, g = gpu_nll_grad(h, padded(p.A, n + 1), n, V, p.Psi)
+    check_nll(f, g, p.A, V, p.Psi)
+
+
+def test_batched_equals_separate_sets(h):
+    # per-set independence: P sets in one launch vs each set alone (within tolerance), and
+    # permuting the sets permutes the outputs exactly
+    p = make_problem(16, 5000, 10000, SEED + 300, accept_reject=False)
+    V = inputs.starts(37, 16, SEED + 301)
+    f, g = gpu_nll_grad(h, p.A, p.n, V, p.Psi)
+    perm = np.random.default_rng(0).permutation(37)
+    fp, gp = gpu_nll_grad(h, p.A, p.n, V[perm], p.Psi)
+    assert np.array_equal(fp, f[perm]) and np.array_equal(gp, g[perm])
+    for q in (0, 17, 36):
+        f1, g1 = gpu_nll_grad(h, p.A, p.n, V[q:q + 1], p.Psi)
+        _, _, cf, cg, _ = oracle.nll_grad(p.A, V[q:q + 1], p.Psi, with_cond=True)
+        assert abs(f1[0] - f[q]) <= 2e-5 * cf[0]
+        assert np.all(np.abs(g1[0] - g[q]) <= 2e-4 * np.repeat(cg[0], 2))
+
+
+def test_deterministic_bitwise(h):
+    p = make_problem(16, 30_000, 30_000, SEED + 400, accept_reject=False)
+    for V in (p.V_true[None, :], inputs.starts(50, 16, 3)):
+        a = gpu_nll_grad(h, p.A, p.n, V, p.Psi)
+        b = gpu_nll_grad(h, p.A, p.n, V, p.Psi)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_padding_is_never_read_as_events(h):
+    # NaN in every padding column must not change the result
+    p = make_problem(16, 9_999, 9_999, SEED + 500, accept_reject=False)
+    V = inputs.starts(5, 16, 4)
+    ld = 10_240
+    a = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), p.n, V, p.Psi)
+    b = gpu_nll_grad(h, padded(p.A, ld), p.n, V, p.Psi)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    a1 = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), p.n, V[:1], p.Psi)
+    b1 = gpu_nll_grad(h, padded(p.A, ld), p.n, V[:1], p.Psi)
+    assert np.array_equal(a1[0], b1[0]) and np.array_equal(a1[1], b1[1])
+
+
+def test_empty_data_sample(h):
+    # n = 0: only the normalisation term remains
+    K = 5
+    Psi = oracle.normint((np.random.default_rng(1).normal(size=(K, 100)) + 0j).astype(np.complex64))
+    V = inputs.starts(3, K, 5)
+    for P in (1, 3):
+        f, g = gpu_nll_grad(h, np.zeros((K, 2), np.complex64), 0, V[:P], Psi, n_factor=7.0)
+        fr, gr = oracle.nll_grad(np.zeros((K, 0), np.complex64), V[:P], Psi, n_factor=7.0)
+        assert np.allclose(f, fr, rtol=1e-14, atol=1e-14) and np.allclose(g, gr, rtol=1e-14, atol=1e-14)
+
+
+def test_zero_intensity_flags_the_set(h):
+    from paper_1108_5882_gb300 import pwa
+    p = make_problem(4, 1000, 1000, SEED + 600, accept_reject=False)
+    A = p.A.copy()
+    A[:, 123] = 0
+    for P in (1, 4):
+        V = inputs.starts(P, 4, 6)
+        f, g = gpu_nll_grad(h, A, p.n, V, p.Psi)
+        assert np.all(np.isinf(f)) and np.all(g == 0)
+        assert h.pwa_sync_status() == pwa.PWA_ERR_NONFINITE
+        assert h.pwa_sync_status() == pwa.PWA_OK  # read-and-clear
+        # the flag does not leak into the next evaluation
+        f2, _ = gpu_nll_grad(h, p.A, p.n, V, p.Psi)
+        assert np.all(np.isfinite(f2))
+
+
+def test_invalid_arguments_are_rejected(h):
+    from paper_1108_5882_gb300 import pwa
+    A = torch.zeros((4, 10), dtype=torch.complex64, device="cuda")
+    V = torch.zeros((1, 4), dtype=torch.complex64, device="cuda")
+    Psi = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
+    nll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(pwa.PWAError, match="ld"):
+        h.pwa_nll(A, 11, V, Psi, 1.0, nll)  # n > ld
+    A9 = torch.zeros((4, 9), dtype=torch.complex64, device="cuda")
+    with pytest.raises(pwa.PWAError, match="even"):
+        h.pwa_nll(A9, 9, V, Psi, 1.0, nll)
+    with pytest.raises(pwa.PWAError, match="n_gen"):
+        h.pwa_normint(A, 10, Psi, n_gen=0.0)
+    with pytest.raises(pwa.PWAError, match="mass"):
+        h.pwa_amplitudes([(0, 0, -1.0, 0.1)] * 4, torch.zeros((3, 10), device="cuda"), 10, A)
+
+
+# ------------------------------------------------------------------- full sizes ---------
+
+def test_scale_workload_full_size(h):
+    # K=16, N_data=1e6 in the launch configuration the benchmark times (one set per launch)
+    K, n = 16, 1_000_000
+    ws = inputs.wave_set_spread(K, SEED + 2)
+    kin = inputs.kinematics(n, SEED + 2, 4)
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin).astype(np.complex64)
+    kin_mc = inputs.kinematics(200_000, SEED + 2, 5)
+    Psi = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
+    V = inputs.production_amplitudes(K, SEED + 2)[None, :]
+    f, g = gpu_nll_grad(h, A, n, V, Psi)
+    check_nll(f, g, A, V, Psi)
+
+
+def test_multistart_workload_full_size_sampled(h):
+    # K=32, N_data=2e6, P=256 in one launch; the oracle checks a sample of the starts
+    K, n, P = 32, 2_000_000, 256
+    ws = inputs.wave_set_spread(K, SEED + 3)
+    kin = inputs.kinematics(n, SEED + 3, 4)
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin).astype(np.complex64)
+    kin_mc = inputs.kinematics(50_000, SEED + 3, 5)
+    Psi = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
+    V = inputs.starts(P, K, SEED + 3)
+    f, g = gpu_nll_grad(h, A, n, V, Psi)
+    for q in (0, 101, 255):
+        check_nll(f[q:q + 1], g[q:q + 1], A, V[q:q + 1], Psi)
+
+
+# ------------------------------------------------------------------- generator ----------
+
+def test_generator_matches_oracle(h):
+    from paper_1108_5882_gb300 import pwa
+    ws = inputs.wave_set_spread(16, SEED + 2)
+    V = inputs.production_amplitudes(16, SEED + 2)
+    C = pwa.pwa_envelope(pwa.waves_from(ws), V)
+    n_cand = 300_000
+    ref, na_ref, mr = oracle.generate(ws.J, ws.lam, ws.M, ws.W, V.astype(np.complex128), 77, 3, 1000, n_cand, C,
+                                      n_cand)
+    assert mr <= 1.0
+    kin = torch.zeros((3, n_cand), dtype=torch.float32, device="cuda")
+    na = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.pwa_generate(pwa.waves_from(ws), dev(V), 77, 3, 1000, n_cand, C, kin, n_cand, na)
+    got_n = int(na.item())
+    got = kin[:, :got_n].cpu().numpy()
+    # candidates are bit-identical; accept decisions may differ only at the FP32/FP64 boundary
+    a = set(map(tuple, got.T.view(np.uint32).tolist()))
+    b = set(map(tuple, ref.T.view(np.uint32).tolist()))
+    assert len(a ^ b) <= max(2, 1e-4 * na_ref), len(a ^ b)
+    assert abs(got_n - na_ref) <= max(2, 1e-4 * na_ref)
+    # order: candidate order, identical geometry-independent prefix
+    kin2 = torch.zeros((3, 100), dtype=torch.float32, device="cuda")
+    h.pwa_generate(pwa.waves_from(ws), dev(V), 77, 3, 1000, n_cand, C, kin2, 100, na)
+    assert torch.equal(kin2, kin[:, :100])
