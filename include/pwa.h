@@ -171,6 +171,50 @@ PWA_API pwa_status pwa_generate(pwa_handle* h, const pwa_wave* waves, int K, con
                         float* kin, int64_t ld_out, int64_t max_out, int64_t* n_accepted,
                         void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched fits: minimise -lnL (Sec. 2, footnote 2) over V for many starts of many fits at
+ * once (repeated fits from random starts, Sec. 2 and Sec. 4).  Every start is an independent
+ * L-BFGS run with Armijo backtracking whose state lives on the device; each iteration is one
+ * batched -lnL + gradient evaluation (pwa_nll_grad) and one L-BFGS step kernel, replayed as a
+ * captured CUDA graph between host convergence checks.  Blocks until all starts stop. */
+typedef struct pwa_fit_desc {
+    const float* A;       /* complex float [K][ld] data amplitudes (device) */
+    int K;
+    int64_t n;
+    int64_t ld;
+    const double* Psi;    /* complex double [K][K] normalisation integral (device) */
+    double n_factor;      /* factor on the normalisation term (N_data for the extended form) */
+    int P;                /* number of starts */
+    const float* V0;      /* complex float [P][K] starting values (device) */
+    double* V_out;        /* complex double [P][K] results (device), may be NULL */
+} pwa_fit_desc;
+
+typedef struct pwa_fit_opts {
+    int max_iter;         /* accepted L-BFGS steps per start (default 1000) */
+    int history;          /* L-BFGS memory, 1..20 (default 10) */
+    double gtol;          /* converged when max_c |grad_c| < gtol * n_factor (default 1e-6) */
+    int check_every;      /* iterations per graph replay between host checks (default 20) */
+    int gauge_fix;        /* 1: rotate each start so that V_0 is real >= 0 and freeze Im V_0 */
+    int use_graph;        /* 1: replay iterations as a captured CUDA graph (default 1) */
+} pwa_fit_opts;
+
+typedef struct pwa_fit_result {
+    double nll;           /* -lnL at the result */
+    double grad_max;      /* max_c |grad_c| at the result (frozen gauge component excluded) */
+    int iterations;       /* accepted steps */
+    int evaluations;      /* -lnL + gradient evaluations */
+    int status;           /* 0 converged, 1 max_iter, 2 line search failed, 3 non-finite start */
+} pwa_fit_result;
+
+/* Fill *opts with the defaults above. */
+PWA_API void pwa_fit_default_opts(pwa_fit_opts* opts);
+
+/* Run n_fits fits (fits[f].P starts each).  results: HOST array of sum_f fits[f].P entries in
+ * (fit, start) order.  opts may be NULL (defaults).  The workspace grows as needed (outside
+ * any stream capture).  Returns PWA_OK once every start has stopped (see result.status). */
+PWA_API pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits,
+                                 const pwa_fit_opts* opts, pwa_fit_result* results, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

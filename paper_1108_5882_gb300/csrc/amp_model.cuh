@@ -33,18 +33,23 @@ __device__ __forceinline__ void event_angles(float ct, float ph, EventAngles& t)
     }
 }
 
-// Angular factor P_J(cos theta) exp(i lambda phi) of wave a.
+// Angular factor P_J(cos theta) exp(i lambda phi) of wave a.  J and lambda are the same for
+// every thread of the launch, so the branches below are uniform (no divergence).
 __device__ __forceinline__ float2 wave_angle(const WaveTable& wt, int a, const EventAngles& t) {
     const int J = wt.J[a];
     const int lam = wt.lam[a];
     const int al = lam < 0 ? -lam : lam;
-    float pj = t.P[0], er = t.zr[0], ei = t.zi[0];
+    float pj = t.P[0];
 #pragma unroll
-    for (int j = 1; j <= AMP_JMAX; ++j) {
-        pj = (J == j) ? t.P[j] : pj;
-        er = (al == j) ? t.zr[j] : er;
-        ei = (al == j) ? t.zi[j] : ei;
-    }
+    for (int j = 1; j <= AMP_JMAX; ++j)
+        if (J == j) pj = t.P[j];
+    float er = t.zr[0], ei = t.zi[0];
+#pragma unroll
+    for (int j = 1; j <= AMP_JMAX; ++j)
+        if (al == j) {
+            er = t.zr[j];
+            ei = t.zi[j];
+        }
     if (lam < 0) ei = -ei;
     return make_float2(pj * er, pj * ei);
 }
@@ -55,7 +60,7 @@ __device__ __forceinline__ float2 bw_inv_den(const WaveTable& wt, int a, float m
     const float dm = (Mh - m) + Ml;  // M - m
     const float sm = (Mh + m) + Ml;  // M + m
     const float dr = dm * sm;        // M^2 - m^2
-    const float inv = 1.f / (dr * dr + MW * MW);
+    const float inv = __frcp_rn(dr * dr + MW * MW);
     *dr_out = dr;
     return make_float2(dr * inv, MW * inv);
 }

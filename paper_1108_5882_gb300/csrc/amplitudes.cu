@@ -9,8 +9,9 @@
 //   dBW/dM = -G (M^2 + m^2) / D^2,   dBW/dG = M (M^2 - m^2) / D^2,   D = M^2 - m^2 - i M G,
 // each times the same angular factor.
 //
-// One thread per event, all K waves: the kinematics are read once (12 B/event) and every
-// wave row is written with one coalesced 8-byte store per thread, so the kernel is bound by
+// Each thread takes four consecutive events and loops over the K waves: the kinematics are
+// read once (12 B/event), the per-wave parameters are uniform across the launch, and every
+// wave row is written with two coalesced 16-byte stores per thread, so the kernel is bound by
 // the HBM write stream of 8K (or 24K with derivatives) bytes per event.
 //
 // Precision: everything in FP32 (see amp_model.cuh for the two-float mass split).
@@ -20,41 +21,87 @@ namespace pwa {
 
 namespace {
 
+constexpr int AMP_EV = 4;  // events per thread (consecutive: two 16-byte stores per wave)
+
+// Legendre P_J(x) by Bonnet's recurrence; J is the same for the whole launch (uniform loop).
+__device__ __forceinline__ float legendre_rec(int J, float x) {
+    if (J == 0) return 1.f;
+    float pm = 1.f, p = x;
+    for (int j = 1; j < J; ++j) {
+        const float pn = ((2.f * j + 1.f) * x * p - (float)j * pm) * __frcp_rn((float)(j + 1));
+        pm = p;
+        p = pn;
+    }
+    return p;
+}
+
 template <bool DERIV>
 __global__ void __launch_bounds__(PWA_THREADS) k_amplitudes(WaveTable wt, const float* __restrict__ kin,
                                                             int64_t n, int64_t ld, float2* __restrict__ A,
                                                             float2* __restrict__ dAdM, float2* __restrict__ dAdW) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += stride) {
-        if (i >= n) {  // zero padding columns
-            for (int a = 0; a < wt.K; ++a) {
-                A[a * ld + i] = make_float2(0.f, 0.f);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * AMP_EV;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * AMP_EV; i0 < ld; i0 += stride) {
+        float m[AMP_EV], ct[AMP_EV], c1[AMP_EV], s1[AMP_EV];
+#pragma unroll
+        for (int k = 0; k < AMP_EV; ++k) {
+            const int64_t i = i0 + k;
+            const bool in = i < n;
+            m[k] = in ? __ldg(kin + i) : 2.f;
+            ct[k] = in ? __ldg(kin + ld + i) : 0.f;
+            const float ph = in ? __ldg(kin + 2 * ld + i) : 0.f;
+            sincosf(ph, &s1[k], &c1[k]);
+        }
+        const bool full = i0 + AMP_EV <= ld;  // ld is even: pairs never straddle it
+        for (int a = 0; a < wt.K; ++a) {
+            const int J = wt.J[a], lam = wt.lam[a];
+            const int al = lam < 0 ? -lam : lam;
+            const float Mh = wt.Mhi[a], Ml = wt.Mlo[a], MW = wt.MW[a], G = wt.W[a];
+            float2 out[AMP_EV], oM[AMP_EV], oW[AMP_EV];
+#pragma unroll
+            for (int k = 0; k < AMP_EV; ++k) {
+                // angular factor P_J(cos theta) exp(i lambda phi)
+                float er = 1.f, ei = 0.f;
+                for (int j = 0; j < al; ++j) {
+                    const float t = er * c1[k] - ei * s1[k];
+                    ei = er * s1[k] + ei * c1[k];
+                    er = t;
+                }
+                if (lam < 0) ei = -ei;
+                const float pj = legendre_rec(J, ct[k]);
+                const float2 ang = make_float2(pj * er, pj * ei);
+                // 1/D, D = M^2 - m^2 - i M G, with M - m from the two-float mass
+                const float dr = ((Mh - m[k]) + Ml) * ((Mh + m[k]) + Ml);
+                const float inv = __frcp_rn(dr * dr + MW * MW);
+                const float2 id = make_float2(dr * inv, MW * inv);
+                const bool in = i0 + k < n;
+                const float2 bw = make_float2(MW * id.x, MW * id.y);
+                out[k] = in ? cmul(bw, ang) : make_float2(0.f, 0.f);
                 if (DERIV) {
-                    dAdM[a * ld + i] = make_float2(0.f, 0.f);
-                    dAdW[a * ld + i] = make_float2(0.f, 0.f);
+                    const float2 id2 = cmul(id, id);                         // 1/D^2
+                    const float cm = -G * (Mh * Mh + m[k] * m[k]);           // -G (M^2 + m^2)
+                    const float cw = (Mh + Ml) * dr;                         // M (M^2 - m^2)
+                    oM[k] = in ? cmul(make_float2(cm * id2.x, cm * id2.y), ang) : make_float2(0.f, 0.f);
+                    oW[k] = in ? cmul(make_float2(cw * id2.x, cw * id2.y), ang) : make_float2(0.f, 0.f);
                 }
             }
-            continue;
-        }
-        const float m = __ldg(kin + i);
-        const float ct = __ldg(kin + ld + i);
-        const float ph = __ldg(kin + 2 * ld + i);
-        EventAngles t;
-        event_angles(ct, ph, t);
-        const float m2 = m * m;
-        for (int a = 0; a < wt.K; ++a) {
-            const float2 ang = wave_angle(wt, a, t);
-            float dr;
-            const float2 id = bw_inv_den(wt, a, m, &dr);  // 1/D
-            const float MW = wt.MW[a];
-            const float2 bw = make_float2(MW * id.x, MW * id.y);
-            A[a * ld + i] = cmul(bw, ang);
+            float2* row = A + a * ld + i0;
+            if (full) {
+                reinterpret_cast<float4*>(row)[0] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+                reinterpret_cast<float4*>(row)[1] = make_float4(out[2].x, out[2].y, out[3].x, out[3].y);
+            } else {
+#pragma unroll
+                for (int k = 0; k < AMP_EV; ++k)
+                    if (i0 + k < ld) row[k] = out[k];
+            }
             if (DERIV) {
-                const float2 id2 = cmul(id, id);                    // 1/D^2
-                const float cm = -wt.W[a] * (wt.Mhi[a] * wt.Mhi[a] + m2);  // -G (M^2 + m^2)
-                const float cw = (wt.Mhi[a] + wt.Mlo[a]) * dr;      // M (M^2 - m^2)
-                dAdM[a * ld + i] = cmul(make_float2(cm * id2.x, cm * id2.y), ang);
-                dAdW[a * ld + i] = cmul(make_float2(cw * id2.x, cw * id2.y), ang);
+                float2* rm = dAdM + a * ld + i0;
+                float2* rw = dAdW + a * ld + i0;
+#pragma unroll
+                for (int k = 0; k < AMP_EV; ++k)
+                    if (i0 + k < ld) {
+                        rm[k] = oM[k];
+                        rw[k] = oW[k];
+                    }
             }
         }
     }
@@ -66,7 +113,7 @@ cudaError_t launch_amplitudes(const WaveTable& wt, const float* kin, int64_t n, 
                               float2* A, float2* dAdM, float2* dAdW, int sm_count,
                               cudaStream_t st) {
     if (ld == 0) return cudaSuccess;
-    int64_t blocks = (ld + PWA_THREADS - 1) / PWA_THREADS;
+    int64_t blocks = (ld + PWA_THREADS * AMP_EV - 1) / (PWA_THREADS * AMP_EV);
     int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (dAdM)

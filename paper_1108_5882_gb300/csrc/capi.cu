@@ -198,6 +198,9 @@ void pwa_destroy(pwa_handle* h) {
     if (h->counters) cudaFree(h->counters);
     if (h->status) cudaFree(h->status);
     if (h->bad) cudaFree(h->bad);
+    if (h->fitws) cudaFree(h->fitws);
+    if (h->fit_event) cudaEventDestroy(h->fit_event);
+    if (h->fit_stream) cudaStreamDestroy(h->fit_stream);
     delete h;
 }
 
@@ -342,6 +345,192 @@ pwa_status pwa_generate(pwa_handle* h, const pwa_wave* waves, int K, const float
                                          envelope, kin, ld_out, max_out, reinterpret_cast<long long*>(n_accepted),
                                          h->ws, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "generate launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+void pwa_fit_default_opts(pwa_fit_opts* o) {
+    if (!o) return;
+    o->max_iter = 1000;
+    o->history = 10;
+    o->gtol = 1e-6;
+    o->check_every = 20;
+    o->gauge_fix = 1;
+    o->use_graph = 1;
+}
+
+pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, const pwa_fit_opts* opts_in,
+                         pwa_fit_result* results, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (!fits || n_fits < 1 || !results) return fail(h, PWA_ERR_INVALID_ARG, "fits/results NULL or n_fits < 1");
+    pwa_fit_opts o;
+    pwa_fit_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1)
+        return fail(h, PWA_ERR_INVALID_ARG, "bad options (max_iter >= 1, 1 <= history <= 20, gtol > 0, check_every >= 1)");
+    int P_tot = 0;
+    size_t ws_need = 0;
+    for (int f = 0; f < n_fits; ++f) {
+        const pwa_fit_desc& d = fits[f];
+        pwa_status st = check_amp_layout(h, d.K, d.n, d.ld);
+        if (st != PWA_OK) return st;
+        if (d.P < 1 || d.P > (1 << 20)) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: P = %d out of range", f, d.P);
+        if ((d.n > 0 && !d.A) || !d.Psi || !d.V0) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: NULL A, Psi or V0", f);
+        if ((d.n > 0 && !aligned16(d.A)) || !aligned16(d.Psi) || (reinterpret_cast<uintptr_t>(d.V0) & 7u))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: misaligned array", f);
+        if (d.V_out && (reinterpret_cast<uintptr_t>(d.V_out) & 15u))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: V_out not 16-byte aligned", f);
+        if (!std::isfinite(d.n_factor)) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: n_factor not finite", f);
+        P_tot += d.P;
+        size_t w = pwa::nll_workspace(d.K, d.n, d.P, h->sm_count);
+        if (w > ws_need) ws_need = w;
+    }
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    // the fitter runs on a handle-owned non-blocking stream (capturable), ordered after the
+    // caller's stream; the call returns after that stream has drained
+    if (!h->fit_stream) {
+        cudaError_t ce = cudaStreamCreateWithFlags(&h->fit_stream, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->fit_event, cudaEventDisableTiming);
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream");
+    }
+    {
+        cudaError_t ce = cudaEventRecord(h->fit_event, (cudaStream_t)stream);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->fit_stream, h->fit_event, 0);
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream ordering");
+    }
+    cudaStream_t s = h->fit_stream;
+    const int m = o.history;
+    pwa_status st = ensure_workspace(h, ws_need, P_tot);
+    if (st != PWA_OK) return st;
+    // fit state + per-fit evaluation buffers (V trial, nll, grad)
+    size_t state_b = pwa::fit_workspace(P_tot, m);
+    size_t need = state_b;
+    for (int f = 0; f < n_fits; ++f) need += pwa::fit_eval_bytes(fits[f].P, fits[f].K);
+    if (need > h->fitws_bytes) {
+        if (h->fitws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->fitws);
+            h->fitws = nullptr;
+            h->fitws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->fitws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PWA_ERR_WORKSPACE, "fit workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        }
+        h->fitws_bytes = need;
+    }
+    struct EvalBuf {
+        float2* Vt;
+        double* nll;
+        double* grad;
+    };
+    std::vector<EvalBuf> eb(n_fits);
+    std::vector<int> K_of_p(P_tot);
+    {
+        char* c = reinterpret_cast<char*>(h->fitws) + state_b;
+        auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+        int q = 0;
+        for (int f = 0; f < n_fits; ++f) {
+            const int P = fits[f].P, K = fits[f].K;
+            eb[f].Vt = reinterpret_cast<float2*>(c);
+            c += r(sizeof(float2) * (size_t)P * K);
+            eb[f].nll = reinterpret_cast<double*>(c);
+            c += r(sizeof(double) * P);
+            eb[f].grad = reinterpret_cast<double*>(c);
+            c += r(sizeof(double) * (size_t)P * 2 * K);
+            for (int p = 0; p < P; ++p) K_of_p[q++] = K;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    int off = 0;
+    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
+        e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(fits[f].V0), fits[f].K, fits[f].P,
+                                 off, o.gauge_fix, eb[f].Vt, s);
+        off += fits[f].P;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "fit init");
+    auto iteration = [&]() -> cudaError_t {
+        int p_off = 0;
+        for (int f = 0; f < n_fits; ++f) {
+            const pwa_fit_desc& d = fits[f];
+            cudaError_t ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
+                                             reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll,
+                                             eb[f].grad, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
+                                             h->sm_count, s);
+            if (ee != cudaSuccess) return ee;
+            ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
+                                      o.gtol * std::fabs(d.n_factor), o.gauge_fix, o.max_iter, s);
+            if (ee != cudaSuccess) return ee;
+            p_off += d.P;
+        }
+        return cudaSuccess;
+    };
+    // eager first iteration (selects tile shapes outside any capture)
+    e = iteration();
+    if (e != cudaSuccess) return cuda_fail(h, e, "fit iteration");
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool graph_ok = false;
+    if (o.use_graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                cudaError_t ce = cudaSuccess;
+                for (int it = 0; it < o.check_every && ce == cudaSuccess; ++it) ce = iteration();
+                cudaError_t ee = cudaStreamEndCapture(s, &graph);
+                if (ce == cudaSuccess && ee == cudaSuccess &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+                    graph_ok = true;
+                cudaGetLastError();
+            }
+        }
+    }
+    int* running_h = nullptr;
+    if (cudaMallocHost(&running_h, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        running_h = nullptr;
+    }
+    int running_local = 1;
+    int* running = running_h ? running_h : &running_local;
+    // every iteration evaluates once; a start stops after max_iter accepted steps, and the line
+    // search can reject a bounded number of times per step, so the loop is bounded too
+    const long long max_loops = 60LL * (long long)o.max_iter + 100;
+    long long loops = 1;
+    while (e == cudaSuccess) {
+        e = pwa::fit_launch_count(h->fitws, P_tot, m, running, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || *running == 0 || loops >= max_loops) break;
+        if (graph_ok) {
+            e = cudaGraphLaunch(exec, s);
+            loops += o.check_every;
+        } else {
+            for (int it = 0; it < o.check_every && e == cudaSuccess; ++it) e = iteration();
+            loops += o.check_every;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (running_h) cudaFreeHost(running_h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fit loop");
+    off = 0;
+    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
+        if (fits[f].V_out) e = pwa::fit_export(h->fitws, P_tot, m, fits[f].K, fits[f].P, off, fits[f].V_out, s);
+        off += fits[f].P;
+    }
+    std::vector<double> fv, gm;
+    std::vector<int> it, ev, stv;
+    if (e == cudaSuccess) e = pwa::fit_read_results(h->fitws, P_tot, m, fv, gm, it, ev, stv, K_of_p.data(), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fit results");
+    for (int p = 0; p < P_tot; ++p) {
+        results[p].nll = fv[p];
+        results[p].grad_max = gm[p];
+        results[p].iterations = it[p];
+        results[p].evaluations = ev[p];
+        results[p].status = stv[p] < 0 ? 1 : stv[p];  // still running at the loop bound: max_iter
+    }
     h->err.clear();
     return PWA_OK;
 }

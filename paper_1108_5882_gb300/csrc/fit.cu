@@ -1,0 +1,412 @@
+// Batched minimisation of -lnL (Sec. 2, footnote 2: -lnL is fed to the minimiser) over the
+// production amplitudes V, many parameter sets at once.
+//
+// The paper's fits run sequentially through Minuit/Fumili (Sec. 4, "More control over the
+// fitters") and are repeated from many random starts to gain confidence in the global minimum
+// (Sec. 2 and Sec. 4, "Fits with large numbers of parameters").  Here every start of every fit
+// is an independent L-BFGS run whose state lives on the device:
+//
+//   one iteration = one batched evaluation of f and g at the trial points of all starts
+//                 + k_lbfgs_step: per start, an Armijo test of the trial point; on acceptance
+//                   the (s, y) pair enters the limited-memory history and the two-loop
+//                   recursion gives the next direction; on rejection the step is shortened
+//                   by safeguarded quadratic interpolation; the next trial point is written
+//                   as single-precision V for the next evaluation.
+//
+// The host replays check_every iterations as one captured CUDA graph and reads back a single
+// counter of running starts between replays.  No lean-fitter extras (no Hessian or error
+// analysis) are done (Sec. 4 asks for exactly this control).
+//
+// Gauge: f is invariant under a global phase of V (Eq. 1), so the Hessian is singular along
+// i V.  With gauge_fix each start is rotated so that V_0 is real and non-negative and the
+// Im V_0 component of the gradient is frozen at zero.
+#include <cmath>
+#include <vector>
+
+#include "pwa_internal.cuh"
+
+namespace pwa {
+
+namespace {
+
+constexpr int FIT_RUNNING = -1;
+
+struct FitState {
+    // per start (P_tot starts over all fits), D = 2K <= 2*PWA_MAX_WAVES
+    double* x;      // [P][DM] accepted point
+    double* g;      // [P][DM] gradient at x
+    double* d;      // [P][DM] search direction
+    double* S;      // [P][m][DM]
+    double* Y;      // [P][m][DM]
+    double* rho;    // [P][m]
+    double* f;      // [P]
+    double* alpha;  // [P]
+    double* gtd;    // [P]
+    int* iter;      // [P]
+    int* nhist;     // [P]
+    int* head;      // [P]
+    int* status;    // [P]
+    int* evals;     // [P]
+    int* running;   // [1]
+};
+
+constexpr int DM = 2 * PWA_MAX_WAVES;
+
+__device__ __forceinline__ double block_dot(const double* a, const double* b, int D, double* red) {
+    // fixed-order dot product over D <= 128 components: per-thread products, shared tree
+    const int t = threadIdx.x;
+    red[t] = t < D ? a[t] * b[t] : 0.0;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) red[t] += red[t + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max_abs(const double* a, int D, double* red) {
+    const int t = threadIdx.x;
+    red[t] = t < D ? fabs(a[t]) : 0.0;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) red[t] = fmax(red[t], red[t + o]);
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// init: x <- gauge-fixed V0 (double), trial <- x, status running
+__global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, int p_off, int gauge,
+                           float2* __restrict__ Vt) {
+    const int p = p_off + blockIdx.x, t = threadIdx.x;
+    const int D = 2 * K;
+    // phase of V_0
+    const float2 v0 = V0[(int64_t)blockIdx.x * K];
+    double c = 1.0, s = 0.0;
+    if (gauge) {
+        const double r = hypot((double)v0.x, (double)v0.y);
+        if (r > 0.0) {
+            c = v0.x / r;
+            s = -v0.y / r;  // multiply by exp(-i arg V_0)
+        }
+    }
+    if (t < K) {
+        const float2 v = V0[(int64_t)blockIdx.x * K + t];
+        const double re = c * v.x - s * v.y, im = c * v.y + s * v.x;
+        st.x[(int64_t)p * DM + 2 * t] = re;
+        st.x[(int64_t)p * DM + 2 * t + 1] = (gauge && t == 0) ? 0.0 : im;
+        Vt[(int64_t)blockIdx.x * K + t] = make_float2((float)re, (gauge && t == 0) ? 0.f : (float)im);
+    }
+    if (t == 0) {
+        st.iter[p] = 0;
+        st.nhist[p] = 0;
+        st.head[p] = 0;
+        st.status[p] = FIT_RUNNING;
+        st.evals[p] = 0;
+        st.alpha[p] = 0.0;  // 0: the first evaluation defines the starting point
+        st.f[p] = INFINITY;
+        st.gtd[p] = 0.0;
+    }
+    (void)D;
+}
+
+// One L-BFGS step per start.  ft/gt: f and g at the trial point just evaluated (layout of
+// pwa_nll_grad).  Writes the next trial point as single-precision V.
+__global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* __restrict__ ft,
+                                                    const double* __restrict__ gt, float2* __restrict__ Vt, int K,
+                                                    int p_off, int m, double gtol, int gauge, int max_iter) {
+    __shared__ double red[128];
+    __shared__ double q[DM], xt[DM];
+    __shared__ double a_hist[32];
+    __shared__ int s_action;  // 0: keep, 1: accepted, 2: rejected
+    const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
+    const int D = 2 * K;
+    double* x = st.x + (int64_t)p * DM;
+    double* g = st.g + (int64_t)p * DM;
+    double* d = st.d + (int64_t)p * DM;
+    double* S = st.S + (int64_t)p * m * DM;
+    double* Y = st.Y + (int64_t)p * m * DM;
+    double* rho = st.rho + (int64_t)p * m;
+    const int status = st.status[p];
+    if (status != FIT_RUNNING) {
+        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        return;
+    }
+    if (t == 0) st.evals[p] += 1;
+    const double fnew = ft[pl];
+    // trial point that was evaluated = x + alpha d (or x itself for the first evaluation)
+    const double alpha = st.alpha[p];
+    if (t < D) {
+        xt[t] = (alpha == 0.0) ? x[t] : x[t] + alpha * d[t];
+        double gv = gt[(int64_t)pl * D + t];
+        if (gauge && t == 1) gv = 0.0;
+        q[t] = gv;  // gradient at the trial point (frozen gauge component)
+    }
+    __syncthreads();
+    // directional derivative at the trial point, phi'(alpha) = g(x + alpha d) . d
+    const double dphi = (alpha == 0.0) ? 0.0 : block_dot(q, d, D, red);
+    if (t == 0) {
+        const bool finite = isfinite(fnew);
+        if (alpha == 0.0) {
+            s_action = finite ? 1 : 3;
+        } else {
+            // Armijo, or the approximate Wolfe conditions of Hager and Zhang (2005), which
+            // judge the step by phi' when f differences fall below the rounding of f itself:
+            // sigma phi'(0) <= phi'(alpha) <= (2 delta - 1) phi'(0), f(alpha) <= f(0) + eps |f(0)|
+            const double f0 = st.f[p], g0 = st.gtd[p];
+            const bool armijo = fnew <= f0 + 1e-4 * alpha * g0;
+            const bool awolfe = fnew <= f0 + 1e-6 * fabs(f0) && dphi >= 0.9 * g0 && dphi <= -0.8 * g0;
+            s_action = (finite && (armijo || awolfe)) ? 1 : 2;
+        }
+    }
+    __syncthreads();
+    const int action = s_action;
+    if (action == 3) {  // non-finite at the start point
+        if (t == 0) st.status[p] = 3;
+        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        return;
+    }
+    if (action == 2) {
+        // shorten the step: minimiser of the quadratic through f0, f0' and f(alpha), clamped
+        if (t == 0) {
+            const double f0 = st.f[p], g0 = st.gtd[p];
+            double an = alpha * 0.5;
+            if (isfinite(fnew) && isfinite(dphi) && dphi > 0.0) {
+                an = alpha * (-g0) / (dphi - g0);  // secant zero of phi' between 0 and alpha
+            } else if (isfinite(fnew)) {
+                const double den = 2.0 * (fnew - f0 - g0 * alpha);
+                if (den > 0.0) an = -g0 * alpha * alpha / den;  // quadratic interpolation of phi
+            }
+            an = fmin(fmax(an, 0.1 * alpha), 0.5 * alpha);
+            st.alpha[p] = an;
+            if (an < 1e-20) st.status[p] = 2;
+        }
+        __syncthreads();
+        const double an = st.alpha[p];
+        if (t < K) {
+            const double re = x[2 * t] + an * d[2 * t], im = x[2 * t + 1] + an * d[2 * t + 1];
+            Vt[(int64_t)pl * K + t] = make_float2((float)re, (float)im);
+        }
+        return;
+    }
+    // ---- accepted: history update with s = xt - x, y = gt - g
+    const int nh = st.nhist[p];
+    int head = st.head[p];
+    if (alpha != 0.0) {
+        double* sN = S + (int64_t)head * DM;
+        double* yN = Y + (int64_t)head * DM;
+        if (t < D) {
+            sN[t] = xt[t] - x[t];
+            yN[t] = q[t] - g[t];
+        }
+        __syncthreads();
+        const double sy = block_dot(sN, yN, D, red);
+        const double yy = block_dot(yN, yN, D, red);
+        if (t == 0) {
+            if (sy > 1e-12 * yy && sy > 0.0) {
+                rho[head] = 1.0 / sy;
+                st.head[p] = (head + 1) % m;
+                st.nhist[p] = nh < m ? nh + 1 : m;
+            }
+        }
+        __syncthreads();
+    }
+    if (t < D) {
+        x[t] = xt[t];
+        g[t] = q[t];
+    }
+    if (t == 0) {
+        st.f[p] = fnew;
+        if (alpha != 0.0) st.iter[p] += 1;
+    }
+    __syncthreads();
+    const double gmax = block_max_abs(g, D, red);
+    if (gmax < gtol) {
+        if (t == 0) st.status[p] = 0;
+        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        return;
+    }
+    if (st.iter[p] >= max_iter) {
+        if (t == 0) st.status[p] = 1;
+        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        return;
+    }
+    // ---- two-loop recursion: q = g; newest to oldest
+    const int n_h = st.nhist[p];
+    head = st.head[p];
+    for (int j = 0; j < n_h; ++j) {
+        const int k = (head - 1 - j + 2 * m) % m;
+        const double a = rho[k] * block_dot(S + (int64_t)k * DM, q, D, red);
+        if (t == 0) a_hist[k] = a;
+        if (t < D) q[t] -= a * Y[(int64_t)k * DM + t];
+        __syncthreads();
+    }
+    double gamma = 1.0;
+    if (n_h > 0) {
+        const int k = (head - 1 + m) % m;
+        const double yy = block_dot(Y + (int64_t)k * DM, Y + (int64_t)k * DM, D, red);
+        gamma = 1.0 / (rho[k] * yy);  // s.y / y.y
+    }
+    if (t < D) q[t] *= gamma;
+    __syncthreads();
+    for (int j = n_h - 1; j >= 0; --j) {
+        const int k = (head - 1 - j + 2 * m) % m;
+        const double b = rho[k] * block_dot(Y + (int64_t)k * DM, q, D, red);
+        if (t < D) q[t] += (a_hist[k] - b) * S[(int64_t)k * DM + t];
+        __syncthreads();
+    }
+    // d = -H g
+    if (t < D) d[t] = (gauge && t == 1) ? 0.0 : -q[t];
+    __syncthreads();
+    double gtd = block_dot(g, d, D, red);
+    double a0 = 1.0;
+    if (!(gtd < 0.0) || n_h == 0) {
+        // no curvature information yet (or not a descent direction): steepest descent with a
+        // step that moves the largest component by 1% of the largest |x| (or 1e-3)
+        if (t < D) d[t] = (gauge && t == 1) ? 0.0 : -g[t];
+        __syncthreads();
+        gtd = block_dot(g, d, D, red);
+        const double xm = block_max_abs(x, D, red);
+        a0 = 0.01 * fmax(xm, 0.1) / gmax;
+        if (!(gtd < 0.0) && t == 0) st.nhist[p] = 0;
+    }
+    if (t == 0) {
+        st.gtd[p] = gtd;
+        st.alpha[p] = a0;
+    }
+    if (t < K) {
+        const double re = x[2 * t] + a0 * d[2 * t], im = x[2 * t + 1] + a0 * d[2 * t + 1];
+        Vt[(int64_t)pl * K + t] = make_float2((float)re, (float)im);
+    }
+}
+
+__global__ void k_count_running(const int* __restrict__ status, int P, int* __restrict__ out) {
+    __shared__ int s[256];
+    int c = 0;
+    for (int i = threadIdx.x; i < P; i += 256) c += status[i] == FIT_RUNNING;
+    s[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void k_fit_export(FitState st, int K, int p_off, int P, double2* __restrict__ Vout) {
+    const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
+    if (t < K && Vout) Vout[(int64_t)pl * K + t] = make_double2(st.x[(int64_t)p * DM + 2 * t], st.x[(int64_t)p * DM + 2 * t + 1]);
+    (void)P;
+}
+
+}  // namespace
+
+size_t fit_state_bytes(int P_tot, int m) {
+    const size_t p = (size_t)P_tot;
+    return sizeof(double) * p * DM * (3 + 2 * (size_t)m) + sizeof(double) * p * ((size_t)m + 3) +
+           sizeof(int) * (p * 5 + 16) + 1024;
+}
+
+struct FitLayout {
+    FitState st;
+};
+
+static FitState carve(void* base, int P_tot, int m) {
+    char* c = reinterpret_cast<char*>(base);
+    auto take = [&](size_t bytes) {
+        void* r = c;
+        c += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    FitState s;
+    const size_t p = (size_t)P_tot;
+    s.x = (double*)take(sizeof(double) * p * DM);
+    s.g = (double*)take(sizeof(double) * p * DM);
+    s.d = (double*)take(sizeof(double) * p * DM);
+    s.S = (double*)take(sizeof(double) * p * m * DM);
+    s.Y = (double*)take(sizeof(double) * p * m * DM);
+    s.rho = (double*)take(sizeof(double) * p * m);
+    s.f = (double*)take(sizeof(double) * p);
+    s.alpha = (double*)take(sizeof(double) * p);
+    s.gtd = (double*)take(sizeof(double) * p);
+    s.iter = (int*)take(sizeof(int) * p);
+    s.nhist = (int*)take(sizeof(int) * p);
+    s.head = (int*)take(sizeof(int) * p);
+    s.status = (int*)take(sizeof(int) * p);
+    s.evals = (int*)take(sizeof(int) * p);
+    s.running = (int*)take(sizeof(int) * 16);
+    return s;
+}
+
+size_t fit_workspace(int P_tot, int m) {
+    // carve() rounds every array to 256 bytes
+    const size_t p = (size_t)P_tot;
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return 3 * r(sizeof(double) * p * DM) + 2 * r(sizeof(double) * p * m * DM) + r(sizeof(double) * p * m) +
+           3 * r(sizeof(double) * p) + 5 * r(sizeof(int) * p) + r(sizeof(int) * 16);
+}
+
+// Per-fit device buffers for the evaluation (V trial, nll, grad) live in `evalbuf`.
+size_t fit_eval_bytes(int P, int K) {
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return r(sizeof(float2) * (size_t)P * K) + r(sizeof(double) * P) + r(sizeof(double) * (size_t)P * 2 * K);
+}
+
+cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
+                            float2* Vt, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_fit_init<<<P, 128, 0, s>>>(st, V0, K, p_off, gauge, Vt);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
+                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, gauge, max_iter);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_count_running<<<1, 256, 0, s>>>(st.status, P_tot, st.running);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(host_out, st.running, sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
+                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int K_of_p[],
+                             cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    f.resize(P_tot);
+    iter.resize(P_tot);
+    evals.resize(P_tot);
+    status.resize(P_tot);
+    gmax.resize(P_tot);
+    std::vector<double> g((size_t)P_tot * DM);
+    cudaError_t e = cudaMemcpyAsync(f.data(), st.f, sizeof(double) * P_tot, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iter.data(), st.iter, sizeof(int) * P_tot, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(evals.data(), st.evals, sizeof(int) * P_tot, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), st.status, sizeof(int) * P_tot, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), st.g, sizeof(double) * P_tot * DM, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    for (int p = 0; p < P_tot; ++p) {
+        double mx = 0.0;
+        for (int c = 0; c < 2 * K_of_p[p]; ++c) mx = fmax(mx, fabs(g[(size_t)p * DM + c]));
+        gmax[p] = mx;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_fit_export<<<P, 128, 0, s>>>(st, K, p_off, P, reinterpret_cast<double2*>(Vout));
+    return cudaGetLastError();
+}
+
+}  // namespace pwa

@@ -30,14 +30,15 @@
 #include <mutex>
 #include <tuple>
 
-#include "pwa_internal.cuh"
+#include "nll_common.cuh"
+#include "tma.cuh"
 
 namespace pwa {
 
 namespace {
 
 // ======================================================================= one parameter set
-template <int KMAX, bool GRAD, bool HOLD>
+template <int KMAX, bool GRAD, bool HOLD, bool FUSED>
 __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
     const float2* __restrict__ A, int K, int64_t n, int64_t ld, const float2* __restrict__ V,
     const double2* __restrict__ Psi, double nfac, float2* __restrict__ part, unsigned* __restrict__ counter,
@@ -46,17 +47,10 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
     // HOLD: keep the event's amplitudes in registers for the gradient pass; otherwise reload
     // them (L1 hits: the same lines were just read) to free registers for more warps
     constexpr int NG = 2 * KMAX;
-    constexpr int ROUNDS = (NG + 31) / 32;
-    constexpr int NW = PWA_THREADS / 32;
     __shared__ float2 sV[KMAX];
-    __shared__ float sred[NW][ROUNDS * 32];
-    __shared__ ff slred[NW];
-    __shared__ int sLast;
-    __shared__ ff sfin[PWA_THREADS];
-    __shared__ double sval[1 + NG];
-    __shared__ double2 sT[KMAX];
+    __shared__ StreamReduceSmem<KMAX, PWA_THREADS> red;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     if (tid < KMAX) sV[tid] = tid < K ? V[tid] : make_float2(0.f, 0.f);
     __syncthreads();
 
@@ -93,8 +87,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
             const float I1 = u1r * u1r + u1i * u1i;
             float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f;
             if (intensity_ok(I0)) {
-                lacc = ff_add_f(lacc, logf(I0));
-                const float r = 1.f / I0;
+                lacc = ff_add_f(lacc, __logf(I0));
+                const float r = __frcp_rn(I0);
                 w0r = u0r * r;
                 w0i = u0i * r;
             } else {
@@ -102,8 +96,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
             }
             if (has1) {
                 if (intensity_ok(I1)) {
-                    lacc = ff_add_f(lacc, logf(I1));
-                    const float r = 1.f / I1;
+                    lacc = ff_add_f(lacc, __logf(I1));
+                    const float r = __frcp_rn(I1);
                     w1r = u1r * r;
                     w1i = u1i * r;
                 } else {
@@ -138,8 +132,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
             const float I0 = ur * ur + ui * ui;
             float wr = 0.f, wi = 0.f;
             if (intensity_ok(I0)) {
-                lacc = ff_add_f(lacc, logf(I0));
-                const float r = 1.f / I0;
+                lacc = ff_add_f(lacc, __logf(I0));
+                const float r = __frcp_rn(I0);
                 wr = ur * r;
                 wi = ui * r;
             } else {
@@ -158,83 +152,164 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
         }
     }
 
-    // ---- warp: reduce-scatter of the gradient partials, butterfly of the ln I pair
-    if (GRAD) {
+    stream_reduce_finalize<KMAX, GRAD, FUSED, PWA_THREADS>(g, lacc, bad, sV, red, K, Psi, nfac, part, counter, badw,
+                                                           status, nll, grad);
+}
+
+// ----------------------------------------------------------------------- TMA-pipelined variant
+// The same arithmetic with the amplitude stream staged through shared memory by bulk copies:
+// thread 0 keeps S stages of E events x K waves in flight (one 1-D cp.async.bulk per wave row,
+// completion counted on the stage's mbarrier), so the bytes in flight no longer depend on how
+// many registers the consumers use.  One thread per event of the tile; persistent grid.
+template <int KMAX>
+struct TmaCfg {
+    static constexpr int E = 128;  // events per tile == threads per block
+    static constexpr int S0 = 98304 / (KMAX * E * 8);
+    static constexpr int S = S0 < 2 ? 2 : (S0 > 4 ? 4 : S0);
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)S * KMAX * E + 64;
+};
+
+template <int KMAX, bool GRAD>
+__global__ void __launch_bounds__(TmaCfg<KMAX>::E) k_nll_tma(
+    const float2* __restrict__ A, int K, int64_t n, int64_t ld, const float2* __restrict__ V,
+    const double2* __restrict__ Psi, double nfac, float2* __restrict__ part, unsigned* __restrict__ counter,
+    int* __restrict__ badw, int* __restrict__ status, double* __restrict__ nll, double* __restrict__ grad) {
+    using C = TmaCfg<KMAX>;
+    constexpr int E = C::E, S = C::S, NG = 2 * KMAX;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(tsm);               // [S] (64 bytes reserved)
+    float2* buf = reinterpret_cast<float2*>(tsm + 64);                // [S][KMAX][E]
+    __shared__ float2 sV[KMAX];
+    __shared__ StreamReduceSmem<KMAX, E> red;
+    const int tid = threadIdx.x;
+    if (tid < KMAX) sV[tid] = tid < K ? V[tid] : make_float2(0.f, 0.f);
+    const int64_t ntile = (n + E - 1) / E;
+    const int64_t my_tiles = blockIdx.x < ntile ? (ntile - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) mbar_init(&full[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t j) {  // tile index j of this block -> stage j % S
+        const int st = (int)(j % S);
+        const int64_t e0 = ((int64_t)blockIdx.x + j * gridDim.x) * E;
+        int64_t ev = n - e0;
+        if (ev > E) ev = E;
+        ev = (ev + 1) & ~(int64_t)1;  // even: 16-byte multiple (ld is even, so still inside the row)
+        const uint32_t row_bytes = (uint32_t)(ev * sizeof(float2));
+        mbar_arrive_expect_tx(&full[st], row_bytes * (uint32_t)K);
+        for (int a = 0; a < K; ++a)
+            bulk_copy_g2s(buf + ((size_t)st * KMAX + a) * E, A + a * ld + e0, row_bytes, &full[st]);
+    };
+    if (tid == 0)
+        for (int64_t j = 0; j < my_tiles && j < S; ++j) issue(j);
+
+    float g[NG];
 #pragma unroll
-        for (int r = 0; r < ROUNDS; ++r) {
-            float x[32];
+    for (int v = 0; v < NG; ++v) g[v] = 0.f;
+    ff lacc = ff_zero();
+    bool bad = false;
+    __shared__ int s_timeout_at;
+    if (tid == 0) s_timeout_at = -1;
+    __syncthreads();
+    int64_t timeout_at = -1;
+    for (int64_t j = 0; j < my_tiles; ++j) {
+        const int st = (int)(j % S);
+        const uint32_t parity = (uint32_t)((j / S) & 1);
+        if (!mbar_wait_bounded(&full[st], parity, 2000000000ull)) timeout_at = j;
+        if (__syncthreads_or(timeout_at >= 0 ? 1 : 0)) {
+            if (timeout_at >= 0) atomicCAS(&s_timeout_at, -1, (int)timeout_at);
+            break;
+        }
+        const int64_t e = ((int64_t)blockIdx.x + j * gridDim.x) * E + tid;
+        if (e < n) {
+            const float2* col = buf + (size_t)st * KMAX * E + tid;
+            float2 a[KMAX];
+            float ur = 0.f, ui = 0.f;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (32 * r + j < NG) x[j] = g[32 * r + j];
-                else x[j] = 0.f;
+            for (int c = 0; c < KMAX; ++c) {
+                a[c] = (c < K) ? col[c * E] : make_float2(0.f, 0.f);
+                const float2 v = sV[c];
+                ur += v.x * a[c].x - v.y * a[c].y;
+                ui += v.x * a[c].y + v.y * a[c].x;
             }
-            warp_transpose_reduce32(x);
-            sred[warp][32 * r + lane] = x[0];
+            const float I0 = ur * ur + ui * ui;
+            if (intensity_ok(I0)) {
+                lacc = ff_add_f(lacc, __logf(I0));
+                if (GRAD) {
+                    const float r = __frcp_rn(I0);
+                    const float wr = ur * r, wi = ui * r;
+#pragma unroll
+                    for (int c = 0; c < KMAX; ++c) {
+                        g[2 * c] += a[c].x * wr + a[c].y * wi;
+                        g[2 * c + 1] += a[c].x * wi - a[c].y * wr;
+                    }
+                }
+            } else {
+                bad = true;
+            }
+        }
+        __syncthreads();  // every thread is done with stage st
+        if (tid == 0 && j + S < my_tiles) {
+            fence_proxy_async_smem();
+            issue(j + S);
         }
     }
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) lacc = ff_add(lacc, ff_shfl_xor(lacc, m));
-    if (lane == 0) slred[warp] = lacc;
-    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    __syncthreads();
+    if (s_timeout_at >= 0) {
+        // a stage never completed: flag the error, then wait (bounded) for the copies of the
+        // stages still in flight so that none lands after the block has exited
+        if (tid == 0) {
+            atomicOr(status, 2);
+            atomicOr(badw, 1);
+            const int64_t j0 = s_timeout_at;
+            for (int64_t jj = j0; jj < my_tiles && jj < j0 + S; ++jj)
+                mbar_wait_bounded(&full[jj % S], (uint32_t)((jj / S) & 1), 100000000ull);
+        }
+        bad = true;
+    }
+    stream_reduce_finalize<KMAX, GRAD, true, E>(g, lacc, bad, sV, red, K, Psi, nfac, part, counter, badw, status, nll,
+                                                grad);
+}
 
-    // ---- block: fixed-order double-single sum over warps -> block partial
+// Second half of the unfused variant: one block sums the G block partials in block order and
+// adds the FP64 normalisation term (same arithmetic and order as the fused last block).
+template <int KMAX, bool GRAD>
+__global__ void __launch_bounds__(PWA_THREADS) k_nll_stream_final(
+    const float2* __restrict__ part, int G, int K, const float2* __restrict__ V, const double2* __restrict__ Psi,
+    double nfac, int* __restrict__ badw, int* __restrict__ status, double* __restrict__ nll,
+    double* __restrict__ grad) {
+    constexpr int NG = 2 * KMAX;
+    __shared__ ff sfin[PWA_THREADS];
+    __shared__ double sval[1 + NG];
+    __shared__ double2 sT[KMAX];
+    __shared__ float2 sV[KMAX];
+    __shared__ int sBad;
+    __shared__ double2 scratch[PWA_THREADS];
+    __shared__ double sS;
+    const int tid = threadIdx.x;
+    if (tid < KMAX) sV[tid] = tid < K ? V[tid] : make_float2(0.f, 0.f);
     const int NV = 1 + 2 * K;
-    float2* bp = part + (int64_t)blockIdx.x * NV;
-    if (tid == 0) {
-        ff s = ff_zero();
-        for (int w = 0; w < NW; ++w) s = ff_add(s, slred[w]);
-        bp[0] = make_float2(s.hi, s.lo);
-    }
-    if (GRAD && tid < 2 * K) {
-        ff s = ff_zero();
-        for (int w = 0; w < NW; ++w) s = ff_add_f(s, sred[w][tid]);
-        bp[1 + tid] = make_float2(s.hi, s.lo);
-    }
-    if (any_bad && tid == 0) atomicOr(badw, 1);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) sLast = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!sLast) return;
-
-    // ---- last block: sum the block partials in block order (double-single), finalise in FP64
-    __threadfence();
     const int NVu = GRAD ? NV : 1;
     const int nch = PWA_THREADS / NVu;
     if (tid < nch * NVu) {
         const int v = tid % NVu, ch = tid / NVu;
-        // blocks ch, ch + nch, ch + 2 nch, ... in increasing order
-        const int cnt = ((int)gridDim.x - ch + nch - 1) / nch;
+        const int cnt = (G - ch + nch - 1) / nch;
         sfin[tid] = ff_sum_strided(part, (int64_t)ch * NV + v, (int64_t)nch * NV, cnt);
     }
+    if (tid == 0) sBad = *badw;
     __syncthreads();
     if (tid < NVu) {
         ff s = ff_zero();
         for (int ch = 0; ch < nch; ++ch) s = ff_add(s, sfin[ch * NVu + tid]);
         sval[tid] = ff_to_double(s);
     }
-    // t_c = sum_a Psi_ac V_a  (FP64, K^2 complex multiply-adds)
-    if (tid < K) {
-        double tr = 0.0, ti = 0.0;
-        for (int a = 0; a < K; ++a) {
-            const double2 p = Psi[a * K + tid];
-            const double vr = sV[a].x, vi = sV[a].y;
-            tr += p.x * vr - p.y * vi;
-            ti += p.x * vi + p.y * vr;
-        }
-        sT[tid] = make_double2(tr, ti);
-    }
-    if (tid == 0) sLast = __ldcg(badw) != 0;  // reuse: now the non-finite flag of this evaluation
-    __syncthreads();
-    const bool isbad = sLast != 0;
+    const double S = psi_times_v<PWA_THREADS>(Psi, sV, K, sT, scratch, &sS);
+    const bool isbad = sBad != 0;
     if (tid == 0) {
-        // S = sum_c conj(V_c) t_c  (real by Hermiticity of Psi)
-        double S = 0.0;
-        for (int c = 0; c < K; ++c) S += (double)sV[c].x * sT[c].x + (double)sV[c].y * sT[c].y;
         nll[0] = isbad ? INFINITY : (-sval[0] + nfac * S);
         if (isbad) atomicOr(status, 1);
         *badw = 0;
-        *counter = 0u;
     }
     if (GRAD && tid < K) {
         grad[2 * tid] = isbad ? 0.0 : (-2.0 * sval[1 + 2 * tid] + 2.0 * nfac * sT[tid].x);
@@ -278,6 +353,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
     const int chunk = blockIdx.x;
     const int p0 = blockIdx.y * PB;
     const int NV = 1 + 2 * K;
+    const int K4 = (K + 3) & ~3;  // <= KMAX (KMAX is a multiple of 8)
 
     for (int idx = tid; idx < KMAX * PB; idx += PWA_THREADS) {
         const int a = idx / PB, p = idx % PB;
@@ -356,13 +432,19 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
         for (int r = 0; r < C::TE; ++r)
 #pragma unroll
             for (int s = 0; s < C::TP; ++s) u[r][s][0] = u[r][s][1] = 0.f;
-#pragma unroll 2
-        for (int a = 0; a < K; ++a) {
+        // rows K..K4-1 of sA and sV are zero, so the wave loop runs in steps of 4 with
+        // compile-time offsets inside each step
+        const float2* pA = sA + 2 * te;
+        const float2* pV = sV + 2 * tp;
+        for (int a0 = 0; a0 < K4; a0 += 4)
+#pragma unroll
+        for (int da = 0; da < 4; ++da) {
+            const int a = a0 + da;
             float4 av[C::TE / 2], vv[C::TP / 2];
 #pragma unroll
-            for (int r = 0; r < C::TE / 2; ++r) av[r] = *reinterpret_cast<const float4*>(sA + a * C::EA + 2 * te + 32 * r);
+            for (int r = 0; r < C::TE / 2; ++r) av[r] = *reinterpret_cast<const float4*>(pA + a * C::EA + 32 * r);
 #pragma unroll
-            for (int s = 0; s < C::TP / 2; ++s) vv[s] = *reinterpret_cast<const float4*>(sV + a * PB + 2 * tp + 32 * s);
+            for (int s = 0; s < C::TP / 2; ++s) vv[s] = *reinterpret_cast<const float4*>(pV + a * PB + 32 * s);
 #pragma unroll
             for (int r = 0; r < C::TE / 2; ++r)
 #pragma unroll
@@ -395,8 +477,8 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
                     float wr = 0.f, wi = 0.f;
                     if (pv && e0 + e + h < e_end) {
                         if (intensity_ok(I)) {
-                            lpart += logf(I);
-                            const float rc = 1.f / I;
+                            lpart += __logf(I);
+                            const float rc = __frcp_rn(I);
                             wr = ur * rc;
                             wi = ui * rc;
                         } else {
@@ -413,7 +495,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
         __syncthreads();
         // ---- GEMM2: G[a][p] += sum_e conj(A[a][e]) W[p][e]
         if (with_grad) {
-#pragma unroll 4
+#pragma unroll
             for (int e = 0; e < E; e += 2) {
                 float4 av[C::KA], wv[C::PP];
 #pragma unroll
@@ -469,30 +551,18 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_finalize(
     double* __restrict__ nll, double* __restrict__ grad, int with_grad) {
     __shared__ double sval[1 + 2 * PWA_MAX_WAVES];
     __shared__ double2 sT[PWA_MAX_WAVES];
-    __shared__ double2 sVd[PWA_MAX_WAVES];
+    __shared__ float2 sVf[PWA_MAX_WAVES];
+    __shared__ double2 scratch[PWA_THREADS];
+    __shared__ double sS;
     const int p = blockIdx.x, tid = threadIdx.x;
     const int NV = 1 + 2 * K;
     const int NVu = with_grad ? NV : 1;
-    if (tid < K) {
-        const float2 v = V[(int64_t)p * K + tid];
-        sVd[tid] = make_double2(v.x, v.y);
-    }
+    if (tid < K) sVf[tid] = V[(int64_t)p * K + tid];
     if (tid < NVu) sval[tid] = ff_to_double(ff_sum_strided(part, (int64_t)p * NV + tid, (int64_t)P * NV, nchunk));
     __syncthreads();
-    if (tid < K) {
-        double tr = 0.0, ti = 0.0;
-        for (int a = 0; a < K; ++a) {
-            const double2 ps = Psi[a * K + tid];
-            tr += ps.x * sVd[a].x - ps.y * sVd[a].y;
-            ti += ps.x * sVd[a].y + ps.y * sVd[a].x;
-        }
-        sT[tid] = make_double2(tr, ti);
-    }
-    __syncthreads();
+    const double S = psi_times_v<PWA_THREADS>(Psi, sVf, K, sT, scratch, &sS);
     const bool isbad = bad[p] != 0;
     if (tid == 0) {
-        double S = 0.0;
-        for (int c = 0; c < K; ++c) S += sVd[c].x * sT[c].x + sVd[c].y * sT[c].y;
         nll[p] = isbad ? INFINITY : (-sval[0] + nfac * S);
         if (isbad) atomicOr(status, 1);
     }
@@ -508,12 +578,12 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_finalize(
 int kmax_stream(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64; }
 int kmax_batched(int K) { return K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64; }
 
-template <int KMAX, bool GRAD, bool HOLD>
+template <int KMAX, bool GRAD, bool HOLD, bool FUSED>
 int stream_occupancy() {
     static int occ = -1;
     if (occ < 0) {
         int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nll_stream<KMAX, GRAD, HOLD>, PWA_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nll_stream<KMAX, GRAD, HOLD, FUSED>, PWA_THREADS, 0);
         occ = o > 0 ? o : 1;
     }
     return occ;
@@ -522,7 +592,10 @@ int stream_occupancy() {
 int64_t stream_grid(int64_t n, int sm_count, int occ) {
     const int64_t npairs = (n + 1) / 2;
     int64_t g = (npairs + PWA_THREADS - 1) / PWA_THREADS;
-    const int64_t cap = (int64_t)sm_count * occ;
+    int64_t cap = (int64_t)sm_count * occ;
+    // PWA_STREAM_GRID: blocks per launch (tuning), at most the workspace bound of 8 per SM
+    const char* e = getenv("PWA_STREAM_GRID");
+    if (e && atoi(e) > 0) cap = atoi(e) < 8 * sm_count ? atoi(e) : 8 * sm_count;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return g;
@@ -530,22 +603,60 @@ int64_t stream_grid(int64_t n, int sm_count, int occ) {
 
 // Register-holding variant by default for K <= 32; PWA_STREAM_HOLD=0/1 overrides (tuning).
 inline int stream_hold_override() {
-    static int v = -2;
-    if (v == -2) {
-        const char* e = getenv("PWA_STREAM_HOLD");
-        v = e ? atoi(e) : -1;
-    }
-    return v;
+    const char* e = getenv("PWA_STREAM_HOLD");
+    return e ? atoi(e) : -1;
 }
 
-template <int KMAX, bool GRAD, bool HOLD>
+// Fused (last block finalises, one launch) or split (streaming kernel + one-block finalise);
+// PWA_STREAM_FUSED=0/1 overrides the default (tuning).
+inline int stream_fused_override() {
+    const char* e = getenv("PWA_STREAM_FUSED");
+    return e ? atoi(e) : -1;
+}
+
+template <int KMAX, bool GRAD, bool HOLD, bool FUSED>
 cudaError_t stream_launch_v(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
                             double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
                             int* badw, int* status, int sm_count, cudaStream_t st) {
-    const int64_t g = stream_grid(KMAX <= 16 ? n : 2 * n, sm_count, stream_occupancy<KMAX, GRAD, HOLD>());
+    const int64_t g = stream_grid(KMAX <= 16 ? n : 2 * n, sm_count, stream_occupancy<KMAX, GRAD, HOLD, FUSED>());
     if ((size_t)g * (1 + 2 * (size_t)K) * sizeof(float2) > ws_bytes) return cudaErrorInvalidValue;
-    k_nll_stream<KMAX, GRAD, HOLD><<<(unsigned)g, PWA_THREADS, 0, st>>>(A, K, n, ld, V, Psi, nfac, (float2*)ws,
-                                                                       counter, badw, status, nll, grad);
+    k_nll_stream<KMAX, GRAD, HOLD, FUSED><<<(unsigned)g, PWA_THREADS, 0, st>>>(A, K, n, ld, V, Psi, nfac, (float2*)ws,
+                                                                              counter, badw, status, nll, grad);
+    if (FUSED) return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_nll_stream_final<KMAX, GRAD><<<1, PWA_THREADS, 0, st>>>((const float2*)ws, (int)g, K, V, Psi, nfac, badw, status,
+                                                               nll, grad);
+    return cudaGetLastError();
+}
+
+inline int stream_tma_override() {
+    const char* e = getenv("PWA_STREAM_TMA");
+    return e ? atoi(e) : -1;
+}
+
+template <int KMAX, bool GRAD>
+cudaError_t tma_launch(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                       double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
+                       int* badw, int* status, int sm_count, cudaStream_t st) {
+    using C = TmaCfg<KMAX>;
+    auto kern = k_nll_tma<KMAX, GRAD>;
+    static int occ = -1;
+    if (occ < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, C::E, C::SMEM);
+        occ = o > 0 ? o : 1;
+    }
+    const int64_t ntile = (n + C::E - 1) / C::E;
+    int64_t g = (int64_t)sm_count * occ;
+    if (g > (int64_t)sm_count * 8) g = (int64_t)sm_count * 8;  // workspace bound
+    const char* e = getenv("PWA_STREAM_GRID");
+    if (e && atoi(e) > 0 && atoi(e) < g) g = atoi(e);
+    if (g > ntile) g = ntile;
+    if (g < 1) g = 1;
+    if ((size_t)g * (1 + 2 * (size_t)K) * sizeof(float2) > ws_bytes) return cudaErrorInvalidValue;
+    kern<<<(unsigned)g, C::E, C::SMEM, st>>>(A, K, n, ld, V, Psi, nfac, (float2*)ws, counter, badw, status, nll, grad);
     return cudaGetLastError();
 }
 
@@ -553,13 +664,18 @@ template <int KMAX, bool GRAD>
 cudaError_t stream_launch(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
                           double nfac, double* nll, double* grad, void* ws, size_t ws_bytes, unsigned* counter,
                           int* badw, int* status, int sm_count, cudaStream_t st) {
+    if (stream_tma_override() == 1)
+        return tma_launch<KMAX, GRAD>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw, status,
+                                      sm_count, st);
     const int ov = stream_hold_override();
     const bool hold = ov >= 0 ? ov != 0 : KMAX <= 32;
-    if (hold)
-        return stream_launch_v<KMAX, GRAD, true>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw,
-                                                 status, sm_count, st);
-    return stream_launch_v<KMAX, GRAD, false>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, badw,
-                                              status, sm_count, st);
+    const int fo = stream_fused_override();
+    const bool fused = fo >= 0 ? fo != 0 : true;
+#define PWA_SL(H, F) stream_launch_v<KMAX, GRAD, H, F>(A, K, n, ld, V, Psi, nfac, nll, grad, ws, ws_bytes, counter, \
+                                                       badw, status, sm_count, st)
+    if (hold) return fused ? PWA_SL(true, true) : PWA_SL(true, false);
+    return fused ? PWA_SL(false, true) : PWA_SL(false, false);
+#undef PWA_SL
 }
 
 template <bool GRAD>

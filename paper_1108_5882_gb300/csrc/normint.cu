@@ -6,11 +6,12 @@
 //
 // This is a Hermitian rank-N update Psi = A diag(w) A^H / N_gen with K <= 64 and N ~ 1e7,
 // so the work is a reduction over events, not a GEMM with reuse in the output: the kernel
-// streams event tiles of E = 64 events through shared memory and gives each thread a 4 x 4
-// block of the upper triangle of Psi and an event phase.  Per event a thread issues 8 shared
-// loads for 16 complex multiply-adds (64 FFMA).
+// streams event tiles of E = 256 events through shared memory (the next tile is prefetched
+// into registers while the current one is consumed) and gives each thread a 4 x 4 block of
+// the upper triangle of Psi and an event phase.  Per event a thread issues 8 shared loads for
+// 16 complex multiply-adds (64 FFMA).
 //
-// Accumulation: FP32 per thread over a window of at most ~32 events, then folded into a
+// Accumulation: FP32 per thread over a window of about 64 events, then folded into a
 // per-thread double-single accumulator held in shared memory (v-major, conflict-free); the
 // phases and then the blocks are combined in a fixed order, and the final division and the
 // Hermitian completion are done in FP64.
@@ -20,43 +21,23 @@ namespace pwa {
 
 namespace {
 
-constexpr int NI_E = 64;  // events per tile
-
-struct NiShape {
-    int KB;      // 4x4 tile rows
-    int NT;      // upper-triangle tiles
-    int nph;     // event phases per block
-    int flush;   // tiles between flushes
-};
-
-__host__ __device__ inline NiShape ni_shape(int KMAX) {
-    NiShape s;
-    s.KB = KMAX / 4;
-    s.NT = s.KB * (s.KB + 1) / 2;
-    s.nph = PWA_THREADS / s.NT;
-    if (s.nph < 1) s.nph = 1;
-    int ev_per_tile = (NI_E + s.nph - 1) / s.nph;
-    s.flush = (32 + ev_per_tile - 1) / ev_per_tile;
-    return s;
-}
+constexpr int NI_E = 256;  // events per tile
+constexpr int NI_ES = NI_E + 1;  // padded row stride (float2)
 
 // block partial layout: part[block][KMAX*KMAX] of complex ff = 4 floats (re.hi, re.lo, im.hi, im.lo)
 template <int KMAX, bool WEIGHTED>
 __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restrict__ A, int K, int64_t n,
                                                          int64_t ld, const float* __restrict__ w,
                                                          int64_t ev_per_block, float4* __restrict__ part) {
-    constexpr NiShape S = {KMAX / 4, (KMAX / 4) * (KMAX / 4 + 1) / 2,
-                           (PWA_THREADS / ((KMAX / 4) * (KMAX / 4 + 1) / 2)) > 0
-                               ? PWA_THREADS / ((KMAX / 4) * (KMAX / 4 + 1) / 2)
-                               : 1,
-                           0};
-    constexpr int NT = S.NT;
-    constexpr int NPH = S.nph;
-    constexpr int EPT = (NI_E + NPH - 1) / NPH;
-    constexpr int FLUSH = (32 + EPT - 1) / EPT;
+    constexpr int KB = KMAX / 4;                 // 4x4 tile rows
+    constexpr int NT = KB * (KB + 1) / 2;        // upper-triangle tiles
+    constexpr int NPH = PWA_THREADS / NT > 0 ? PWA_THREADS / NT : 1;  // event phases
+    constexpr int EPT = (NI_E + NPH - 1) / NPH;  // events per thread and tile
+    constexpr int FLUSH = (64 + EPT - 1) / EPT;  // tiles per FP32 accumulation window (~64 events)
+    constexpr int LD2 = KMAX * NI_E / PWA_THREADS;  // float2 tile loads per thread
     extern __shared__ float4 smem4[];
-    float2* sA = reinterpret_cast<float2*>(smem4);  // [KMAX][NI_E + 1]
-    float* sw = reinterpret_cast<float*>(sA + KMAX * (NI_E + 1));  // [NI_E]
+    float2* sA = reinterpret_cast<float2*>(smem4);              // [KMAX][NI_ES]
+    float* sw = reinterpret_cast<float*>(sA + KMAX * NI_ES);    // [NI_E]
     float* sacc = sw + NI_E;  // [64][PWA_THREADS]: 16 complex ff per thread, v-major
 
     const int tid = threadIdx.x;
@@ -66,7 +47,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     // tile t -> (ti, tj) with ti <= tj, row-major over the upper triangle
     int ti = 0, tj = 0;
     {
-        int r = t, row = 0, len = S.KB;
+        int r = t, row = 0, len = KB;
         while (r >= len) { r -= len; ++row; --len; }
         ti = row;
         tj = row + r;
@@ -77,30 +58,43 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     int64_t e_end = e_begin + ev_per_block;
     if (e_end > n) e_end = n;
 
+    // register prefetch of the next tile: element idx = tid + 256 j -> row idx / NI_E, event idx % NI_E
+    float2 pre[LD2];
+    float prew = 0.f;
+    auto load_tile = [&](int64_t e0) {
+#pragma unroll
+        for (int j = 0; j < LD2; ++j) {
+            const int idx = tid + PWA_THREADS * j;
+            const int a = idx / NI_E, e = idx % NI_E;
+            pre[j] = (a < K && e0 + e < e_end) ? __ldg(A + a * ld + e0 + e) : make_float2(0.f, 0.f);
+        }
+        if (WEIGHTED) prew = (e0 + tid < e_end) ? __ldg(w + e0 + tid) : 0.f;  // NI_E == PWA_THREADS
+    };
+
     float acc[32];
 #pragma unroll
     for (int v = 0; v < 32; ++v) acc[v] = 0.f;
     int since_flush = 0;
 
+    if (e_begin < e_end) load_tile(e_begin);
     for (int64_t e0 = e_begin; e0 < e_end; e0 += NI_E) {
-        __syncthreads();
-        // stage the tile: KMAX rows x 64 events (float2), zero beyond n or K
-        for (int idx = tid; idx < KMAX * NI_E; idx += PWA_THREADS) {
-            const int a = idx / NI_E, e = idx % NI_E;
-            float2 v = make_float2(0.f, 0.f);
-            if (a < K && e0 + e < e_end) v = __ldg(A + a * ld + e0 + e);
-            sA[a * (NI_E + 1) + e] = v;
+        __syncthreads();  // previous tile consumed
+#pragma unroll
+        for (int j = 0; j < LD2; ++j) {
+            const int idx = tid + PWA_THREADS * j;
+            sA[(idx / NI_E) * NI_ES + idx % NI_E] = pre[j];
         }
-        if (WEIGHTED)
-            for (int e = tid; e < NI_E; e += PWA_THREADS) sw[e] = (e0 + e < e_end) ? __ldg(w + e0 + e) : 0.f;
+        if (WEIGHTED) sw[tid] = prew;
         __syncthreads();
+        if (e0 + NI_E < e_end) load_tile(e0 + NI_E);
         if (active) {
+#pragma unroll 2
             for (int e = ph; e < NI_E; e += NPH) {
                 float2 xa[4], xb[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    xa[r] = sA[(4 * ti + r) * (NI_E + 1) + e];
-                    xb[r] = sA[(4 * tj + r) * (NI_E + 1) + e];
+                    xa[r] = sA[(4 * ti + r) * NI_ES + e];
+                    xb[r] = sA[(4 * tj + r) * NI_ES + e];
                 }
                 if (WEIGHTED) {
                     const float we = sw[e];
@@ -148,7 +142,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
             re = ff_add(re, ff{sacc[(4 * q) * PWA_THREADS + th], sacc[(4 * q + 1) * PWA_THREADS + th]});
             im = ff_add(im, ff{sacc[(4 * q + 2) * PWA_THREADS + th], sacc[(4 * q + 3) * PWA_THREADS + th]});
         }
-        int r2 = tt, row = 0, len = S.KB;
+        int r2 = tt, row = 0, len = KB;
         while (r2 >= len) { r2 -= len; ++row; --len; }
         const int a = 4 * row + q / 4, b = 4 * (row + r2) + q % 4;
         bp[a * KMAX + b] = make_float4(re.hi, re.lo, im.hi, im.lo);
@@ -184,7 +178,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint_final(const float4* __r
 
 template <int KMAX>
 size_t ni_smem() {
-    return sizeof(float2) * KMAX * (NI_E + 1) + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
+    return sizeof(float2) * KMAX * NI_ES + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
 }
 
 template <int KMAX>

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/pwa.h"
 
@@ -26,6 +27,10 @@ struct pwa_handle {
     int* status = nullptr;         // sticky device status word (bit 0: non-finite intensity)
     int* bad = nullptr;            // per-parameter-set non-finite flags [bad_cap]
     int bad_cap = 0;
+    void* fitws = nullptr;         // batched-fit state and evaluation buffers
+    size_t fitws_bytes = 0;
+    cudaStream_t fit_stream = nullptr;  // capturable stream the fitter runs on
+    cudaEvent_t fit_event = nullptr;
 };
 
 namespace pwa {
@@ -135,6 +140,18 @@ size_t nll_workspace(int K, int64_t n, int P, int sm_count);
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
                        unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
+
+size_t fit_workspace(int P_tot, int m);
+size_t fit_eval_bytes(int P, int K);
+cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
+                            float2* Vt, cudaStream_t s);
+cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
+                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s);
+cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaStream_t s);
+cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
+                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int K_of_p[],
+                             cudaStream_t s);
+cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s);
 
 size_t generate_workspace(int64_t n_cand);
 cudaError_t launch_generate(const WaveTable& wt, const float2* V, uint64_t seed, uint32_t stream, int64_t cand0,

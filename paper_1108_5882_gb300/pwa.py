@@ -90,10 +90,30 @@ def _register_optional(lib):
     lib.pwa_envelope.argtypes = [ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int]
     lib.pwa_envelope.restype = ctypes.c_double
+    lib.pwa_fit_default_opts.argtypes = [ctypes.POINTER(pwa_fit_opts)]
+    lib.pwa_fit_default_opts.restype = None
+    lib.pwa_fit_batch.argtypes = [_vp, ctypes.POINTER(pwa_fit_desc), ctypes.c_int, ctypes.POINTER(pwa_fit_opts),
+                                  ctypes.POINTER(pwa_fit_result), _vp]
+    lib.pwa_fit_batch.restype = S
     if hasattr(lib, "pwa_generate"):
         lib.pwa_generate.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_uint64,
                                      ctypes.c_uint32, _i64, _i64, ctypes.c_double, _vp, _i64, _i64, _vp, _vp]
         lib.pwa_generate.restype = S
+
+
+class pwa_fit_desc(ctypes.Structure):
+    _fields_ = [("A", _vp), ("K", ctypes.c_int), ("n", _i64), ("ld", _i64), ("Psi", _vp), ("n_factor", ctypes.c_double),
+                ("P", ctypes.c_int), ("V0", _vp), ("V_out", _vp)]
+
+
+class pwa_fit_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("history", ctypes.c_int), ("gtol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class pwa_fit_result(ctypes.Structure):
+    _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("evaluations", ctypes.c_int), ("status", ctypes.c_int)]
 
 
 def status_string(s: int) -> str:
@@ -241,6 +261,40 @@ def _gen(self, waves, V, seed, stream_id, cand0, n_cand, envelope, kin, max_out,
 
 
 Handle.pwa_generate = _gen
+
+
+def fit_opts(**kw) -> pwa_fit_opts:
+    o = pwa_fit_opts()
+    load().pwa_fit_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _fit_batch(self, fits, opts=None, stream=None):
+    """fits: list of dicts with A (complex64 [K][ld]), n, Psi (complex128 [K][K]), n_factor,
+    V0 (complex64 [P][K]) and optionally V_out (complex128 [P][K]).  Returns a list of
+    per-start result dicts in (fit, start) order."""
+    arr = (pwa_fit_desc * len(fits))()
+    P_tot = 0
+    for i, f in enumerate(fits):
+        _check_cuda(f["A"], "A", torch.complex64)
+        _check_cuda(f["Psi"], "Psi", torch.complex128)
+        _check_cuda(f["V0"], "V0", torch.complex64)
+        _check_cuda(f.get("V_out"), "V_out", torch.complex128)
+        K, ld = f["A"].shape
+        P = f["V0"].shape[0]
+        arr[i] = pwa_fit_desc(f["A"].data_ptr(), K, int(f["n"]), ld, f["Psi"].data_ptr(), float(f["n_factor"]), P,
+                              f["V0"].data_ptr(), f["V_out"].data_ptr() if f.get("V_out") is not None else None)
+        P_tot += P
+    res = (pwa_fit_result * P_tot)()
+    o = opts if opts is not None else fit_opts()
+    self._chk(self.lib.pwa_fit_batch(self.h, arr, len(fits), ctypes.byref(o), res, _stream_ptr(stream)))
+    return [dict(nll=r.nll, grad_max=r.grad_max, iterations=r.iterations, evaluations=r.evaluations, status=r.status)
+            for r in res]
+
+
+Handle.pwa_fit_batch = _fit_batch
 
 
 def waves_from(ws) -> list[tuple[int, int, float, float]]:
