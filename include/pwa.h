@@ -215,6 +215,24 @@ PWA_API void pwa_fit_default_opts(pwa_fit_opts* opts);
 PWA_API pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits,
                                  const pwa_fit_opts* opts, pwa_fit_result* results, void* stream);
 
+/* -lnL and its gradient for ONE parameter set (P = 1) with no device allocation at all: no
+ * handle, no workspace, no cudaMalloc / cudaFree, for callers that cannot allocate device
+ * memory (inside a stream capture they do not own, under a memory manager that forbids
+ * allocation after start-up, or as a plug-in of a program that owns all device memory).  The
+ * paper has no counterpart; this is an interface convenience.
+ *   Arguments, layouts and results as pwa_nll_grad with P = 1, on the CURRENT device.
+ *   Scratch: a static device array of 1,056,768 + 256 bytes compiled into the library (held
+ *   by every GPU that loads it until exit) supports K <= PWA_MAX_WAVES and at most 1024 blocks
+ *   per launch; larger K is rejected with PWA_ERR_INVALID_ARG (message via pwa_last_error(NULL)).
+ *   The first call on a device looks up the scratch's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture.
+ *   Every call shares the scratch: calls ordered on one stream are safe (each call clears the
+ *   scratch's counter and flag words on its stream), calls that overlap on the GPU race.
+ *   A set that meets I_i <= 0 or a non-finite intensity gets nll = +inf and a zero gradient. */
+PWA_API pwa_status pwa_nll_grad_noalloc(const float* A, int K, int64_t n, int64_t ld, const float* V,
+                                        const double* Psi, double n_factor, double* nll,
+                                        double* grad, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

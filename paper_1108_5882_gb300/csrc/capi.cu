@@ -141,6 +141,13 @@ pwa_status nll_common(pwa_handle* h, const float* A, int K, int64_t n, int64_t l
 
 }  // namespace
 
+namespace pwa {
+void record_global_error(const char* msg) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = msg;
+}
+}  // namespace pwa
+
 extern "C" {
 
 int pwa_abi_version(void) { return PWA_ABI_VERSION; }

@@ -839,7 +839,40 @@ int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const flo
     return best;
 }
 
+// One parameter set with caller-provided scratch and a cap on the number of blocks (used by
+// the allocation-free entry point): the fused streaming kernel, register-holding variant.
+template <int KMAX>
+cudaError_t stream_launch_capped(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                                 double nfac, double* nll, double* grad, float2* part, size_t part_bytes,
+                                 unsigned* counter, int* badw, int* status, int max_blocks, int sm_count,
+                                 cudaStream_t st) {
+    constexpr bool HOLD = KMAX <= 32;
+    int64_t g = stream_grid(KMAX <= 16 ? n : 2 * n, sm_count, stream_occupancy<KMAX, true, HOLD, true>());
+    if (g > max_blocks) g = max_blocks;
+    if ((size_t)g * (1 + 2 * (size_t)K) * sizeof(float2) > part_bytes) return cudaErrorInvalidValue;
+    k_nll_stream<KMAX, true, HOLD, true><<<(unsigned)g, PWA_THREADS, 0, st>>>(A, K, n, ld, V, Psi, nfac, part, counter,
+                                                                             badw, status, nll, grad);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t ld, const float2* V,
+                                    const double2* Psi, double nfac, double* nll, double* grad, float2* part,
+                                    size_t part_bytes, unsigned* counter, int* badw, int* status, int max_blocks,
+                                    int sm_count, cudaStream_t st) {
+#define PWA_SC(KM) stream_launch_capped<KM>(A, K, n, ld, V, Psi, nfac, nll, grad, part, part_bytes, counter, badw, \
+                                            status, max_blocks, sm_count, st)
+    switch (kmax_stream(K)) {
+        case 4: return PWA_SC(4);
+        case 8: return PWA_SC(8);
+        case 16: return PWA_SC(16);
+        case 32: return PWA_SC(32);
+        case 48: return PWA_SC(48);
+        default: return PWA_SC(64);
+    }
+#undef PWA_SC
+}
 
 size_t nll_workspace(int K, int64_t n, int P, int sm_count) {
     const size_t NV = 1 + 2 * (size_t)K;

@@ -1,0 +1,104 @@
+// -lnL and its gradient for one parameter set without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a CUDA stream capture it does not
+// own, host code under a memory manager that forbids allocations after start-up, or plug-ins
+// of a larger program that owns all device memory.  pwa_nll_grad needs a handle, and both the
+// handle and its workspace are allocated with cudaMalloc.  pwa_nll_grad_noalloc needs neither:
+// its scratch (block partial sums, the completion counter, the non-finite flag) lives in the
+// file-scope device array below, which every GPU that loads the library holds until exit.
+//
+// Limits: K <= PWA_MAX_WAVES and at most NOALLOC_MAX_BLOCKS blocks per launch (the launch is
+// capped there; any n is accepted).  The scratch is shared by every call on a device and keeps
+// the last call's contents: each call clears the counter and flag words on its stream before
+// its kernel runs, so calls ordered on one stream are safe, while calls that overlap on the
+// GPU (different streams, different host threads) race on the scratch and give wrong results.
+#include <cstring>
+#include <mutex>
+
+#include "pwa_internal.cuh"
+
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 1024;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr size_t NOALLOC_HEADER = 256;  // counter, flag, status words
+constexpr size_t NOALLOC_PART_BYTES = sizeof(float2) * (size_t)NOALLOC_MAX_BLOCKS * (1 + 2 * PWA_MAX_WAVES);
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_PART_BYTES;  // 1,056,768 + 256 bytes
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array and the SM count of the current device, looked up once
+// per device (with that device current).  In host code the symbol g_noalloc_scratch is only a
+// host-side stand-in: its device address has to come from cudaGetSymbolAddress.
+cudaError_t noalloc_setup(int dev, void** ptr, int* sms) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_sms[dev] = n > 0 ? n : 1;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return cudaSuccess;
+}
+
+pwa_status noalloc_fail(pwa_status st, const char* msg) {
+    pwa::record_global_error(msg);
+    return st;
+}
+
+}  // namespace
+
+extern "C" PWA_API pwa_status pwa_nll_grad_noalloc(const float* A, int K, int64_t n, int64_t ld, const float* V,
+                                                   const double* Psi, double n_factor, double* nll, double* grad,
+                                                   void* stream) {
+    if (K < 1 || K > PWA_MAX_WAVES) return noalloc_fail(PWA_ERR_INVALID_ARG, "pwa_nll_grad_noalloc: K outside [1, 64]");
+    if (n < 0 || ld < n || (ld & 1) || (int64_t)K * ld > ((int64_t)1 << 40))
+        return noalloc_fail(PWA_ERR_INVALID_ARG, "pwa_nll_grad_noalloc: need 0 <= n <= ld, ld even");
+    if ((n > 0 && !A) || !V || !Psi || !nll || !grad)
+        return noalloc_fail(PWA_ERR_INVALID_ARG, "pwa_nll_grad_noalloc: NULL array argument");
+    if ((n > 0 && (reinterpret_cast<uintptr_t>(A) & 15u)) || (reinterpret_cast<uintptr_t>(Psi) & 15u) ||
+        (reinterpret_cast<uintptr_t>(V) & 7u))
+        return noalloc_fail(PWA_ERR_INVALID_ARG, "pwa_nll_grad_noalloc: misaligned array");
+    if (!(n_factor == n_factor) || n_factor > 1e300 || n_factor < -1e300)
+        return noalloc_fail(PWA_ERR_INVALID_ARG, "pwa_nll_grad_noalloc: n_factor not finite");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return noalloc_fail(PWA_ERR_NO_DEVICE, "pwa_nll_grad_noalloc: no usable current device");
+    }
+    void* base = nullptr;
+    int sms = 1;
+    cudaError_t e = noalloc_setup(dev, &base, &sms);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(PWA_ERR_CUDA, "pwa_nll_grad_noalloc: cudaGetSymbolAddress of the scratch failed");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* b = reinterpret_cast<unsigned char*>(base);
+    unsigned* counter = reinterpret_cast<unsigned*>(b);
+    int* badw = reinterpret_cast<int*>(b + 4);
+    int* status = reinterpret_cast<int*>(b + 8);
+    float2* part = reinterpret_cast<float2*>(b + NOALLOC_HEADER);
+    // the previous call's words may be left set (e.g. the status bit of a non-finite set)
+    e = cudaMemsetAsync(b, 0, 16, st);
+    if (e == cudaSuccess)
+        e = pwa::launch_nll_grad_scratch(reinterpret_cast<const float2*>(A), K, n, ld,
+                                         reinterpret_cast<const float2*>(V), reinterpret_cast<const double2*>(Psi),
+                                         n_factor, nll, grad, part, NOALLOC_PART_BYTES, counter, badw, status,
+                                         NOALLOC_MAX_BLOCKS, sms, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(PWA_ERR_CUDA, "pwa_nll_grad_noalloc: launch failed");
+    }
+    return PWA_OK;
+}

@@ -137,9 +137,16 @@ cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const 
                            double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st);
 
 size_t nll_workspace(int K, int64_t n, int P, int sm_count);
+cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t ld, const float2* V,
+                                    const double2* Psi, double nfac, double* nll, double* grad, float2* part,
+                                    size_t part_bytes, unsigned* counter, int* badw, int* status, int max_blocks,
+                                    int sm_count, cudaStream_t st);
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
                        unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
+
+// record a message for pwa_last_error(NULL) (calls without a handle)
+void record_global_error(const char* msg);
 
 size_t fit_workspace(int P_tot, int m);
 size_t fit_eval_bytes(int P, int K);
