@@ -114,6 +114,25 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def measured_traffic(kernel_tag):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None when
+    the kernel's sources changed since that capture (their sha256 no longer matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        hsh = hashlib.sha256()
+        for f in d["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                hsh.update(fh.read())
+        if hsh.hexdigest() != d["sources_sha256"]:
+            return None
+        return float(d["dram_bytes_read"]) + float(d["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -312,7 +331,7 @@ def run_ours(args, world, rank, local):
                 "what": "pinned H2D of data+MC kinematics, amplitudes(data, MC), Psi, -lnL+grad, D2H of nll+grad"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_nll_stream<16,true>", "bytes_per_launch": alg_bytes,
+                     "traffic": measured_traffic("k_nll_stream_scale"), "kernel": "k_nll_stream<16,true,true,true>", "bytes_per_launch": alg_bytes,
                      "kernel_us": kernel_ms * 1e3, "peak_kind": f"{peak_kind} (copy bandwidth)"},
         "clocks": sampler.summary(),
         "status": pwa.status_string(ok), "wall_s_timed": wall,
