@@ -48,6 +48,7 @@ extern "C" {
 
 #define PWA_ABI_VERSION 1
 #define PWA_MAX_WAVES 64
+#define PWA_MAX_FLOAT 8   /* floating shape parameters per likelihood (pwa_nll_grad_shape) */
 
 typedef enum pwa_status {
     PWA_OK = 0,
@@ -214,6 +215,63 @@ PWA_API void pwa_fit_default_opts(pwa_fit_opts* opts);
  * any stream capture).  Returns PWA_OK once every start has stopped (see result.status). */
 PWA_API pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits,
                                  const pwa_fit_opts* opts, pwa_fit_result* results, void* stream);
+
+/* -lnL and its gradient when resonance masses and widths float.  Sec. 2: then neither the MC
+ * bracket of Eq. 3 nor the per-event products can be precomputed, so the normalisation is the
+ * MC sum itself (streamed) and the amplitudes of the floating waves are recomputed by the caller
+ * (pwa_amplitudes with derivatives) at every new (M, Gamma):
+ *   f = -sum_i ln|u_i|^2 + (n_factor / n_gen) sum_j w_j |u_j|^2,   u = sum_a V_a A_a,
+ *   grad[2c], grad[2c+1] = d f / d Re V_c, d f / d Im V_c,
+ *   grad[2K + q] = d f / d theta_q = -2 sum_i Re(conj(u_i) V_r dA_iq)/I_i
+ *                                    + 2 (n_factor/n_gen) sum_j w_j Re(conj(u_j) V_r dA_jq),
+ * for floating parameter q of wave r = float_wave[q] with derivative row dA_q = dA_r/dtheta_q.
+ *   A, A_mc   complex float [K][ld], [K][ld_mc]   current amplitudes of data and MC events
+ *   dA, dA_mc complex float [F][ld], [F][ld_mc]   derivative rows (NULL if F = 0)
+ *   w_mc      float [n_mc] or NULL (acceptance flags / weights), n_gen as pwa_normint
+ *   float_wave HOST int [F], 0 <= F <= PWA_MAX_FLOAT
+ *   V complex float [K]; nll double [1]; grad double [2K + F] (outputs, device)
+ * One parameter set.  Deterministic (fixed-order double-single sums, FP64 combination). */
+PWA_API pwa_status pwa_nll_grad_shape(pwa_handle* h, const float* A, const float* dA, int K,
+                                      int64_t n, int64_t ld, const float* A_mc, const float* dA_mc,
+                                      int64_t n_mc, int64_t ld_mc, const float* w_mc, double n_gen,
+                                      const int* float_wave, int F, const float* V,
+                                      double n_factor, double* nll, double* grad, void* stream);
+
+/* Fits with floating resonance masses and widths, many channels (independent fits of uneven
+ * wave and event counts) at once.  Sec. 2: with floating shape parameters the amplitudes are
+ * recomputed every iteration and the MC normalisation is summed anew (pwa_nll_grad_shape);
+ * Sec. 4: at least three or four free parameters per resonance.  One start per channel:
+ * x = (Re V, Im V, theta), theta the floating masses/widths; each iteration recomputes the
+ * floating waves' amplitudes and derivatives for data and MC from the device trial point,
+ * evaluates the streamed likelihood and takes one L-BFGS step (widths and masses kept above
+ * 1e-3 GeV by a fraction-to-the-boundary step limit).  The channels' chains run on parallel
+ * streams captured into one CUDA graph per check_every iterations. */
+typedef struct pwa_shape_fit_desc {
+    const pwa_wave* waves;      /* HOST [K]: J, lambda and the starting mass/width of each wave */
+    int K;
+    const float* kin;           /* data kinematics float [3][ld] (device) */
+    int64_t n;
+    int64_t ld;
+    const float* kin_mc;        /* MC kinematics float [3][ld_mc] (device) */
+    int64_t n_mc;
+    int64_t ld_mc;
+    const float* w_mc;          /* float [n_mc] or NULL */
+    double n_gen;               /* generated MC events */
+    double n_factor;            /* N_data for the extended likelihood */
+    int F;                      /* floating parameters, 0..PWA_MAX_FLOAT, 2K + F <= 128 */
+    const int* float_wave;      /* HOST [F]: wave index of each floating parameter */
+    const int* float_kind;      /* HOST [F]: 0 = mass, 1 = width */
+    float* A;                   /* work: complex float [K][ld] (device, overwritten) */
+    float* A_mc;                /* work: complex float [K][ld_mc] */
+    float* dA;                  /* work: complex float [F][ld] */
+    float* dA_mc;               /* work: complex float [F][ld_mc] */
+    const float* V0;            /* complex float [K] starting V (device) */
+    double* x_out;              /* double [2K + F] result (Re V_0, Im V_0, ..., theta) or NULL */
+} pwa_shape_fit_desc;
+
+PWA_API pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, int n_fits,
+                                       const pwa_fit_opts* opts, pwa_fit_result* results,
+                                       void* stream);
 
 /* -lnL and its gradient for ONE parameter set (P = 1) with no device allocation at all: no
  * handle, no workspace, no cudaMalloc / cudaFree, for callers that cannot allocate device

@@ -80,6 +80,12 @@ def _register_fit(lib):
     lib.orc_generate.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                  _i64, ctypes.c_double, _fp, _i64, _i64, _dp]
     lib.orc_generate.restype = ctypes.c_int64
+    lib.orc_nll_grad_shape.argtypes = [ctypes.c_int, _i64, _fp, _fp, _i64, _i64, _fp, _fp, _i64, _fp, ctypes.c_double,
+                                       _ip, ctypes.c_int, _dp, ctypes.c_double, _dp, _dp, _dp]
+    lib.orc_nll_grad_shape.restype = ctypes.c_int
+    lib.orc_nll_shape_from_kin.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _i64, _fp, _i64, _fp, ctypes.c_double,
+                                           _dp, ctypes.c_double]
+    lib.orc_nll_shape_from_kin.restype = ctypes.c_double
 
 
 def _ptr(a, t):
@@ -205,3 +211,45 @@ def generate(J, lam, M, W, V, seed, stream, cand0, n_cand, C, max_out):
                           kin.shape[1], int(max_out), _ptr(mr, _dp))
     n_out = min(int(na), int(max_out))
     return np.ascontiguousarray(kin[:, :n_out]), int(na), float(mr[0])
+
+
+# ------------------------------------------------------------------ floating masses/widths -----
+
+def nll_grad_shape(A, dA, A_mc, dA_mc, fwave, V, n_factor=None, w_mc=None, n_gen=None):
+    """f, grad_V [2K], grad_shape [F] with the streamed MC normalisation (floating M, Gamma).
+
+    A [K][n], dA [F][n], A_mc [K][n_mc], dA_mc [F][n_mc]: complex64; fwave: wave index per
+    floating parameter; V complex [K]."""
+    lib = _load()
+    K, n = A.shape
+    n_mc = A_mc.shape[1]
+    F = len(fwave)
+    Af, dAf = _c64_as_f32(A), _c64_as_f32(dA.reshape(F, n))
+    Amf, dAmf = _c64_as_f32(A_mc), _c64_as_f32(dA_mc.reshape(F, n_mc))
+    fw = np.ascontiguousarray(fwave, dtype=np.int32)
+    Vd = np.ascontiguousarray(V, dtype=np.complex128).reshape(K)
+    wf = None if w_mc is None else np.ascontiguousarray(w_mc, dtype=np.float32)
+    nll = np.zeros(1)
+    gV = np.zeros(2 * K)
+    gS = np.zeros(max(F, 1))
+    bad = lib.orc_nll_grad_shape(K, n, _ptr(Af, _fp), _ptr(dAf, _fp), n, n_mc, _ptr(Amf, _fp), _ptr(dAmf, _fp), n_mc,
+                                 _ptr(wf, _fp), float(n_mc if n_gen is None else n_gen), _ptr(fw, _ip), F,
+                                 _ptr(Vd, _dp), float(n if n_factor is None else n_factor), _ptr(nll, _dp),
+                                 _ptr(gV, _dp), _ptr(gS, _dp))
+    return nll[0], gV, gS[:F], bad
+
+
+def nll_shape_from_kin(J, lam, M, W, kin, kin_mc, V, n_factor=None, n_gen=None):
+    """The floating-parameter objective in FP64 straight from the kinematics."""
+    lib = _load()
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    kin = np.ascontiguousarray(kin, dtype=np.float32)
+    kin_mc = np.ascontiguousarray(kin_mc, dtype=np.float32)
+    Vd = np.ascontiguousarray(V, dtype=np.complex128)
+    n, n_mc = kin.shape[1], kin_mc.shape[1]
+    return lib.orc_nll_shape_from_kin(J.shape[0], _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), n,
+                                      _ptr(kin, _fp), n_mc, _ptr(kin_mc, _fp), float(n_mc if n_gen is None else n_gen),
+                                      _ptr(Vd, _dp), float(n if n_factor is None else n_factor))

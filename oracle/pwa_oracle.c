@@ -229,3 +229,89 @@ double orc_nll_double_sum(int K, int64_t n, const float* A, int64_t ld, const do
         }
     return (double)(-lnsum + (long double)n_factor * norm);
 }
+
+/* ---------- floating resonance parameters (streamed MC normalisation) -------------------- */
+
+/* When masses and widths float, Psi cannot be precomputed (Sec. 2, the remark after Eq. 3) and
+ * the normalisation is the MC sum itself:
+ *   f(V, theta) = -sum_i ln|u_i|^2 + (n_factor / n_gen) sum_j w_j |u_j|^2,  u = sum_a V_a A_a.
+ * Gradients: g_c = 2 df/dconj(V_c) (re, im) and, for each floating parameter q of wave r_q with
+ * derivative rows dA_q = dA_{r_q}/dtheta_q,
+ *   df/dtheta_q = -2 sum_i Re(conj(u_i) V_r dA_iq)/I_i + 2 (n_factor/n_gen) sum_j w_j Re(conj(u_j) V_r dA_jq).
+ * A, A_mc: complex64 [K][ld]; dA, dA_mc: complex64 [F][ld]; w_mc may be NULL.
+ * Outputs: *nll, grad_V [2K], grad_shape [F]; returns 1 if some data event has I <= 0. */
+int orc_nll_grad_shape(int K, int64_t n, const float* A, const float* dA, int64_t ld, int64_t n_mc,
+                       const float* A_mc, const float* dA_mc, int64_t ld_mc, const float* w_mc,
+                       double n_gen, const int* fwave, int F, const double* Vd, double n_factor,
+                       double* nll, double* grad_V, double* grad_shape) {
+    const cplx* V = (const cplx*)Vd;
+    nsum lsum = {0, 0}, ssum = {0, 0};
+    nsum* gd = (nsum*)calloc((size_t)(2 * K + F), sizeof(nsum));  /* data sums */
+    nsum* gm = (nsum*)calloc((size_t)(2 * K + F), sizeof(nsum));  /* MC sums */
+    cplx* Ai = (cplx*)malloc(sizeof(cplx) * (size_t)K);
+    int bad = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t cnt = pass == 0 ? n : n_mc;
+        const float* AA = pass == 0 ? A : A_mc;
+        const float* DD = pass == 0 ? dA : dA_mc;
+        const int64_t L = pass == 0 ? ld : ld_mc;
+        nsum* acc = pass == 0 ? gd : gm;
+        for (int64_t i = 0; i < cnt; ++i) {
+            cplx u = 0.0;
+            for (int a = 0; a < K; ++a) {
+                Ai[a] = AA[2 * ((int64_t)a * L + i)] + I * AA[2 * ((int64_t)a * L + i) + 1];
+                u += V[a] * Ai[a];
+            }
+            double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
+            cplx wgt;
+            if (pass == 0) {
+                if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; continue; }
+                nsum_add(&lsum, log(Ii));
+                wgt = u / Ii;
+            } else {
+                double wj = w_mc ? (double)w_mc[i] : 1.0;
+                nsum_add(&ssum, wj * Ii);
+                wgt = wj * u;
+            }
+            for (int c = 0; c < K; ++c) {
+                cplx t = conj(Ai[c]) * wgt;
+                nsum_add(&acc[2 * c], creal(t));
+                nsum_add(&acc[2 * c + 1], cimag(t));
+            }
+            for (int q = 0; q < F; ++q) {
+                cplx d = DD[2 * ((int64_t)q * L + i)] + I * DD[2 * ((int64_t)q * L + i) + 1];
+                nsum_add(&acc[2 * K + q], creal(conj(wgt) * V[fwave[q]] * d));
+            }
+        }
+    }
+    const double sc = n_factor / n_gen;
+    *nll = bad ? INFINITY : (-nsum_get(&lsum) + sc * nsum_get(&ssum));
+    for (int v = 0; v < 2 * K; ++v) grad_V[v] = bad ? 0.0 : (-2.0 * nsum_get(&gd[v]) + 2.0 * sc * nsum_get(&gm[v]));
+    for (int q = 0; q < F; ++q)
+        grad_shape[q] = bad ? 0.0 : (-2.0 * nsum_get(&gd[2 * K + q]) + 2.0 * sc * nsum_get(&gm[2 * K + q]));
+    free(gd); free(gm); free(Ai);
+    return bad;
+}
+
+/* The same objective evaluated in FP64 directly from the kinematics (amplitudes recomputed
+ * in double precision for the given masses and widths); used by the finite-difference pins. */
+double orc_nll_shape_from_kin(int K, const int* J, const int* lam, const double* M, const double* W,
+                              int64_t n, const float* kin, int64_t n_mc, const float* kin_mc,
+                              double n_gen, const double* Vd, double n_factor) {
+    const cplx* V = (const cplx*)Vd;
+    nsum lsum = {0, 0}, ssum = {0, 0};
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t cnt = pass == 0 ? n : n_mc;
+        const float* kk = pass == 0 ? kin : kin_mc;
+        for (int64_t i = 0; i < cnt; ++i) {
+            double m = kk[i], ct = kk[cnt + i], ph = kk[2 * cnt + i];
+            cplx u = 0.0;
+            for (int a = 0; a < K; ++a)
+                u += V[a] * orc_bw(m, M[a], W[a]) * orc_legendre(J[a], ct) * cexp(I * (lam[a] * ph));
+            double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
+            if (pass == 0) nsum_add(&lsum, log(Ii));
+            else nsum_add(&ssum, Ii);
+        }
+    }
+    return -nsum_get(&lsum) + n_factor / n_gen * nsum_get(&ssum);
+}

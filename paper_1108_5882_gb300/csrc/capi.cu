@@ -139,6 +139,89 @@ pwa_status nll_common(pwa_handle* h, const float* A, int K, int64_t n, int64_t l
     return PWA_OK;
 }
 
+
+// The fitter runs on a handle-owned non-blocking (capturable) stream ordered after the
+// caller's stream; the fit calls return after that stream has drained.
+pwa_status fit_stream_begin(pwa_handle* h, void* stream, cudaStream_t* out) {
+    if (!h->fit_stream) {
+        cudaError_t ce = cudaStreamCreateWithFlags(&h->fit_stream, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->fit_event, cudaEventDisableTiming);
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream");
+    }
+    cudaError_t ce = cudaEventRecord(h->fit_event, (cudaStream_t)stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->fit_stream, h->fit_event, 0);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream ordering");
+    *out = h->fit_stream;
+    return PWA_OK;
+}
+
+// One eager iteration (tile-shape selection happens outside any capture), then check_every
+// iterations per captured graph replay until no start is running.  Bounded: every iteration
+// evaluates once and a start stops after max_iter accepted steps.
+template <class Iter>
+cudaError_t run_fit_loop(pwa_handle* h, cudaStream_t s, const pwa_fit_opts& o, int P_tot, int m, Iter iteration) {
+    cudaError_t e = iteration();
+    if (e != cudaSuccess) return e;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool graph_ok = false;
+    if (o.use_graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusNone &&
+            cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaError_t ce = cudaSuccess;
+            for (int it = 0; it < o.check_every && ce == cudaSuccess; ++it) ce = iteration();
+            cudaError_t ee = cudaStreamEndCapture(s, &graph);
+            if (ce == cudaSuccess && ee == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+                graph_ok = true;
+            cudaGetLastError();
+        }
+    }
+    int* running_h = nullptr;
+    if (cudaMallocHost(&running_h, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        running_h = nullptr;
+    }
+    int running_local = 1;
+    int* running = running_h ? running_h : &running_local;
+    const long long max_loops = 60LL * (long long)o.max_iter + 100;
+    long long loops = 1;
+    while (e == cudaSuccess) {
+        e = pwa::fit_launch_count(h->fitws, P_tot, m, running, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || *running == 0 || loops >= max_loops) break;
+        if (graph_ok) {
+            e = cudaGraphLaunch(exec, s);
+        } else {
+            for (int it = 0; it < o.check_every && e == cudaSuccess; ++it) e = iteration();
+        }
+        loops += o.check_every;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (running_h) cudaFreeHost(running_h);
+    return e;
+}
+
+pwa_status grow_fitws(pwa_handle* h, size_t need) {
+    if (need > h->fitws_bytes) {
+        if (h->fitws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->fitws);
+            h->fitws = nullptr;
+            h->fitws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->fitws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PWA_ERR_WORKSPACE, "fit workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        }
+        h->fitws_bytes = need;
+    }
+    return PWA_OK;
+}
+
 }  // namespace
 
 namespace pwa {
@@ -208,6 +291,11 @@ void pwa_destroy(pwa_handle* h) {
     if (h->fitws) cudaFree(h->fitws);
     if (h->fit_event) cudaEventDestroy(h->fit_event);
     if (h->fit_stream) cudaStreamDestroy(h->fit_stream);
+    for (int k = 0; k < 8; ++k) {
+        if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
+        if (h->aux_join[k]) cudaEventDestroy(h->aux_join[k]);
+    }
+    if (h->aux_fork) cudaEventDestroy(h->aux_fork);
     delete h;
 }
 
@@ -356,6 +444,43 @@ pwa_status pwa_generate(pwa_handle* h, const pwa_wave* waves, int K, const float
     return PWA_OK;
 }
 
+pwa_status pwa_nll_grad_shape(pwa_handle* h, const float* A, const float* dA, int K, int64_t n, int64_t ld,
+                              const float* A_mc, const float* dA_mc, int64_t n_mc, int64_t ld_mc, const float* w_mc,
+                              double n_gen, const int* float_wave, int F, const float* V, double n_factor,
+                              double* nll, double* grad, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    st = check_amp_layout(h, K, n_mc, ld_mc);
+    if (st != PWA_OK) return st;
+    if (F < 0 || F > PWA_MAX_FLOAT) return fail(h, PWA_ERR_INVALID_ARG, "F = %d outside [0, %d]", F, PWA_MAX_FLOAT);
+    if (F > 0 && !float_wave) return fail(h, PWA_ERR_INVALID_ARG, "float_wave is NULL");
+    for (int q = 0; q < F; ++q)
+        if (float_wave[q] < 0 || float_wave[q] >= K)
+            return fail(h, PWA_ERR_INVALID_ARG, "float_wave[%d] = %d outside [0, K)", q, float_wave[q]);
+    if ((n > 0 && (!A || (F > 0 && !dA))) || (n_mc > 0 && (!A_mc || (F > 0 && !dA_mc))) || !V || !nll || !grad)
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array argument");
+    if ((A && !aligned16(A)) || (dA && !aligned16(dA)) || (A_mc && !aligned16(A_mc)) || (dA_mc && !aligned16(dA_mc)))
+        return fail(h, PWA_ERR_INVALID_ARG, "amplitude arrays must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) || (w_mc && (reinterpret_cast<uintptr_t>(w_mc) & 3u)))
+        return fail(h, PWA_ERR_INVALID_ARG, "misaligned V or w_mc");
+    if (!(n_gen > 0.0) || !std::isfinite(n_gen) || !std::isfinite(n_factor))
+        return fail(h, PWA_ERR_INVALID_ARG, "n_gen must be finite and > 0, n_factor finite");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::shape_workspace(K, F, h->sm_count), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_nll_shape(reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(dA), K,
+                                          n, ld, reinterpret_cast<const float2*>(A_mc),
+                                          reinterpret_cast<const float2*>(dA_mc), n_mc, ld_mc, w_mc, n_gen,
+                                          float_wave, F, reinterpret_cast<const float2*>(V), n_factor, nll, grad,
+                                          h->ws, h->ws_bytes, h->counters, reinterpret_cast<int*>(h->counters + 1),
+                                          h->status, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shape launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
 void pwa_fit_default_opts(pwa_fit_opts* o) {
     if (!o) return;
     o->max_iter = 1000;
@@ -394,19 +519,11 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     }
     DeviceGuard dg(h->device);
     if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
-    // the fitter runs on a handle-owned non-blocking stream (capturable), ordered after the
-    // caller's stream; the call returns after that stream has drained
-    if (!h->fit_stream) {
-        cudaError_t ce = cudaStreamCreateWithFlags(&h->fit_stream, cudaStreamNonBlocking);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->fit_event, cudaEventDisableTiming);
-        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream");
-    }
+    cudaStream_t s;
     {
-        cudaError_t ce = cudaEventRecord(h->fit_event, (cudaStream_t)stream);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->fit_stream, h->fit_event, 0);
-        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit stream ordering");
+        pwa_status fs = fit_stream_begin(h, stream, &s);
+        if (fs != PWA_OK) return fs;
     }
-    cudaStream_t s = h->fit_stream;
     const int m = o.history;
     pwa_status st = ensure_workspace(h, ws_need, P_tot);
     if (st != PWA_OK) return st;
@@ -414,20 +531,8 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     size_t state_b = pwa::fit_workspace(P_tot, m);
     size_t need = state_b;
     for (int f = 0; f < n_fits; ++f) need += pwa::fit_eval_bytes(fits[f].P, fits[f].K);
-    if (need > h->fitws_bytes) {
-        if (h->fitws) {
-            cudaDeviceSynchronize();
-            cudaFree(h->fitws);
-            h->fitws = nullptr;
-            h->fitws_bytes = 0;
-        }
-        cudaError_t e = cudaMalloc(&h->fitws, need);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(h, PWA_ERR_WORKSPACE, "fit workspace of %zu bytes: %s", need, cudaGetErrorString(e));
-        }
-        h->fitws_bytes = need;
-    }
+    st = grow_fitws(h, need);
+    if (st != PWA_OK) return st;
     struct EvalBuf {
         float2* Vt;
         double* nll;
@@ -447,7 +552,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
             c += r(sizeof(double) * P);
             eb[f].grad = reinterpret_cast<double*>(c);
             c += r(sizeof(double) * (size_t)P * 2 * K);
-            for (int p = 0; p < P; ++p) K_of_p[q++] = K;
+            for (int p = 0; p < P; ++p) K_of_p[q++] = 2 * K;  // components per start
         }
     }
     cudaError_t e = cudaSuccess;
@@ -474,53 +579,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
         }
         return cudaSuccess;
     };
-    // eager first iteration (selects tile shapes outside any capture)
-    e = iteration();
-    if (e != cudaSuccess) return cuda_fail(h, e, "fit iteration");
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    bool graph_ok = false;
-    if (o.use_graph) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaStreamIsCapturing(s, &cs);
-        if (cs == cudaStreamCaptureStatusNone) {
-            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                cudaError_t ce = cudaSuccess;
-                for (int it = 0; it < o.check_every && ce == cudaSuccess; ++it) ce = iteration();
-                cudaError_t ee = cudaStreamEndCapture(s, &graph);
-                if (ce == cudaSuccess && ee == cudaSuccess &&
-                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
-                    graph_ok = true;
-                cudaGetLastError();
-            }
-        }
-    }
-    int* running_h = nullptr;
-    if (cudaMallocHost(&running_h, sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        running_h = nullptr;
-    }
-    int running_local = 1;
-    int* running = running_h ? running_h : &running_local;
-    // every iteration evaluates once; a start stops after max_iter accepted steps, and the line
-    // search can reject a bounded number of times per step, so the loop is bounded too
-    const long long max_loops = 60LL * (long long)o.max_iter + 100;
-    long long loops = 1;
-    while (e == cudaSuccess) {
-        e = pwa::fit_launch_count(h->fitws, P_tot, m, running, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess || *running == 0 || loops >= max_loops) break;
-        if (graph_ok) {
-            e = cudaGraphLaunch(exec, s);
-            loops += o.check_every;
-        } else {
-            for (int it = 0; it < o.check_every && e == cudaSuccess; ++it) e = iteration();
-            loops += o.check_every;
-        }
-    }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (running_h) cudaFreeHost(running_h);
+    e = run_fit_loop(h, s, o, P_tot, m, iteration);
     if (e != cudaSuccess) return cuda_fail(h, e, "fit loop");
     off = 0;
     for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
@@ -537,6 +596,184 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
         results[p].iterations = it[p];
         results[p].evaluations = ev[p];
         results[p].status = stv[p] < 0 ? 1 : stv[p];  // still running at the loop bound: max_iter
+    }
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, int n_fits, const pwa_fit_opts* opts_in,
+                               pwa_fit_result* results, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (!fits || n_fits < 1 || !results) return fail(h, PWA_ERR_INVALID_ARG, "fits/results NULL or n_fits < 1");
+    pwa_fit_opts o;
+    pwa_fit_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1)
+        return fail(h, PWA_ERR_INVALID_ARG, "bad options");
+    std::vector<pwa::WaveTable> wts(n_fits);
+    for (int f = 0; f < n_fits; ++f) {
+        const pwa_shape_fit_desc& d = fits[f];
+        pwa_status st = check_amp_layout(h, d.K, d.n, d.ld);
+        if (st == PWA_OK) st = check_amp_layout(h, d.K, d.n_mc, d.ld_mc);
+        if (st != PWA_OK) return st;
+        if (!d.waves) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: waves NULL", f);
+        st = fill_waves(h, d.waves, d.K, &wts[f]);
+        if (st != PWA_OK) return st;
+        if (d.F < 0 || d.F > PWA_MAX_FLOAT || (d.F > 0 && (!d.float_wave || !d.float_kind)))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: F out of range or NULL float_wave/float_kind", f);
+        if (2 * d.K + d.F > 128) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: 2K + F > 128", f);
+        for (int q = 0; q < d.F; ++q) {
+            if (d.float_wave[q] < 0 || d.float_wave[q] >= d.K || (d.float_kind[q] != 0 && d.float_kind[q] != 1))
+                return fail(h, PWA_ERR_INVALID_ARG, "fit %d: bad floating parameter %d", f, q);
+            for (int r = 0; r < q; ++r)
+                if (d.float_wave[r] == d.float_wave[q] && d.float_kind[r] == d.float_kind[q])
+                    return fail(h, PWA_ERR_INVALID_ARG, "fit %d: floating parameter %d repeated", f, q);
+        }
+        if (!d.kin || !d.kin_mc || !d.A || !d.A_mc || !d.V0 || (d.F > 0 && (!d.dA || !d.dA_mc)))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: NULL array", f);
+        if (!aligned16(d.kin) || !aligned16(d.kin_mc) || !aligned16(d.A) || !aligned16(d.A_mc) ||
+            (d.dA && !aligned16(d.dA)) || (d.dA_mc && !aligned16(d.dA_mc)) || (reinterpret_cast<uintptr_t>(d.V0) & 7u) ||
+            (d.x_out && (reinterpret_cast<uintptr_t>(d.x_out) & 7u)))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: misaligned array", f);
+        if (!(d.n_gen > 0.0) || !std::isfinite(d.n_gen) || !std::isfinite(d.n_factor))
+            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: bad n_gen or n_factor", f);
+    }
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t s;
+    pwa_status pst = fit_stream_begin(h, stream, &s);
+    if (pst != PWA_OK) return pst;
+    const int NS = n_fits < 8 ? n_fits : 8;
+    for (int k = 0; k < NS; ++k) {
+        cudaError_t ce = cudaSuccess;
+        if (!h->aux[k]) ce = cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking);
+        if (ce == cudaSuccess && !h->aux_join[k]) ce = cudaEventCreateWithFlags(&h->aux_join[k], cudaEventDisableTiming);
+        if (ce == cudaSuccess && !h->aux_fork) ce = cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming);
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit streams");
+    }
+    const int m = o.history;
+    const int P_tot = n_fits;
+    // workspace: fit state + per-channel trial point, outputs, partial sums and counters
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t state_b = pwa::fit_workspace(P_tot, m);
+    size_t need = state_b;
+    for (int f = 0; f < n_fits; ++f) {
+        const pwa_shape_fit_desc& d = fits[f];
+        need += r256(sizeof(float2) * d.K) + r256(sizeof(double) * (d.F + 1)) + r256(sizeof(double)) +
+                r256(sizeof(double) * (2 * d.K + d.F)) + r256(pwa::shape_workspace(d.K, d.F, h->sm_count)) + 256;
+    }
+    pst = grow_fitws(h, need);
+    if (pst != PWA_OK) return pst;
+    struct Ch {
+        float2* Vt;
+        double* th;
+        double* nll;
+        double* grad;
+        void* part;
+        size_t part_b;
+        unsigned* cnt;
+    };
+    std::vector<Ch> ch(n_fits);
+    {
+        char* c = reinterpret_cast<char*>(h->fitws) + state_b;
+        for (int f = 0; f < n_fits; ++f) {
+            const pwa_shape_fit_desc& d = fits[f];
+            ch[f].Vt = reinterpret_cast<float2*>(c);
+            c += r256(sizeof(float2) * d.K);
+            ch[f].th = reinterpret_cast<double*>(c);
+            c += r256(sizeof(double) * (d.F + 1));
+            ch[f].nll = reinterpret_cast<double*>(c);
+            c += r256(sizeof(double));
+            ch[f].grad = reinterpret_cast<double*>(c);
+            c += r256(sizeof(double) * (2 * d.K + d.F));
+            ch[f].part = c;
+            ch[f].part_b = pwa::shape_workspace(d.K, d.F, h->sm_count);
+            c += r256(ch[f].part_b);
+            ch[f].cnt = reinterpret_cast<unsigned*>(c);
+            c += 256;
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(h->fitws) + state_b, 0, need - state_b, s);
+    // amplitudes of every wave at the starting masses and widths, then the fit state
+    std::vector<std::vector<double>> th0(n_fits), lb(n_fits);
+    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
+        const pwa_shape_fit_desc& d = fits[f];
+        e = pwa::launch_amplitudes(wts[f], d.kin, d.n, d.ld, reinterpret_cast<float2*>(d.A), nullptr, nullptr,
+                                   h->sm_count, s);
+        if (e == cudaSuccess)
+            e = pwa::launch_amplitudes(wts[f], d.kin_mc, d.n_mc, d.ld_mc, reinterpret_cast<float2*>(d.A_mc), nullptr,
+                                       nullptr, h->sm_count, s);
+        th0[f].resize(d.F);
+        lb[f].assign(d.F, 1e-3);
+        for (int q = 0; q < d.F; ++q)
+            th0[f][q] = d.float_kind[q] == 0 ? d.waves[d.float_wave[q]].mass : d.waves[d.float_wave[q]].width;
+        if (e == cudaSuccess)
+            e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(d.V0), d.K, 1, f, o.gauge_fix,
+                                     ch[f].Vt, s, d.F, th0[f].data(), ch[f].th);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "shape fit init");
+    auto channel = [&](int f, cudaStream_t sc) -> cudaError_t {
+        const pwa_shape_fit_desc& d = fits[f];
+        cudaError_t ee = cudaSuccess;
+        for (int q = 0; q < d.F && ee == cudaSuccess; ++q) {
+            const int r = d.float_wave[q];
+            bool first = true;  // one recomputation per floating wave
+            for (int q2 = 0; q2 < q; ++q2) first = first && d.float_wave[q2] != r;
+            if (!first) continue;
+            int qM = -1, qW = -1;
+            for (int q2 = 0; q2 < d.F; ++q2)
+                if (d.float_wave[q2] == r) (d.float_kind[q2] == 0 ? qM : qW) = q2;
+            const pwa_wave& w = d.waves[r];
+            for (int smp = 0; smp < 2 && ee == cudaSuccess; ++smp) {
+                const float* kin = smp == 0 ? d.kin : d.kin_mc;
+                const int64_t nn = smp == 0 ? d.n : d.n_mc, L = smp == 0 ? d.ld : d.ld_mc;
+                float2* AA = reinterpret_cast<float2*>(smp == 0 ? d.A : d.A_mc);
+                float2* DD = reinterpret_cast<float2*>(smp == 0 ? d.dA : d.dA_mc);
+                ee = pwa::launch_amp_floating(w.J, w.lambda, qM >= 0 ? ch[f].th + qM : nullptr, w.mass,
+                                              qW >= 0 ? ch[f].th + qW : nullptr, w.width, kin, nn, L, AA + r * L,
+                                              qM >= 0 ? DD + qM * L : nullptr, qW >= 0 ? DD + qW * L : nullptr,
+                                              h->sm_count, sc);
+            }
+        }
+        if (ee != cudaSuccess) return ee;
+        ee = pwa::launch_nll_shape(reinterpret_cast<const float2*>(d.A), reinterpret_cast<const float2*>(d.dA), d.K,
+                                   d.n, d.ld, reinterpret_cast<const float2*>(d.A_mc),
+                                   reinterpret_cast<const float2*>(d.dA_mc), d.n_mc, d.ld_mc, d.w_mc, d.n_gen,
+                                   d.float_wave, d.F, ch[f].Vt, d.n_factor, ch[f].nll, ch[f].grad, ch[f].part,
+                                   ch[f].part_b, ch[f].cnt, reinterpret_cast<int*>(ch[f].cnt + 1), h->status,
+                                   h->sm_count, sc);
+        if (ee != cudaSuccess) return ee;
+        return pwa::fit_launch_step(h->fitws, P_tot, m, ch[f].nll, ch[f].grad, ch[f].Vt, d.K, 1, f,
+                                    o.gtol * std::fabs(d.n_factor), o.gauge_fix, o.max_iter, sc, d.F, ch[f].th,
+                                    lb[f].data());
+    };
+    auto iteration = [&]() -> cudaError_t {
+        cudaError_t ee = cudaEventRecord(h->aux_fork, s);
+        for (int k = 0; k < NS && ee == cudaSuccess; ++k) ee = cudaStreamWaitEvent(h->aux[k], h->aux_fork, 0);
+        for (int f = 0; f < n_fits && ee == cudaSuccess; ++f) ee = channel(f, h->aux[f % NS]);
+        for (int k = 0; k < NS && ee == cudaSuccess; ++k) {
+            ee = cudaEventRecord(h->aux_join[k], h->aux[k]);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(s, h->aux_join[k], 0);
+        }
+        return ee;
+    };
+    e = run_fit_loop(h, s, o, P_tot, m, iteration);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shape fit loop");
+    std::vector<int> D_of_p(P_tot);
+    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
+        D_of_p[f] = 2 * fits[f].K + fits[f].F;
+        if (fits[f].x_out) e = pwa::fit_export_x(h->fitws, P_tot, m, D_of_p[f], f, fits[f].x_out, s);
+    }
+    std::vector<double> fv, gm;
+    std::vector<int> it, ev, stv;
+    if (e == cudaSuccess) e = pwa::fit_read_results(h->fitws, P_tot, m, fv, gm, it, ev, stv, D_of_p.data(), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "shape fit results");
+    for (int p = 0; p < P_tot; ++p) {
+        results[p].nll = fv[p];
+        results[p].grad_max = gm[p];
+        results[p].iterations = it[p];
+        results[p].evaluations = ev[p];
+        results[p].status = stv[p] < 0 ? 1 : stv[p];
     }
     h->err.clear();
     return PWA_OK;

@@ -80,8 +80,13 @@ __device__ __forceinline__ double block_max_abs(const double* a, int D, double* 
 }
 
 // init: x <- gauge-fixed V0 (double), trial <- x, status running
+struct Theta0 {
+    double v[PWA_MAX_FLOAT];
+    double lb[PWA_MAX_FLOAT];
+};
+
 __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, int p_off, int gauge,
-                           float2* __restrict__ Vt) {
+                           float2* __restrict__ Vt, int F, Theta0 th, double* __restrict__ theta_t) {
     const int p = p_off + blockIdx.x, t = threadIdx.x;
     const int D = 2 * K;
     // phase of V_0
@@ -101,6 +106,10 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
         st.x[(int64_t)p * DM + 2 * t + 1] = (gauge && t == 0) ? 0.0 : im;
         Vt[(int64_t)blockIdx.x * K + t] = make_float2((float)re, (gauge && t == 0) ? 0.f : (float)im);
     }
+    if (t < F) {
+        st.x[(int64_t)p * DM + 2 * K + t] = th.v[t];
+        theta_t[(int64_t)blockIdx.x * F + t] = th.v[t];
+    }
     if (t == 0) {
         st.iter[p] = 0;
         st.nhist[p] = 0;
@@ -116,15 +125,25 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
 
 // One L-BFGS step per start.  ft/gt: f and g at the trial point just evaluated (layout of
 // pwa_nll_grad).  Writes the next trial point as single-precision V.
+// Writes the trial V (and, for F > 0 floating shape parameters, the trial theta) of the next
+// evaluation; x = (Re V_0, Im V_0, ..., Re V_K-1, Im V_K-1, theta_0..theta_F-1).
+__device__ __forceinline__ void write_trial(const double* x, const double* d, double a, int K, int F, int pl,
+                                            float2* Vt, double* theta_t) {
+    const int t = threadIdx.x;
+    if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)(x[2 * t] + a * d[2 * t]), (float)(x[2 * t + 1] + a * d[2 * t + 1]));
+    if (t < F) theta_t[(int64_t)pl * F + t] = x[2 * K + t] + a * d[2 * K + t];
+}
+
 __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* __restrict__ ft,
                                                     const double* __restrict__ gt, float2* __restrict__ Vt, int K,
-                                                    int p_off, int m, double gtol, int gauge, int max_iter) {
+                                                    int p_off, int m, double gtol, int gauge, int max_iter, int F,
+                                                    double* __restrict__ theta_t, Theta0 th) {
     __shared__ double red[128];
     __shared__ double q[DM], xt[DM];
     __shared__ double a_hist[32];
     __shared__ int s_action;  // 0: keep, 1: accepted, 2: rejected
     const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
-    const int D = 2 * K;
+    const int D = 2 * K + F;
     double* x = st.x + (int64_t)p * DM;
     double* g = st.g + (int64_t)p * DM;
     double* d = st.d + (int64_t)p * DM;
@@ -133,7 +152,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     double* rho = st.rho + (int64_t)p * m;
     const int status = st.status[p];
     if (status != FIT_RUNNING) {
-        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
         return;
     }
     if (t == 0) st.evals[p] += 1;
@@ -167,7 +186,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const int action = s_action;
     if (action == 3) {  // non-finite at the start point
         if (t == 0) st.status[p] = 3;
-        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
         return;
     }
     if (action == 2) {
@@ -186,11 +205,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
             if (an < 1e-20) st.status[p] = 2;
         }
         __syncthreads();
-        const double an = st.alpha[p];
-        if (t < K) {
-            const double re = x[2 * t] + an * d[2 * t], im = x[2 * t + 1] + an * d[2 * t + 1];
-            Vt[(int64_t)pl * K + t] = make_float2((float)re, (float)im);
-        }
+        write_trial(x, d, st.alpha[p], K, F, pl, Vt, theta_t);
         return;
     }
     // ---- accepted: history update with s = xt - x, y = gt - g
@@ -227,12 +242,12 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const double gmax = block_max_abs(g, D, red);
     if (gmax < gtol) {
         if (t == 0) st.status[p] = 0;
-        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
         return;
     }
     if (st.iter[p] >= max_iter) {
         if (t == 0) st.status[p] = 1;
-        if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)x[2 * t], (float)x[2 * t + 1]);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
         return;
     }
     // ---- two-loop recursion: q = g; newest to oldest
@@ -274,14 +289,25 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
         a0 = 0.01 * fmax(xm, 0.1) / gmax;
         if (!(gtd < 0.0) && t == 0) st.nhist[p] = 0;
     }
+    // fraction to the boundary: shape parameters stay above their lower bounds
+    if (F > 0) {
+        if (t == 0) {
+            double amax = a0;
+            for (int q = 0; q < F; ++q) {
+                const double dq = d[2 * K + q];
+                if (dq < 0.0) amax = fmin(amax, 0.9 * (x[2 * K + q] - th.lb[q]) / (-dq));
+            }
+            red[0] = amax;
+        }
+        __syncthreads();
+        a0 = red[0];
+        __syncthreads();
+    }
     if (t == 0) {
         st.gtd[p] = gtd;
         st.alpha[p] = a0;
     }
-    if (t < K) {
-        const double re = x[2 * t] + a0 * d[2 * t], im = x[2 * t + 1] + a0 * d[2 * t + 1];
-        Vt[(int64_t)pl * K + t] = make_float2((float)re, (float)im);
-    }
+    write_trial(x, d, a0, K, F, pl, Vt, theta_t);
 }
 
 __global__ void k_count_running(const int* __restrict__ status, int P, int* __restrict__ out) {
@@ -301,6 +327,11 @@ __global__ void k_fit_export(FitState st, int K, int p_off, int P, double2* __re
     const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
     if (t < K && Vout) Vout[(int64_t)pl * K + t] = make_double2(st.x[(int64_t)p * DM + 2 * t], st.x[(int64_t)p * DM + 2 * t + 1]);
     (void)P;
+}
+
+__global__ void k_fit_export_x(FitState st, int D, int p, double* __restrict__ xout) {
+    const int t = threadIdx.x;
+    if (t < D) xout[t] = st.x[(int64_t)p * DM + t];
 }
 
 }  // namespace
@@ -356,17 +387,28 @@ size_t fit_eval_bytes(int P, int K) {
     return r(sizeof(float2) * (size_t)P * K) + r(sizeof(double) * P) + r(sizeof(double) * (size_t)P * 2 * K);
 }
 
+static Theta0 make_theta0(int F, const double* theta0, const double* lb) {
+    Theta0 th;
+    for (int q = 0; q < PWA_MAX_FLOAT; ++q) {
+        th.v[q] = q < F && theta0 ? theta0[q] : 0.0;
+        th.lb[q] = q < F && lb ? lb[q] : 0.0;
+    }
+    return th;
+}
+
 cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
-                            float2* Vt, cudaStream_t s) {
+                            float2* Vt, cudaStream_t s, int F, const double* theta0, double* theta_t) {
     FitState st = carve(fitws, P_tot, m);
-    k_fit_init<<<P, 128, 0, s>>>(st, V0, K, p_off, gauge, Vt);
+    k_fit_init<<<P, 128, 0, s>>>(st, V0, K, p_off, gauge, Vt, F, make_theta0(F, theta0, nullptr), theta_t);
     return cudaGetLastError();
 }
 
 cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
-                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s) {
+                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s, int F,
+                            double* theta_t, const double* lb) {
     FitState st = carve(fitws, P_tot, m);
-    k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, gauge, max_iter);
+    k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, gauge, max_iter, F, theta_t,
+                                   make_theta0(F, nullptr, lb));
     return cudaGetLastError();
 }
 
@@ -379,7 +421,7 @@ cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaS
 }
 
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
-                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int K_of_p[],
+                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int D_of_p[],
                              cudaStream_t s) {
     FitState st = carve(fitws, P_tot, m);
     f.resize(P_tot);
@@ -397,10 +439,16 @@ cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>&
     if (e != cudaSuccess) return e;
     for (int p = 0; p < P_tot; ++p) {
         double mx = 0.0;
-        for (int c = 0; c < 2 * K_of_p[p]; ++c) mx = fmax(mx, fabs(g[(size_t)p * DM + c]));
+        for (int c = 0; c < D_of_p[p]; ++c) mx = fmax(mx, fabs(g[(size_t)p * DM + c]));
         gmax[p] = mx;
     }
     return cudaSuccess;
+}
+
+cudaError_t fit_export_x(void* fitws, int P_tot, int m, int D, int p, double* xout, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_fit_export_x<<<1, 128, 0, s>>>(st, D, p, xout);
+    return cudaGetLastError();
 }
 
 cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s) {

@@ -31,6 +31,9 @@ struct pwa_handle {
     size_t fitws_bytes = 0;
     cudaStream_t fit_stream = nullptr;  // capturable stream the fitter runs on
     cudaEvent_t fit_event = nullptr;
+    cudaStream_t aux[8] = {};            // fork/join streams of the multi-channel fits
+    cudaEvent_t aux_join[8] = {};
+    cudaEvent_t aux_fork = nullptr;
 };
 
 namespace pwa {
@@ -151,14 +154,27 @@ void record_global_error(const char* msg);
 size_t fit_workspace(int P_tot, int m);
 size_t fit_eval_bytes(int P, int K);
 cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
-                            float2* Vt, cudaStream_t s);
+                            float2* Vt, cudaStream_t s, int F = 0, const double* theta0 = nullptr,
+                            double* theta_t = nullptr);
 cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
-                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s);
+                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s, int F = 0,
+                            double* theta_t = nullptr, const double* lb = nullptr);
+cudaError_t fit_export_x(void* fitws, int P_tot, int m, int D, int p, double* xout, cudaStream_t s);
 cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaStream_t s);
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
-                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int K_of_p[],
+                             std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int D_of_p[],
                              cudaStream_t s);
 cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s);
+
+size_t shape_workspace(int K, int F, int sm_count);
+cudaError_t launch_nll_shape(const float2* A, const float2* dA, int K, int64_t n, int64_t ld, const float2* Am,
+                             const float2* dAm, int64_t nm, int64_t ldm, const float* wm, double n_gen,
+                             const int* fwave, int F, const float2* V, double nfac, double* nll, double* grad,
+                             void* ws, size_t ws_bytes, unsigned* counter, int* badw, int* status, int sm_count,
+                             cudaStream_t st);
+cudaError_t launch_amp_floating(int J, int lam, const double* Mdev, double Mc, const double* Gdev, double Gc,
+                                const float* kin, int64_t n, int64_t ld, float2* A, float2* dM, float2* dG,
+                                int sm_count, cudaStream_t st);
 
 size_t generate_workspace(int64_t n_cand);
 cudaError_t launch_generate(const WaveTable& wt, const float2* V, uint64_t seed, uint32_t stream, int64_t cand0,

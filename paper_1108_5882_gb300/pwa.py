@@ -90,6 +90,13 @@ def _register_optional(lib):
     lib.pwa_envelope.argtypes = [ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int]
     lib.pwa_envelope.restype = ctypes.c_double
+    lib.pwa_nll_grad_shape.argtypes = [_vp, _vp, _vp, ctypes.c_int, _i64, _i64, _vp, _vp, _i64, _i64, _vp,
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp,
+                                       ctypes.c_double, _vp, _vp, _vp]
+    lib.pwa_nll_grad_shape.restype = S
+    lib.pwa_fit_shape_batch.argtypes = [_vp, ctypes.POINTER(pwa_shape_fit_desc), ctypes.c_int,
+                                        ctypes.POINTER(pwa_fit_opts), ctypes.POINTER(pwa_fit_result), _vp]
+    lib.pwa_fit_shape_batch.restype = S
     lib.pwa_fit_default_opts.argtypes = [ctypes.POINTER(pwa_fit_opts)]
     lib.pwa_fit_default_opts.restype = None
     lib.pwa_fit_batch.argtypes = [_vp, ctypes.POINTER(pwa_fit_desc), ctypes.c_int, ctypes.POINTER(pwa_fit_opts),
@@ -114,6 +121,14 @@ class pwa_fit_opts(ctypes.Structure):
 class pwa_fit_result(ctypes.Structure):
     _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iterations", ctypes.c_int),
                 ("evaluations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class pwa_shape_fit_desc(ctypes.Structure):
+    _fields_ = [("waves", ctypes.POINTER(pwa_wave)), ("K", ctypes.c_int), ("kin", _vp), ("n", _i64), ("ld", _i64),
+                ("kin_mc", _vp), ("n_mc", _i64), ("ld_mc", _i64), ("w_mc", _vp), ("n_gen", ctypes.c_double),
+                ("n_factor", ctypes.c_double), ("F", ctypes.c_int), ("float_wave", ctypes.POINTER(ctypes.c_int)),
+                ("float_kind", ctypes.POINTER(ctypes.c_int)), ("A", _vp), ("A_mc", _vp), ("dA", _vp), ("dA_mc", _vp),
+                ("V0", _vp), ("x_out", _vp)]
 
 
 def status_string(s: int) -> str:
@@ -295,6 +310,67 @@ def _fit_batch(self, fits, opts=None, stream=None):
 
 
 Handle.pwa_fit_batch = _fit_batch
+
+
+def _nll_grad_shape(self, A, dA, n, A_mc, dA_mc, n_mc, float_wave, V, n_factor, nll, grad, w_mc=None, n_gen=None,
+                    stream=None):
+    """Floating-shape -lnL: A [K][ld], dA [F][ld], A_mc [K][ld_mc], dA_mc [F][ld_mc] complex64;
+    V complex64 [K]; nll float64 [1], grad float64 [2K+F] outputs."""
+    for t, nm in ((A, "A"), (A_mc, "A_mc"), (V, "V")):
+        _check_cuda(t, nm, torch.complex64)
+    _check_cuda(dA, "dA", torch.complex64)
+    _check_cuda(dA_mc, "dA_mc", torch.complex64)
+    _check_cuda(nll, "nll", torch.float64)
+    _check_cuda(grad, "grad", torch.float64)
+    _check_cuda(w_mc, "w_mc", torch.float32)
+    K, ld = A.shape
+    ld_mc = A_mc.shape[1]
+    F = len(float_wave)
+    fw = (ctypes.c_int * max(F, 1))(*[int(x) for x in float_wave])
+    self._chk(self.lib.pwa_nll_grad_shape(self.h, _ptr(A), _ptr(dA), K, int(n), ld, _ptr(A_mc), _ptr(dA_mc),
+                                          int(n_mc), ld_mc, _ptr(w_mc), float(n_mc if n_gen is None else n_gen), fw,
+                                          F, _ptr(V), float(n_factor), _ptr(nll), _ptr(grad), _stream_ptr(stream)))
+
+
+Handle.pwa_nll_grad_shape = _nll_grad_shape
+
+
+def _fit_shape_batch(self, channels, opts=None, stream=None):
+    """channels: list of dicts with waves [(J, lambda, M, W)], kin / kin_mc (float32 [3][ld] CUDA),
+    n, n_mc, n_gen, n_factor, float_wave, float_kind, V0 (complex64 [K] CUDA), optional w_mc and
+    x_out (float64 [2K+F] CUDA).  Work buffers are allocated here.  Returns per-channel results."""
+    arr = (pwa_shape_fit_desc * len(channels))()
+    keep = []
+    for i, c in enumerate(channels):
+        K = len(c["waves"])
+        F = len(c["float_wave"])
+        ld, ld_mc = c["kin"].shape[1], c["kin_mc"].shape[1]
+        dev = c["kin"].device
+        A = torch.empty((K, ld), dtype=torch.complex64, device=dev)
+        Am = torch.empty((K, ld_mc), dtype=torch.complex64, device=dev)
+        dA = torch.empty((max(F, 1), ld), dtype=torch.complex64, device=dev)
+        dAm = torch.empty((max(F, 1), ld_mc), dtype=torch.complex64, device=dev)
+        wv = _wave_array(c["waves"])
+        fw = (ctypes.c_int * max(F, 1))(*[int(x) for x in c["float_wave"]])
+        fk = (ctypes.c_int * max(F, 1))(*[int(x) for x in c["float_kind"]])
+        _check_cuda(c["V0"], "V0", torch.complex64)
+        _check_cuda(c.get("x_out"), "x_out", torch.float64)
+        keep += [A, Am, dA, dAm, wv, fw, fk]
+        arr[i] = pwa_shape_fit_desc(wv, K, c["kin"].data_ptr(), int(c["n"]), ld, c["kin_mc"].data_ptr(), int(c["n_mc"]),
+                                    ld_mc, c["w_mc"].data_ptr() if c.get("w_mc") is not None else None,
+                                    float(c.get("n_gen", c["n_mc"])), float(c.get("n_factor", c["n"])), F, fw, fk,
+                                    A.data_ptr(), Am.data_ptr(), dA.data_ptr(), dAm.data_ptr(), c["V0"].data_ptr(),
+                                    c["x_out"].data_ptr() if c.get("x_out") is not None else None)
+    res = (pwa_fit_result * len(channels))()
+    o = opts if opts is not None else fit_opts()
+    self._chk(self.lib.pwa_fit_shape_batch(self.h, arr, len(channels), ctypes.byref(o), res, _stream_ptr(stream)))
+    torch.cuda.synchronize()
+    del keep
+    return [dict(nll=r.nll, grad_max=r.grad_max, iterations=r.iterations, evaluations=r.evaluations, status=r.status)
+            for r in res]
+
+
+Handle.pwa_fit_shape_batch = _fit_shape_batch
 
 
 def waves_from(ws) -> list[tuple[int, int, float, float]]:

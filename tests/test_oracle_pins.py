@@ -328,3 +328,59 @@ def test_tree_sum_beats_sequential_fp32_sum():
     scale = np.sum(np.abs(x.astype(np.float64)))
     assert abs(float(tree[0]) - exact) < 1e-6 * scale
     assert abs(float(seq) - exact) > 10 * abs(float(tree[0]) - exact)
+
+
+# ---------------------------------------------------------------- floating masses / widths -
+
+def _shape_problem(seed=101, n=1500, n_mc=3000):
+    ws = inputs.wave_set_spread(6, seed)
+    kin = inputs.kinematics(n, seed, 4)
+    kin_mc = inputs.kinematics(n_mc, seed, 5)
+    V = _rand_V(6, seed + 1)
+    return ws, kin, kin_mc, V
+
+
+def test_shape_gradient_finite_differences():
+    # df/dM_r and df/dGamma_r of the streamed-normalisation objective: analytic (from dA) vs
+    # central differences of the objective recomputed from the kinematics in FP64
+    ws, kin, kin_mc, V = _shape_problem()
+    A, dM, dW = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin, derivs=True)
+    Am, dMm, dWm = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc, derivs=True)
+    fwave = [1, 4, 1, 4]  # masses of waves 1, 4 then widths of waves 1, 4
+    dA = np.stack([dM[1], dM[4], dW[1], dW[4]])
+    dAm = np.stack([dMm[1], dMm[4], dWm[1], dWm[4]])
+    # complex128 amplitudes passed through complex64 storage: use the FD of the float-free
+    # objective with a loose tolerance that covers the complex64 rounding
+    f, gV, gS, bad = oracle.nll_grad_shape(A.astype(np.complex64), dA.astype(np.complex64),
+                                           Am.astype(np.complex64), dAm.astype(np.complex64), fwave, V)
+    assert bad == 0
+    f_kin = oracle.nll_shape_from_kin(ws.J, ws.lam, ws.M, ws.W, kin, kin_mc, V)
+    assert abs(f - f_kin) < 1e-5 * abs(f_kin)
+    h = 1e-6
+    for q, (wave, kind) in enumerate([(1, "M"), (4, "M"), (1, "W"), (4, "W")]):
+        Mp, Mm_, Wp, Wm_ = ws.M.copy(), ws.M.copy(), ws.W.copy(), ws.W.copy()
+        if kind == "M":
+            Mp[wave] += h
+            Mm_[wave] -= h
+        else:
+            Wp[wave] += h
+            Wm_[wave] -= h
+        fp = oracle.nll_shape_from_kin(ws.J, ws.lam, Mp, Wp, kin, kin_mc, V)
+        fm = oracle.nll_shape_from_kin(ws.J, ws.lam, Mm_, Wm_, kin, kin_mc, V)
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - gS[q]) < 1e-4 * max(1.0, abs(fd)) + 1e-3, (q, fd, gS[q])
+
+
+def test_shape_objective_reduces_to_psi_form():
+    # with the same MC events, the streamed normalisation equals n V^T Psi V*: f and grad_V of
+    # the shape objective equal those of nll_grad with Psi = normint(A_mc)
+    ws, kin, kin_mc, V = _shape_problem(202)
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin).astype(np.complex64)
+    Am = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64)
+    z = np.zeros((1, A.shape[1]), np.complex64)
+    zm = np.zeros((1, Am.shape[1]), np.complex64)
+    f, gV, gS, _ = oracle.nll_grad_shape(A, z, Am, zm, [0], V)
+    f2, g2 = oracle.nll_grad(A, V[None, :], oracle.normint(Am))
+    assert abs(f - f2[0]) < 1e-11 * abs(f2[0])
+    assert np.max(np.abs(gV - g2[0])) < 1e-9 * np.max(np.abs(g2[0]))
+    assert gS[0] == 0.0
