@@ -273,6 +273,62 @@ PWA_API pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* 
                                        const pwa_fit_opts* opts, pwa_fit_result* results,
                                        void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned start proposer (no counterpart in the paper; its Sec. 2 and Sec. 4 describe the
+ * expense of repeating fits from many random starts, which the proposer targets).
+ * Features: per mass bin (n_bins equal bins of [m_lo, m_hi)) the event averages of the 25 real
+ * spherical harmonics Y_LM(theta, phi), L <= 4, index L^2 + L + M (orthonormal, associated
+ * Legendre functions with the Condon-Shortley phase).  Accumulated as exact fixed-point
+ * integers (2^-36 resolution): deterministic. */
+
+/* feat double [n_bins][25] (device) of n events kin float [3][ld]; 1 <= n_bins <= 64. */
+PWA_API pwa_status pwa_moments(pwa_handle* h, const float* kin, int64_t n, int64_t ld, int n_bins,
+                               double m_lo, double m_hi, double* feat, void* stream);
+
+/* Toy samples drawn by accept-reject from I(Omega) (Eq. 1) under T production-amplitude sets
+ * V [T][K] (device), reduced to features on the fly (events are never stored) on the flat
+ * phase space m in [0.99, 3.0).  Toy t uses the pwa_generate candidates of (seed,
+ * stream_base + t), its own envelope (the pwa_envelope bound, FP64 on the device, 4096
+ * intervals) and n_cand_t = ceil(n_target * C_t / S_t) candidates, S_t = V_t^T Psi_flat V_t*
+ * the mean intensity over the flat phase space (Psi_flat: pwa_normint of flat MC), so about
+ * n_target events are accepted.  Outputs feat double [T][n_bins][25] and n_acc int64 [T]. */
+PWA_API pwa_status pwa_toy_moments(pwa_handle* h, const pwa_wave* waves, int K, const float* V, int T,
+                                   const double* Psi_flat, double n_target, uint64_t seed,
+                                   uint32_t stream_base, int n_bins, double* feat, int64_t* n_acc,
+                                   void* stream);
+
+/* MLP building blocks of the proposer (BF16 = bfloat16 bit patterns in uint16_t; FP32 accumulate).
+ * pwa_mlp_gemm: C[m][n] = sum_{k<Kc} A(m,k) B(n,k) (+ bias[n]) (ReLU if relu), over m < M, n < N,
+ *   with A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk] (element strides; a_type/b_type
+ *   0 = float32, 1 = bfloat16); writes C (float, row stride ldc) and/or C_bf16; accumulate adds
+ *   the previous C.  Forward: A = X[B][in], B = W[out][in].  Data gradient: A = dY, B = W with
+ *   (sbn, sbk) = (1, in).  Weight gradient: A = dY with (sam, sak) = (1, out), B = X with (1, in). */
+PWA_API pwa_status pwa_mlp_gemm(pwa_handle* h, int M, int N, int Kc, const void* A, int a_type,
+                                int64_t sam, int64_t sak, const void* B, int b_type, int64_t sbn,
+                                int64_t sbk, const float* bias, int relu, int accumulate, float* C,
+                                uint16_t* C_bf16, int64_t ldc, void* stream);
+/* dY[i] = 0 where the layer's (post-ReLU) output Y_bf16[i] <= 0. */
+PWA_API pwa_status pwa_mlp_relu_backward(pwa_handle* h, const uint16_t* Y_bf16, float* dY, int64_t n,
+                                         void* stream);
+/* db[n] = sum_b dY[b][n] (fixed order). */
+PWA_API pwa_status pwa_mlp_bias_grad(pwa_handle* h, const float* dY, int B, int N, float* db,
+                                     void* stream);
+/* Winner-takes-all loss over C <= 32 candidate V (out [B][C][2K], (re, im) pairs) against the
+ * target V (target [B][2K]): d_c = |V_c|^2 + |T|^2 - 2|sum_a conj(V_ca) T_a| (distance after the
+ * optimal global phase), loss[b] = (1 - eps) min_c d_c + eps mean_c d_c; dout = d(mean_b loss)
+ * / d out (may be NULL); winner[b] (may be NULL). */
+PWA_API pwa_status pwa_mlp_wta_loss(pwa_handle* h, const float* out, const float* target, int B, int C,
+                                    int K, float eps, float* loss, float* dout, int* winner,
+                                    void* stream);
+/* One Adam step (Kingma and Ba, bias-corrected, step >= 1) on FP32 parameters p with gradient g
+ * and moments m, v; writes the BF16 copy p_bf16 if given. */
+PWA_API pwa_status pwa_mlp_adam(pwa_handle* h, float* p, const float* g, float* m, float* v,
+                                uint16_t* p_bf16, int64_t n, float lr, float b1, float b2, float eps,
+                                int step, void* stream);
+/* y = bfloat16(scale * x) (round to nearest even). */
+PWA_API pwa_status pwa_mlp_to_bf16(pwa_handle* h, const double* x, uint16_t* y, int64_t n, float scale,
+                                   void* stream);
+
 /* -lnL and its gradient for ONE parameter set (P = 1) with no device allocation at all: no
  * handle, no workspace, no cudaMalloc / cudaFree, for callers that cannot allocate device
  * memory (inside a stream capture they do not own, under a memory manager that forbids

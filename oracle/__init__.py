@@ -80,6 +80,10 @@ def _register_fit(lib):
     lib.orc_generate.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                  _i64, ctypes.c_double, _fp, _i64, _i64, _dp]
     lib.orc_generate.restype = ctypes.c_int64
+    lib.orc_ylm_real.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.orc_ylm_real.restype = ctypes.c_double
+    lib.orc_moments.argtypes = [_i64, _fp, _i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+    lib.orc_moments.restype = None
     lib.orc_nll_grad_shape.argtypes = [ctypes.c_int, _i64, _fp, _fp, _i64, _i64, _fp, _fp, _i64, _fp, ctypes.c_double,
                                        _ip, ctypes.c_int, _dp, ctypes.c_double, _dp, _dp, _dp]
     lib.orc_nll_grad_shape.restype = ctypes.c_int
@@ -253,3 +257,19 @@ def nll_shape_from_kin(J, lam, M, W, kin, kin_mc, V, n_factor=None, n_gen=None):
     return lib.orc_nll_shape_from_kin(J.shape[0], _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), n,
                                       _ptr(kin, _fp), n_mc, _ptr(kin_mc, _fp), float(n_mc if n_gen is None else n_gen),
                                       _ptr(Vd, _dp), float(n if n_factor is None else n_factor))
+
+
+# ------------------------------------------------------------------ angular moments ------------
+
+def ylm_real(L, M, ct, phi) -> float:
+    return _load().orc_ylm_real(int(L), int(M), float(ct), float(phi))
+
+
+def moments(kin, n_bins=40, m_lo=0.99, m_hi=3.0):
+    """feat [n_bins][25] = (1/n) sum over events of each mass bin of the real Y_LM, L <= 4."""
+    lib = _load()
+    kin = np.ascontiguousarray(kin, dtype=np.float32)
+    n = kin.shape[1]
+    feat = np.zeros((n_bins, 25))
+    lib.orc_moments(n, _ptr(kin, _fp), n, int(n_bins), float(m_lo), float(m_hi), _ptr(feat, _dp))
+    return feat

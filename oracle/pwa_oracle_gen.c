@@ -121,3 +121,63 @@ int64_t orc_generate(int K, const int* J, const int* lam, const double* M, const
     if (max_ratio) *max_ratio = mr;
     return na;
 }
+
+/* ---------- angular moments (features of the learned start proposer) ------------------ */
+
+/* Real spherical harmonics Y_LM(theta, phi), L <= 4, index k = L^2 + L + M, orthonormal on the
+ * sphere: Y_L0 = N_L0 P_L(x); M > 0: sqrt(2) N_LM P_L^M(x) cos(M phi);
+ * M < 0: sqrt(2) N_L|M| P_L^|M|(x) sin(|M| phi);  N_LM = sqrt((2L+1)/(4 pi) (L-M)!/(L+M)!),
+ * P_L^M the associated Legendre function with the Condon-Shortley phase (-1)^M. */
+static double factorial(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+static double assoc_legendre(int L, int M, double x) {
+    /* P_M^M = (-1)^M (2M-1)!! (1-x^2)^{M/2}; P_{M+1}^M = x (2M+1) P_M^M;
+     * (L-M) P_L^M = x (2L-1) P_{L-1}^M - (L+M-1) P_{L-2}^M */
+    double pmm = 1.0;
+    double s = sqrt((1.0 - x) * (1.0 + x));
+    for (int i = 1; i <= M; ++i) pmm *= -(2.0 * i - 1.0) * s;
+    if (L == M) return pmm;
+    double pm1 = x * (2.0 * M + 1.0) * pmm;
+    if (L == M + 1) return pm1;
+    double pl = 0.0;
+    for (int l = M + 2; l <= L; ++l) {
+        pl = (x * (2.0 * l - 1.0) * pm1 - (l + M - 1.0) * pmm) / (l - M);
+        pmm = pm1;
+        pm1 = pl;
+    }
+    return pl;
+}
+
+double orc_ylm_real(int L, int M, double ct, double phi) {
+    int am = M < 0 ? -M : M;
+    const double pi = 3.14159265358979323846;
+    double N = sqrt((2.0 * L + 1.0) / (4.0 * pi) * factorial(L - am) / factorial(L + am));
+    double p = assoc_legendre(L, am, ct);
+    if (M == 0) return N * p;
+    if (M > 0) return sqrt(2.0) * N * p * cos(am * phi);
+    return sqrt(2.0) * N * p * sin(am * phi);
+}
+
+/* feat[b][k] = (1/n) sum_{events in mass bin b} Y_k(theta, phi), bins of equal width on
+ * [m_lo, m_hi), 25 moments (L <= 4) per bin.  kin is float SoA [3][ld]. */
+void orc_moments(int64_t n, const float* kin, int64_t ld, int n_bins, double m_lo, double m_hi,
+                 double* feat) {
+    for (int i = 0; i < n_bins * 25; ++i) feat[i] = 0.0;
+    /* the bin index is an integer decided by floating point: it is taken in single precision,
+     * (m - m_lo) * (n_bins / (m_hi - m_lo)) with both factors rounded to float, as the kernel
+     * does, so both sides put every event in the same bin */
+    const float lo_f = (float)m_lo;
+    const float inv_w = (float)((double)n_bins / (m_hi - m_lo));
+    for (int64_t i = 0; i < n; ++i) {
+        double m = kin[i], ct = kin[ld + i], ph = kin[2 * ld + i];
+        float dm = kin[i] - lo_f;
+        float xb = dm * inv_w;
+        int b = (int)floorf(xb);
+        if (b < 0) b = 0;
+        if (b >= n_bins) b = n_bins - 1;
+        for (int L = 0; L <= 4; ++L)
+            for (int M = -L; M <= L; ++M) feat[b * 25 + L * L + L + M] += orc_ylm_real(L, M, ct, ph);
+    }
+    if (n > 0)
+        for (int i = 0; i < n_bins * 25; ++i) feat[i] /= (double)n;
+}

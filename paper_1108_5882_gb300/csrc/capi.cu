@@ -481,6 +481,115 @@ pwa_status pwa_nll_grad_shape(pwa_handle* h, const float* A, const float* dA, in
     return PWA_OK;
 }
 
+pwa_status pwa_moments(pwa_handle* h, const float* kin, int64_t n, int64_t ld, int n_bins, double m_lo, double m_hi,
+                       double* feat, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (n < 0 || ld < n || (n > 0 && !kin) || !feat) return fail(h, PWA_ERR_INVALID_ARG, "bad sizes or NULL array");
+    if (n_bins < 1 || n_bins > 64 || !(m_hi > m_lo))
+        return fail(h, PWA_ERR_INVALID_ARG, "n_bins must be 1..64 and m_hi > m_lo");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    pwa_status st = ensure_workspace(h, pwa::moments_workspace(n_bins, 1), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_moments(kin, n, ld, n_bins, m_lo, m_hi, feat, h->ws, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_toy_moments(pwa_handle* h, const pwa_wave* waves, int K, const float* V, int T, const double* Psi_flat,
+                           double n_target, uint64_t seed, uint32_t stream_base, int n_bins, double* feat,
+                           int64_t* n_acc, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (!waves || !V || !Psi_flat || !feat || !n_acc || T < 1 || T > (1 << 24))
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array or T out of range");
+    if (K < 1 || K > PWA_MAX_WAVES) return fail(h, PWA_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, PWA_MAX_WAVES);
+    if (n_bins < 1 || n_bins > 64) return fail(h, PWA_ERR_INVALID_ARG, "n_bins must be 1..64");
+    if (!(n_target >= 1.0) || !(n_target <= 1e9)) return fail(h, PWA_ERR_INVALID_ARG, "n_target out of range");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) || !aligned16(Psi_flat) || (reinterpret_cast<uintptr_t>(n_acc) & 7u))
+        return fail(h, PWA_ERR_INVALID_ARG, "misaligned array");
+    pwa::WaveTable wt;
+    pwa_status st = fill_waves(h, waves, K, &wt);
+    if (st != PWA_OK) return st;
+    double Md[PWA_MAX_WAVES], Wd[PWA_MAX_WAVES];
+    for (int a = 0; a < K; ++a) {
+        Md[a] = waves[a].mass;
+        Wd[a] = waves[a].width;
+    }
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::toy_moments_workspace(n_bins, T), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_toy_moments(wt, Md, Wd, reinterpret_cast<const float2*>(V), T,
+                                            reinterpret_cast<const double2*>(Psi_flat), n_target, seed, stream_base,
+                                            n_bins, feat, reinterpret_cast<long long*>(n_acc), h->ws,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "toy moments launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_mlp_gemm(pwa_handle* h, int M, int N, int Kc, const void* A, int a_type, int64_t sam, int64_t sak,
+                        const void* B, int b_type, int64_t sbn, int64_t sbk, const float* bias, int relu,
+                        int accumulate, float* C, uint16_t* C_bf16, int64_t ldc, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (M < 1 || N < 1 || Kc < 1 || !A || !B || (!C && !C_bf16) || ldc < N || (accumulate && !C))
+        return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: bad sizes or NULL arrays");
+    if ((a_type != 0 && a_type != 1) || (b_type != 0 && b_type != 1))
+        return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: element type must be 0 (float32) or 1 (bfloat16)");
+    if (sam < 0 || sak < 0 || sbn < 0 || sbk < 0) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: negative stride");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_gemm(M, N, Kc, A, a_type, sam, sak, B, b_type, sbn, sbk, bias, relu, accumulate, C,
+                                         C_bf16, ldc, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp gemm");
+    return PWA_OK;
+}
+
+pwa_status pwa_mlp_relu_backward(pwa_handle* h, const uint16_t* Y_bf16, float* dY, int64_t n, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!Y_bf16 || !dY))) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_relu_backward: bad args");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_relu_bwd(Y_bf16, dY, n, h->sm_count, (cudaStream_t)stream);
+    return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "relu backward");
+}
+
+pwa_status pwa_mlp_bias_grad(pwa_handle* h, const float* dY, int B, int N, float* db, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (B < 1 || N < 1 || !dY || !db) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_bias_grad: bad args");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_bias_grad(dY, B, N, db, (cudaStream_t)stream);
+    return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "bias grad");
+}
+
+pwa_status pwa_mlp_wta_loss(pwa_handle* h, const float* out, const float* target, int B, int C, int K, float eps,
+                            float* loss, float* dout, int* winner, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (B < 1 || C < 1 || C > 32 || K < 1 || K > PWA_MAX_WAVES || !out || !target || !loss || !(eps >= 0.f && eps <= 1.f))
+        return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_wta_loss: bad args (1 <= C <= 32, 0 <= eps <= 1)");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_wta(out, target, B, C, K, eps, loss, dout, winner, (cudaStream_t)stream);
+    return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "wta loss");
+}
+
+pwa_status pwa_mlp_adam(pwa_handle* h, float* p, const float* g, float* m, float* v, uint16_t* p_bf16, int64_t n,
+                        float lr, float b1, float b2, float eps, int step, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!p || !g || !m || !v)) || step < 1 || !(lr > 0.f) || !(b1 >= 0.f && b1 < 1.f) ||
+        !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f))
+        return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_adam: bad args");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_adam(p, g, m, v, p_bf16, n, lr, b1, b2, eps, step, h->sm_count, (cudaStream_t)stream);
+    return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "adam");
+}
+
+pwa_status pwa_mlp_to_bf16(pwa_handle* h, const double* x, uint16_t* y, int64_t n, float scale, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_to_bf16: bad args");
+    DeviceGuard dg(h->device);
+    cudaError_t e = pwa::launch_mlp_to_bf16(x, y, n, scale, h->sm_count, (cudaStream_t)stream);
+    return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "to bf16");
+}
+
 void pwa_fit_default_opts(pwa_fit_opts* o) {
     if (!o) return;
     o->max_iter = 1000;

@@ -176,6 +176,25 @@ cudaError_t launch_amp_floating(int J, int lam, const double* Mdev, double Mc, c
                                 const float* kin, int64_t n, int64_t ld, float2* A, float2* dM, float2* dG,
                                 int sm_count, cudaStream_t st);
 
+size_t moments_workspace(int n_bins, int T);
+size_t toy_moments_workspace(int n_bins, int T);
+cudaError_t launch_moments(const float* kin, int64_t n, int64_t ld, int n_bins, double m_lo, double m_hi, double* feat,
+                           void* ws, int sm_count, cudaStream_t st);
+cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const double* Wd, const float2* V, int T,
+                               const double2* Psi_flat, double n_target, uint64_t seed, uint32_t stream_base,
+                               int n_bins, double* feat, long long* n_acc, void* ws, cudaStream_t st);
+
+cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
+                            int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
+                            uint16_t* Cb, int64_t ldc, cudaStream_t st);
+cudaError_t launch_mlp_relu_bwd(const uint16_t* Y, float* dY, int64_t n, int sm_count, cudaStream_t st);
+cudaError_t launch_mlp_bias_grad(const float* dY, int B, int N, float* db, cudaStream_t st);
+cudaError_t launch_mlp_wta(const float* out, const float* target, int B, int C, int K, float eps, float* loss,
+                           float* dout, int* winner, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* p, const float* g, float* m, float* v, uint16_t* pb, int64_t n, float lr, float b1,
+                            float b2, float eps, int step, int sm_count, cudaStream_t st);
+cudaError_t launch_mlp_to_bf16(const double* x, uint16_t* y, int64_t n, float scale, int sm_count, cudaStream_t st);
+
 size_t generate_workspace(int64_t n_cand);
 cudaError_t launch_generate(const WaveTable& wt, const float2* V, uint64_t seed, uint32_t stream, int64_t cand0,
                             int64_t n_cand, double envelope, float* kin, int64_t ld_out, int64_t max_out,

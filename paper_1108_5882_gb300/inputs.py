@@ -113,3 +113,20 @@ def uneven_channels(n_channels: int, seed: int, kmin: int = 4, kmax: int = 48,
 
 def pad_to(n: int, mult: int = 256) -> int:
     return ((n + mult - 1) // mult) * mult
+
+
+def bf16_bits(x) -> np.ndarray:
+    """float32 values -> bfloat16 bit patterns (uint16), rounding to nearest even."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    return ((b + 0x7FFF + lsb) >> 16).astype(np.uint16)
+
+
+def mlp_weights(dims, seed: int, stream: int = 21):
+    """He-initialised weights W_l [out][in] (float32) and zero biases for layer sizes dims."""
+    g = rng(seed, stream)
+    Ws, bs = [], []
+    for i in range(len(dims) - 1):
+        Ws.append((g.normal(size=(dims[i + 1], dims[i])) * math.sqrt(2.0 / dims[i])).astype(np.float32))
+        bs.append(np.zeros(dims[i + 1], dtype=np.float32))
+    return Ws, bs

@@ -97,6 +97,23 @@ def _register_optional(lib):
     lib.pwa_fit_shape_batch.argtypes = [_vp, ctypes.POINTER(pwa_shape_fit_desc), ctypes.c_int,
                                         ctypes.POINTER(pwa_fit_opts), ctypes.POINTER(pwa_fit_result), _vp]
     lib.pwa_fit_shape_batch.restype = S
+    lib.pwa_moments.argtypes = [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]
+    lib.pwa_moments.restype = S
+    lib.pwa_toy_moments.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _vp, _vp, _vp]
+    lib.pwa_toy_moments.restype = S
+    lib.pwa_mlp_gemm.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _i64, _i64, _vp,
+                                 ctypes.c_int, _i64, _i64, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _vp]
+    lib.pwa_mlp_relu_backward.argtypes = [_vp, _vp, _vp, _i64, _vp]
+    lib.pwa_mlp_bias_grad.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    lib.pwa_mlp_wta_loss.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp,
+                                     _vp, _vp, _vp]
+    lib.pwa_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_int, _vp]
+    lib.pwa_mlp_to_bf16.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_float, _vp]
+    for f in ("pwa_mlp_gemm", "pwa_mlp_relu_backward", "pwa_mlp_bias_grad", "pwa_mlp_wta_loss", "pwa_mlp_adam",
+              "pwa_mlp_to_bf16"):
+        getattr(lib, f).restype = S
     lib.pwa_fit_default_opts.argtypes = [ctypes.POINTER(pwa_fit_opts)]
     lib.pwa_fit_default_opts.restype = None
     lib.pwa_fit_batch.argtypes = [_vp, ctypes.POINTER(pwa_fit_desc), ctypes.c_int, ctypes.POINTER(pwa_fit_opts),
@@ -371,6 +388,97 @@ def _fit_shape_batch(self, channels, opts=None, stream=None):
 
 
 Handle.pwa_fit_shape_batch = _fit_shape_batch
+
+
+def _moments(self, kin, n, feat, n_bins=40, m_lo=0.99, m_hi=3.0, stream=None):
+    _check_cuda(kin, "kin", torch.float32)
+    _check_cuda(feat, "feat", torch.float64)
+    self._chk(self.lib.pwa_moments(self.h, _ptr(kin), int(n), int(kin.shape[1]), int(n_bins), float(m_lo),
+                                   float(m_hi), _ptr(feat), _stream_ptr(stream)))
+
+
+def _toy_moments(self, waves, V, Psi_flat, n_target, seed, stream_base, feat, n_acc, n_bins=40, stream=None):
+    """V complex64 [T][K]; Psi_flat complex128 [K][K]; feat float64 [T][n_bins*25]; n_acc int64 [T]."""
+    _check_cuda(V, "V", torch.complex64)
+    _check_cuda(Psi_flat, "Psi_flat", torch.complex128)
+    _check_cuda(feat, "feat", torch.float64)
+    _check_cuda(n_acc, "n_acc", torch.int64)
+    self._chk(self.lib.pwa_toy_moments(self.h, _wave_array(waves), len(waves), _ptr(V), int(V.shape[0]),
+                                       _ptr(Psi_flat), float(n_target), int(seed), int(stream_base), int(n_bins),
+                                       _ptr(feat), _ptr(n_acc), _stream_ptr(stream)))
+
+
+Handle.pwa_moments = _moments
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return 0
+    if t.dtype == torch.bfloat16:
+        return 1
+    raise ValueError("float32 or bfloat16 expected")
+
+
+def _mlp_gemm(self, M, N, Kc, A, sa, B, sb, C=None, C_bf16=None, bias=None, relu=False, accumulate=False, ldc=None,
+              stream=None):
+    """C[m][n] = sum_k A(m,k) B(n,k) (+bias) (ReLU); sa = (sam, sak), sb = (sbn, sbk) element strides."""
+    for t, nm in ((A, "A"), (B, "B")):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor")
+    _check_cuda(C, "C", torch.float32)
+    _check_cuda(C_bf16, "C_bf16", torch.bfloat16)
+    _check_cuda(bias, "bias", torch.float32)
+    self._chk(self.lib.pwa_mlp_gemm(self.h, int(M), int(N), int(Kc), _ptr(A), _dtype_code(A), int(sa[0]), int(sa[1]),
+                                    _ptr(B), _dtype_code(B), int(sb[0]), int(sb[1]), _ptr(bias), int(relu),
+                                    int(accumulate), _ptr(C), _ptr(C_bf16), int(ldc if ldc is not None else N),
+                                    _stream_ptr(stream)))
+
+
+def _mlp_relu_backward(self, Y_bf16, dY, stream=None):
+    _check_cuda(Y_bf16, "Y", torch.bfloat16)
+    _check_cuda(dY, "dY", torch.float32)
+    self._chk(self.lib.pwa_mlp_relu_backward(self.h, _ptr(Y_bf16), _ptr(dY), int(dY.numel()), _stream_ptr(stream)))
+
+
+def _mlp_bias_grad(self, dY, db, stream=None):
+    _check_cuda(dY, "dY", torch.float32)
+    _check_cuda(db, "db", torch.float32)
+    B, N = dY.shape
+    self._chk(self.lib.pwa_mlp_bias_grad(self.h, _ptr(dY), int(B), int(N), _ptr(db), _stream_ptr(stream)))
+
+
+def _mlp_wta_loss(self, out, target, C, K, eps, loss, dout=None, winner=None, stream=None):
+    _check_cuda(out, "out", torch.float32)
+    _check_cuda(target, "target", torch.float32)
+    _check_cuda(loss, "loss", torch.float32)
+    _check_cuda(dout, "dout", torch.float32)
+    _check_cuda(winner, "winner", torch.int32)
+    B = target.shape[0]
+    self._chk(self.lib.pwa_mlp_wta_loss(self.h, _ptr(out), _ptr(target), int(B), int(C), int(K), float(eps),
+                                        _ptr(loss), _ptr(dout), _ptr(winner), _stream_ptr(stream)))
+
+
+def _mlp_adam(self, p, g, m, v, p_bf16, lr, step, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    for t, nm in ((p, "p"), (g, "g"), (m, "m"), (v, "v")):
+        _check_cuda(t, nm, torch.float32)
+    _check_cuda(p_bf16, "p_bf16", torch.bfloat16)
+    self._chk(self.lib.pwa_mlp_adam(self.h, _ptr(p), _ptr(g), _ptr(m), _ptr(v), _ptr(p_bf16), int(p.numel()),
+                                    float(lr), float(b1), float(b2), float(eps), int(step), _stream_ptr(stream)))
+
+
+def _mlp_to_bf16(self, x, y, scale=1.0, stream=None):
+    _check_cuda(x, "x", torch.float64)
+    _check_cuda(y, "y", torch.bfloat16)
+    self._chk(self.lib.pwa_mlp_to_bf16(self.h, _ptr(x), _ptr(y), int(x.numel()), float(scale), _stream_ptr(stream)))
+
+
+Handle.pwa_mlp_gemm = _mlp_gemm
+Handle.pwa_mlp_relu_backward = _mlp_relu_backward
+Handle.pwa_mlp_bias_grad = _mlp_bias_grad
+Handle.pwa_mlp_wta_loss = _mlp_wta_loss
+Handle.pwa_mlp_adam = _mlp_adam
+Handle.pwa_mlp_to_bf16 = _mlp_to_bf16
+Handle.pwa_toy_moments = _toy_moments
 
 
 def waves_from(ws) -> list[tuple[int, int, float, float]]:

@@ -1,0 +1,208 @@
+"""Learned start proposer on the GPU: moments features, fused toy generation, MLP kernels,
+all against the FP64 oracle (oracle/ and oracle/mlp.py)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1108_5882_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+SEED = inputs.SEED_BASE + 5
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_1108_5882_gb300 import build, pwa
+    build.build()
+    return pwa.Handle(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_moments_parity_and_determinism(h):
+    n = 100_001
+    kin = inputs.kinematics(n, SEED, 4)
+    ld = n + 1
+    kin_p = np.zeros((3, ld), np.float32)
+    kin_p[:, :n] = kin
+    feat = torch.zeros(40 * 25, dtype=torch.float64, device="cuda")
+    h.pwa_moments(dev(kin_p), n, feat)
+    f1 = feat.cpu().numpy().copy()
+    h.pwa_moments(dev(kin_p), n, feat)
+    assert np.array_equal(f1, feat.cpu().numpy())  # fixed-point integer sums: bitwise reproducible
+    ref = oracle.moments(kin).reshape(-1)
+    assert np.max(np.abs(f1 - ref)) <= 1e-6 + 1e-5 * np.max(np.abs(ref))
+
+
+def test_toy_moments_match_oracle_generator(h):
+    from paper_1108_5882_gb300 import pwa
+    K, T, n_target = 16, 3, 20_000
+    ws = inputs.wave_set_spread(K, SEED + 1)
+    waves = pwa.waves_from(ws)
+    kin_mc = inputs.kinematics(200_000, SEED + 1, 5)
+    Psi = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
+    V = np.stack([inputs.production_amplitudes(K, SEED + 10 + t) for t in range(T)])
+    feat = torch.zeros((T, 1000), dtype=torch.float64, device="cuda")
+    nacc = torch.zeros(T, dtype=torch.int64, device="cuda")
+    h.pwa_toy_moments(waves, dev(V), dev(Psi), n_target, 99, 1000, feat, nacc)
+    torch.cuda.synchronize()
+    fg, ng = feat.cpu().numpy(), nacc.cpu().numpy()
+    for t in range(T):
+        Vt = V[t].astype(np.complex128)
+        C = oracle.envelope(ws.M, ws.W, Vt)
+        S = float(np.real(Vt @ Psi @ Vt.conj()))
+        n_cand = math.ceil(n_target * C / S)
+        kin, na, mr = oracle.generate(ws.J, ws.lam, ws.M, ws.W, Vt, 99, 1000 + t, 0, n_cand, C, 10 * n_target)
+        assert mr <= 1.0
+        assert abs(ng[t] - na) <= 2, (ng[t], na)  # accept decisions differ only at the FP32/FP64 boundary
+        assert abs(na - n_target) < 6 * math.sqrt(n_target)
+        ref = oracle.moments(kin).reshape(-1)
+        assert np.max(np.abs(fg[t] - ref)) <= 2e-5, np.max(np.abs(fg[t] - ref))
+
+
+# ------------------------------------------------------------------- MLP kernels ----------
+
+def _bf16_dev(bits):
+    return torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+
+
+def test_mlp_gemm_forward_and_backward_match_oracle(h):
+    from oracle import mlp
+    g = np.random.default_rng(21)
+    B, n_in, n_out = 37, 300, 70
+    Xb = inputs.bf16_bits(g.normal(size=(B, n_in)).astype(np.float32))
+    Wb = inputs.bf16_bits((g.normal(size=(n_out, n_in)) * 0.1).astype(np.float32))
+    bias = g.normal(size=n_out).astype(np.float32)
+    X, W = mlp.bf16_to_f64(Xb), mlp.bf16_to_f64(Wb)
+    Y = torch.empty((B, n_out), dtype=torch.float32, device="cuda")
+    Yb = torch.empty((B, n_out), dtype=torch.bfloat16, device="cuda")
+    h.pwa_mlp_gemm(B, n_out, n_in, _bf16_dev(Xb), (n_in, 1), _bf16_dev(Wb), (n_in, 1), C=Y, C_bf16=Yb,
+                   bias=dev(bias), relu=True)
+    ref = mlp.linear(X, W, bias.astype(np.float64), relu=True)
+    scale = np.abs(X) @ np.abs(W).T + np.abs(bias)
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-5 * scale)
+    # the BF16 copy is the round-to-nearest-even of the FP32 output
+    yb = Yb.cpu().view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(yb, inputs.bf16_bits(Y.cpu().numpy()))
+    # backward: dX = (dY o mask) W and dW = (dY o mask)^T X, db = sum_b
+    dY = g.normal(size=(B, n_out)).astype(np.float32)
+    dYd = dev(dY)
+    h.pwa_mlp_relu_backward(Yb, dYd)
+    Ymask = mlp.bf16_to_f64(yb)
+    _, dW_ref, db_ref = mlp.linear_backward(X, W, Ymask, dY.astype(np.float64), relu=True)
+    gmask = dY * (Ymask > 0)
+    dX_ref = gmask @ W
+    dX = torch.empty((B, n_in), dtype=torch.float32, device="cuda")
+    dW = torch.empty((n_out, n_in), dtype=torch.float32, device="cuda")
+    db = torch.empty(n_out, dtype=torch.float32, device="cuda")
+    h.pwa_mlp_gemm(B, n_in, n_out, dYd, (n_out, 1), _bf16_dev(Wb), (1, n_in), C=dX)
+    h.pwa_mlp_gemm(n_out, n_in, B, dYd, (1, n_out), _bf16_dev(Xb), (1, n_in), C=dW)
+    h.pwa_mlp_bias_grad(dYd, db)
+    assert np.all(np.abs(dX.cpu().numpy() - dX_ref) <= 1e-5 * (np.abs(gmask) @ np.abs(W)) + 1e-30)
+    assert np.all(np.abs(dW.cpu().numpy() - dW_ref) <= 1e-5 * (np.abs(gmask).T @ np.abs(X)) + 1e-30)
+    assert np.all(np.abs(db.cpu().numpy() - db_ref) <= 1e-5 * np.abs(gmask).sum(axis=0) + 1e-30)
+
+
+def test_mlp_wta_loss_and_adam_match_oracle(h):
+    from oracle import mlp
+    g = np.random.default_rng(22)
+    B, C, K = 50, 32, 16
+    out = g.normal(size=(B, C * 2 * K)).astype(np.float32)
+    tgt = g.normal(size=(B, 2 * K)).astype(np.float32)
+    loss = torch.empty(B, dtype=torch.float32, device="cuda")
+    dout = torch.empty((B, C * 2 * K), dtype=torch.float32, device="cuda")
+    win = torch.empty(B, dtype=torch.int32, device="cuda")
+    h.pwa_mlp_wta_loss(dev(out), dev(tgt), C, K, 0.05, loss, dout, win)
+    l_ref, d_ref, w_ref = mlp.wta_loss(out.astype(np.float64), tgt.astype(np.float64), C, K, 0.05)
+    assert np.array_equal(win.cpu().numpy(), w_ref)
+    assert np.allclose(loss.cpu().numpy(), l_ref, rtol=2e-5, atol=1e-4)
+    assert np.allclose(dout.cpu().numpy(), d_ref, rtol=1e-4, atol=1e-6)
+    n = 1000
+    p, gr = g.normal(size=n).astype(np.float32), g.normal(size=n).astype(np.float32)
+    m, v = (0.1 * g.normal(size=n)).astype(np.float32), np.abs(0.1 * g.normal(size=n)).astype(np.float32)
+    pd, md, vd = dev(p), dev(m), dev(v)
+    pb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    h.pwa_mlp_adam(pd, dev(gr), md, vd, pb, 1e-3, 7)
+    p_ref, m_ref, v_ref = mlp.adam(p.astype(np.float64), gr.astype(np.float64), m.astype(np.float64),
+                                   v.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 7)
+    # FP32 rounding is relative to the operands of each update, not to its (possibly smaller)
+    # result; the FP32 constants b1, 1 - b1, b2, 1 - b2 carry their own representation error
+    # (~3e-8 relative): a few roundings of u = 6e-8 each stay below 1e-6 of the operands
+    m64, v64, g64 = m.astype(np.float64), v.astype(np.float64), gr.astype(np.float64)
+    assert np.all(np.abs(md.cpu().numpy() - m_ref) <= 1e-6 * (0.9 * np.abs(m64) + 0.1 * np.abs(g64)))
+    assert np.all(np.abs(vd.cpu().numpy() - v_ref) <= 1e-6 * (0.999 * v64 + 0.001 * g64 * g64))
+    assert np.all(np.abs(pd.cpu().numpy() - p_ref) <= 1e-6 * np.abs(p) + 1e-3 * 1e-5)
+
+
+def test_network_gradient_matches_oracle_chain():
+    # one full forward/backward of the 4-layer proposer through the kernels vs the FP64 chain
+    # rule on the same BF16 weights and the GPU's own BF16 activations (the only rounding the
+    # GPU adds between layers)
+    from oracle import mlp
+    from paper_1108_5882_gb300 import build, learned, pwa
+    build.build()
+    hh = pwa.Handle(0)
+    prop = learned.Proposer(hh, K=4, C=8, hidden=(64, 64, 64), n_feat=100, seed=3)
+    g = np.random.default_rng(23)
+    B = 16
+    Xb = inputs.bf16_bits(g.normal(size=(B, 100)).astype(np.float32))
+    tgt = g.normal(size=(B, 8)).astype(np.float32)
+    acts, out = prop.forward(_bf16_dev(Xb))
+    loss = torch.empty(B, dtype=torch.float32, device="cuda")
+    dout = torch.empty_like(out)
+    hh.pwa_mlp_wta_loss(out, dev(tgt), 8, 4, 0.05, loss, dout)
+    gW, gb = prop.backward(acts, dout.clone())
+    # oracle chain on the GPU's BF16 activations
+    A = [mlp.bf16_to_f64(a.cpu().view(torch.int16).numpy().view(np.uint16)) for a in acts]
+    Ws = [mlp.bf16_to_f64(w.cpu().view(torch.int16).numpy().view(np.uint16)) for w in prop.Wb]
+    _, d_ref, _ = mlp.wta_loss(out.cpu().numpy().astype(np.float64), tgt.astype(np.float64), 8, 4, 0.05)
+    dY = d_ref
+    for i in reversed(range(4)):
+        Yi = A[i + 1] if i < 3 else None
+        if i < 3:
+            dY = dY * (Yi > 0)
+        dW_ref = dY.T @ A[i]
+        db_ref = dY.sum(axis=0)
+        scale = np.abs(dY).T @ np.abs(A[i])
+        assert np.all(np.abs(gW[i].cpu().numpy() - dW_ref) <= 2e-3 * scale + 1e-6), i
+        assert np.all(np.abs(gb[i].cpu().numpy() - db_ref) <= 2e-3 * np.abs(dY).sum(axis=0) + 1e-6), i
+        dY = dY @ Ws[i]
+
+
+def test_learned_proposer_trains_and_competes_with_random_starts():
+    # reduced configuration: 3000 training toys of 20k events, 6 held-out toys of 100k events;
+    # checks that training lowers the loss and that the global minimum used by the comparison
+    # (best GPU objective among converged starts) is the oracle's FP64 best among the clusters
+    from paper_1108_5882_gb300 import build, learned, pwa
+    build.build()
+    hh = pwa.Handle(0)
+    seed = inputs.SEED_BASE + 5
+    ws = inputs.wave_set_spread(16, seed)
+    waves = pwa.waves_from(ws)
+    Psi = learned.flat_psi(hh, waves, n_mc=500_000)
+    feats, targets, _, nacc = learned.make_training_set(hh, waves, Psi, 3000, 20_000, seed)
+    assert abs(float(nacc.double().mean()) - 20_000) < 500
+    prop = learned.Proposer(hh)
+    hist = learned.train(prop, feats, targets, epochs=8, batch=128, lr=2e-3)
+    assert hist[-1] < 0.8 * hist[0], hist
+    Vh = learned.random_truths(6, 16, seed + 1)
+    outs = []
+    Psi_np = Psi.cpu().numpy()
+    for t in range(6):
+        o = learned.evaluate_toy(hh, waves, Psi, prop, Vh[t], 100_000, seed + 1, 7 + t, P_rand=64)
+        if len(o["reps"]) >= 2:
+            A = o["A"].cpu().numpy()
+            f_or = [oracle.nll_grad(A, o["Vs"][r].astype(np.complex64)[None, :], Psi_np)[0][0] for r in o["reps"][:4]]
+            assert int(np.argmin(f_or)) == 0 or abs(min(f_or) - f_or[0]) < 1e-3 * abs(f_or[0]) * 1e-3, f_or
+        o.pop("A")
+        o.pop("kin")
+        outs.append(o)
+    s = learned.summarize(outs)
+    print("learned-vs-random (reduced):", s)
+    assert s["toys"] >= 4

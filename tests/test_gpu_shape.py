@@ -117,3 +117,48 @@ def test_shape_fits_of_uneven_channels(h):
         for q, (wv, kd) in enumerate(zip(fwave, fkind)):
             if kd == 0:
                 assert abs(x[2 * K + q] - ws.M[wv]) < abs(1.01 * ws.M[wv] - ws.M[wv])
+
+
+def test_shape_gradient_against_gpu_finite_differences(h):
+    # d f / d M_r and d f / d Gamma_r from pwa_nll_grad_shape vs central differences of the GPU
+    # objective itself, with the amplitudes recomputed by pwa_amplitudes at theta +- h
+    from paper_1108_5882_gb300 import pwa
+    K, n, n_mc = 6, 30_000, 60_000
+    ws = inputs.wave_set_spread(K, SEED + 500)
+    V = inputs.production_amplitudes(K, SEED + 500)
+    kin = dev(inputs.kinematics(n, SEED + 500, 4))
+    kin_mc = dev(inputs.kinematics(n_mc, SEED + 500, 5))
+    Vd = dev(V)
+    nll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(2 * K + 2, dtype=torch.float64, device="cuda")
+
+    def objective(waves, with_grad=False):
+        A = torch.zeros((K, n), dtype=torch.complex64, device="cuda")
+        Am = torch.zeros((K, n_mc), dtype=torch.complex64, device="cuda")
+        dM = torch.zeros((K, n), dtype=torch.complex64, device="cuda")
+        dW = torch.zeros((K, n), dtype=torch.complex64, device="cuda")
+        dMm = torch.zeros((K, n_mc), dtype=torch.complex64, device="cuda")
+        dWm = torch.zeros((K, n_mc), dtype=torch.complex64, device="cuda")
+        h.pwa_amplitudes(waves, kin, n, A, dM, dW)
+        h.pwa_amplitudes(waves, kin_mc, n_mc, Am, dMm, dWm)
+        dA = torch.stack([dM[2], dW[2]]).contiguous()
+        dAm = torch.stack([dMm[2], dWm[2]]).contiguous()
+        h.pwa_nll_grad_shape(A, dA, n, Am, dAm, n_mc, [2, 2], Vd, float(n), nll, grad)
+        torch.cuda.synchronize()
+        return nll.item(), grad.cpu().numpy().copy()
+
+    waves = pwa.waves_from(ws)
+    f0, g0 = objective(waves)
+    for q, field in ((0, 2), (1, 3)):  # mass, width of wave 2
+        step = 1e-4
+        wp = [list(w) for w in waves]
+        wm = [list(w) for w in waves]
+        wp[2][field] += step
+        wm[2][field] -= step
+        fp, _ = objective([tuple(w) for w in wp])
+        fm, _ = objective([tuple(w) for w in wm])
+        fd = (fp - fm) / (2 * step)
+        analytic = g0[2 * K + q]
+        # f ~ 1e5 is evaluated in FP32 per event: its rounding noise (~1e-3 absolute) / step
+        # bounds the FD error, far below the gradient's scale
+        assert abs(fd - analytic) <= 2e-3 * max(abs(analytic), 1e3) + 50.0, (q, fd, analytic)

@@ -384,3 +384,98 @@ def test_shape_objective_reduces_to_psi_form():
     assert abs(f - f2[0]) < 1e-11 * abs(f2[0])
     assert np.max(np.abs(gV - g2[0])) < 1e-9 * np.max(np.abs(g2[0]))
     assert gS[0] == 0.0
+
+
+# ---------------------------------------------------------------- angular moments ----------
+
+def test_real_spherical_harmonics_match_scipy_and_are_orthonormal():
+    # against scipy's associated Legendre functions (lpmv, Condon-Shortley phase) with the
+    # textbook normalisation, and orthonormality by Gauss-Legendre x trapezoid quadrature
+    from scipy.special import lpmv
+    g = np.random.default_rng(5)
+    for _ in range(20):
+        ct, ph = g.uniform(-1, 1), g.uniform(0, 2 * np.pi)
+        for L in range(5):
+            for M in range(-L, L + 1):
+                am = abs(M)
+                N = math.sqrt((2 * L + 1) / (4 * math.pi) * math.factorial(L - am) / math.factorial(L + am))
+                p = lpmv(am, L, ct)
+                ref = N * p if M == 0 else math.sqrt(2) * N * p * (math.cos(am * ph) if M > 0 else math.sin(am * ph))
+                assert abs(oracle.ylm_real(L, M, ct, ph) - ref) < 1e-13
+    xs, wx = np.polynomial.legendre.leggauss(24)
+    phis = np.linspace(0, 2 * np.pi, 48, endpoint=False)
+    Y = np.array([[[oracle.ylm_real(L, M, x, p) for p in phis] for x in xs] for L in range(5) for M in range(-L, L + 1)])
+    G = np.einsum("aij,bij,i->ab", Y, Y, wx) * (2 * np.pi / len(phis))
+    assert np.max(np.abs(G - np.eye(25))) < 1e-12
+
+
+def test_moments_of_flat_phase_space():
+    # flat phase space: every bin holds ~1/40 of the events, Y_00 = 1/sqrt(4 pi) times that
+    # fraction, and all L > 0 moments average to zero within their statistical error
+    kin = inputs.kinematics(400_000, 17, 3)
+    f = oracle.moments(kin)
+    assert abs(np.sum(f[:, 0]) - 1 / math.sqrt(4 * math.pi)) < 1e-12
+    assert np.all(np.abs(f[:, 0] * math.sqrt(4 * math.pi) - 1 / 40) < 5 * math.sqrt(1 / 40 / 400_000))
+    assert np.max(np.abs(f[:, 1:])) < 5 * 0.5 / math.sqrt(400_000 / 40) / 40
+
+
+# ---------------------------------------------------------------- MLP reference ------------
+
+def test_mlp_oracle_against_finite_differences():
+    # linear_backward and wta_loss gradients against central differences of their forward
+    from oracle import mlp
+    g = np.random.default_rng(8)
+    B, n_in, n_out = 5, 7, 6
+    X, W, b = g.normal(size=(B, n_in)), g.normal(size=(n_out, n_in)), g.normal(size=n_out)
+    R = g.normal(size=(B, n_out))
+
+    def obj(X, W, b):
+        return float(np.sum(R * mlp.linear(X, W, b, relu=True)))
+    Y = mlp.linear(X, W, b, relu=True)
+    dX, dW, db = mlp.linear_backward(X, W, Y, R, relu=True)
+    h = 1e-6
+    for arr, grad in ((X, dX), (W, dW), (b, db)):
+        it = np.nditer(arr, flags=["multi_index"])
+        for _ in it:
+            i = it.multi_index
+            old = arr[i]
+            arr[i] = old + h
+            fp = obj(X, W, b)
+            arr[i] = old - h
+            fm = obj(X, W, b)
+            arr[i] = old
+            assert abs((fp - fm) / (2 * h) - grad[i]) < 1e-6
+    C, K = 4, 3
+    out, tgt = g.normal(size=(B, C * 2 * K)), g.normal(size=(B, 2 * K))
+    loss, dout, win = mlp.wta_loss(out, tgt, C, K, 0.1)
+    for j in range(out.size):
+        o = out.reshape(-1)
+        old = o[j]
+        o[j] = old + h
+        fp = np.mean(mlp.wta_loss(out, tgt, C, K, 0.1)[0])
+        o[j] = old - h
+        fm = np.mean(mlp.wta_loss(out, tgt, C, K, 0.1)[0])
+        o[j] = old
+        assert abs((fp - fm) / (2 * h) - dout.reshape(-1)[j]) < 1e-6
+
+
+def test_wta_distance_is_phase_invariant_and_zero_at_target():
+    # d(e^{i phi} T, T) = 0 for every global phase: the loss sees no global phase (Eq. 1)
+    from oracle import mlp
+    K = 5
+    T = np.random.default_rng(9).normal(size=(1, 2 * K))
+    Tc = T[0, 0::2] + 1j * T[0, 1::2]
+    for phi in (0.0, 1.0, -2.5):
+        Vc = np.exp(1j * phi) * Tc
+        out = np.stack([Vc.real, Vc.imag], axis=-1).reshape(1, 2 * K)
+        loss, _, _ = mlp.wta_loss(out, T, 1, K, 0.0)
+        assert abs(loss[0]) < 1e-12
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    from oracle import mlp
+    x = np.array([1.0, 1.00390625, 1.0078125, 1.01171875, -3.14159, 1e-3, 65504.0], np.float32)
+    b = inputs.bf16_bits(x)
+    back = mlp.bf16_to_f64(b)
+    assert back[0] == 1.0 and back[1] == 1.0 and back[2] == 1.0078125 and back[3] == 1.015625  # ties to even
+    assert np.all(np.abs(back - x) <= np.abs(x) * 2.0 ** -8)
