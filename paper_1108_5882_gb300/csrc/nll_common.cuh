@@ -28,15 +28,19 @@ struct StreamReduceSmem {
     double S;
 };
 
-// t_c = sum_a Psi_ac V_a for c < K and S = sum_c conj(V_c) t_c (FP64), with every thread of
-// the block loading its share of Psi at once (one memory round trip instead of K dependent
-// ones) and fixed-order sums (thread parts in order, then a sequential sum over c).
-// scratch must hold NTHR double2.  Call with the whole block; returns S (valid in all threads).
+// t_c = sum_a Psi_ac V_a for c < K and S = sum_c conj(V_c) t_c (FP64).  Every thread of the
+// block loads its share of Psi at once (one memory round trip), and both sums are fixed-order
+// pairwise trees: GB300 executes FP64 with a long latency, so a sequential chain of K dependent
+// additions would dominate the whole finalisation.  scratch must hold NTHR double2 (and the
+// tree over c uses scratch again).  Call with the whole block; returns S in all threads.
 template <int NTHR>
 __device__ __forceinline__ double psi_times_v(const double2* __restrict__ Psi, const float2* sV, int K,
                                               double2* sT, double2* scratch, double* sS) {
     const int tid = threadIdx.x;
-    const int nparts = NTHR / K > 0 ? NTHR / K : 1;
+    int nparts = NTHR / K > 0 ? NTHR / K : 1;
+    int np2 = 1;  // parts rounded down to a power of two for the tree
+    while (np2 * 2 <= nparts) np2 *= 2;
+    nparts = np2;
     if (tid < nparts * K) {
         const int c = tid % K, part = tid / K;
         double tr = 0.0, ti = 0.0;
@@ -50,20 +54,27 @@ __device__ __forceinline__ double psi_times_v(const double2* __restrict__ Psi, c
         scratch[tid] = make_double2(tr, ti);
     }
     __syncthreads();
-    for (int c = tid; c < K; c += NTHR) {
-        double tr = 0.0, ti = 0.0;
-        for (int part = 0; part < nparts; ++part) {
-            tr += scratch[part * K + c].x;
-            ti += scratch[part * K + c].y;
+    // pairwise tree over the parts: level h adds part p + h into part p (p < h)
+    for (int hlf = nparts / 2; hlf > 0; hlf /= 2) {
+        if (tid < hlf * K) {
+            const double2 a = scratch[tid], b = scratch[tid + hlf * K];
+            scratch[tid] = make_double2(a.x + b.x, a.y + b.y);
         }
-        sT[c] = make_double2(tr, ti);
+        __syncthreads();
     }
+    for (int c = tid; c < K; c += NTHR) sT[c] = scratch[c];
     __syncthreads();
-    if (tid == 0) {
-        double S = 0.0;
-        for (int c = 0; c < K; ++c) S += (double)sV[c].x * sT[c].x + (double)sV[c].y * sT[c].y;
-        *sS = S;
+    // S: products per c, then a pairwise tree over c (padded with zeros to a power of two)
+    int kp = 1;
+    while (kp < K) kp *= 2;
+    for (int c = tid; c < kp; c += NTHR)
+        scratch[c].x = c < K ? (double)sV[c].x * sT[c].x + (double)sV[c].y * sT[c].y : 0.0;
+    __syncthreads();
+    for (int hlf = kp / 2; hlf > 0; hlf /= 2) {
+        for (int c = tid; c < hlf; c += NTHR) scratch[c].x += scratch[c + hlf].x;
+        __syncthreads();
     }
+    if (tid == 0) *sS = scratch[0].x;
     __syncthreads();
     return *sS;
 }
@@ -124,7 +135,7 @@ __device__ __forceinline__ void stream_reduce_finalize(float (&g)[2 * KMAX], ff 
     for (int vv = tid; vv < nch * NVu; vv += NTHR) {
         const int v = vv % NVu, ch = vv / NVu;
         const int cnt = ((int)gridDim.x - ch + nch - 1) / nch;
-        sm.sfin[vv] = ff_sum_strided(part, (int64_t)ch * NV + v, (int64_t)nch * NV, cnt);
+        sm.sfin[vv] = ff_sum_strided<32>(part, (int64_t)ch * NV + v, (int64_t)nch * NV, cnt);
     }
     __syncthreads();
     for (int v = tid; v < NVu; v += NTHR) {

@@ -279,11 +279,16 @@ def summarize(outs):
     # expected number of fits is 1/q for a per-start success rate q
     t_plain = t1 / qr if qr > 0 else float("inf")
     t_l, t_r = float(np.mean(tl)), float(np.mean(tr))
+    ql = float(np.mean(q_l))
+    # learned candidates used one at a time, like the plain method but in the network's order
+    t_learned_seq = t1 / ql if ql > 0 else float("inf")
     return dict(toys=len(hit_l), learned_reaches_global=float(np.mean(hit_l)), random_reaches_global=float(np.mean(hit_r)),
                 per_start_success_learned=float(np.mean(q_l)), per_start_success_random=qr,
                 wall_s_per_fit_learned=t_l, wall_s_per_fit_random=t_r, wall_s_single_start_fit=t1,
                 time_to_global_plain_s=t_plain, time_to_global_batched_s=t_r, time_to_global_learned_s=t_l,
-                speedup_batched_vs_plain=t_plain / t_r, speedup_learned_vs_plain=t_plain / t_l)
+                speedup_batched_vs_plain=t_plain / t_r, speedup_learned_vs_plain=t_plain / t_l,
+                time_to_global_learned_sequential_s=t_learned_seq,
+                speedup_learned_sequential_vs_plain=t_plain / t_learned_seq)
 
 
 def main():

@@ -129,8 +129,10 @@ def test_mlp_wta_loss_and_adam_match_oracle(h):
     pd, md, vd = dev(p), dev(m), dev(v)
     pb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
     h.pwa_mlp_adam(pd, dev(gr), md, vd, pb, 1e-3, 7)
+    # the kernel's hyperparameters are FP32 values; the oracle gets exactly those
+    f32 = lambda x: float(np.float32(x))
     p_ref, m_ref, v_ref = mlp.adam(p.astype(np.float64), gr.astype(np.float64), m.astype(np.float64),
-                                   v.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 7)
+                                   v.astype(np.float64), f32(1e-3), f32(0.9), f32(0.999), f32(1e-8), 7)
     # FP32 rounding is relative to the operands of each update, not to its (possibly smaller)
     # result; the FP32 constants b1, 1 - b1, b2, 1 - b2 carry their own representation error
     # (~3e-8 relative): a few roundings of u = 6e-8 each stay below 1e-6 of the operands
