@@ -267,8 +267,8 @@ pwa_status pwa_create(pwa_handle** out, int device) {
     h->device = device;
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (h->sm_count <= 0) h->sm_count = 1;
-    e = cudaMalloc(&h->counters, 64 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 64 * sizeof(unsigned));
+    e = cudaMalloc(&h->counters, pwa::HANDLE_COUNTER_BYTES);
+    if (e == cudaSuccess) e = cudaMemset(h->counters, 0, pwa::HANDLE_COUNTER_BYTES);
     if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
     if (e != cudaSuccess) {

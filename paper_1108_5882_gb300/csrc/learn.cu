@@ -2,11 +2,16 @@
 // spherical harmonics Y_LM(theta, phi), L <= 4 (40 bins x 25 = 1000 features), of a data
 // sample, and the same for toy samples drawn on the fly from many production-amplitude sets.
 //
-// Moments are accumulated as fixed-point integers (Y * 2^36 rounded to int64) with integer
-// atomics: integer addition is associative, so the sums do not depend on the order in which
-// threads and blocks arrive (the result is deterministic), and |Y| < 1 keeps 1e7 events far
-// from int64 overflow.  Toy events are generated, tested and accumulated without ever being
-// stored: each block owns a range of one toy's candidates.
+// Moments are accumulated as fixed-point integers (Y * 2^36 rounded to int64): integer addition
+// is associative, so the sums do not depend on the order in which events, warps and blocks are
+// added (the result is deterministic), and |Y| < 1 keeps 1e7 events far from int64 overflow.
+// Each warp owns a private accumulator [n_bins][25] in shared memory.  The events a warp takes
+// in one step are added one after the other: the event's lane broadcasts its 25 values by
+// shuffles, lane k adds value k, so no two lanes touch the same word and no atomics are needed
+// in the event loop (shared-memory 64-bit atomics serialise badly when lanes share a bin).  The
+// block sums its warps' accumulators and adds them to the grid's with integer atomics.  Toy
+// events are generated, tested and accumulated without ever being stored: each block owns a
+// range of one toy's candidates.
 //
 // Per toy t, the number of candidates is chosen so that about N_target events are accepted:
 // n_cand = N_target * C_t / S_t, with C_t the accept-reject envelope (the per-mass-interval bound
@@ -81,29 +86,64 @@ __device__ __forceinline__ int mass_bin(float m, int n_bins, float m_lo, float i
     return b < 0 ? 0 : (b >= n_bins ? n_bins - 1 : b);
 }
 
-__device__ __forceinline__ void add_event(unsigned long long* acc, int b, const float (&y)[LM]) {
+// Adds the events of the lanes in `mask` to the warp's accumulator wacc [n_bins][25]: per event
+// (in lane order) 25 shuffles from its lane, lane k adding component k.  Call with the whole warp.
+__device__ __forceinline__ void warp_add_events(long long* wacc, unsigned mask, int b, const float (&y)[LM]) {
+    const int lane = threadIdx.x & 31;
+    while (mask) {
+        const int e = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int be = __shfl_sync(0xffffffffu, b, e);
+        long long mine = 0;
 #pragma unroll
-    for (int k = 0; k < LM; ++k)
-        atomicAdd(acc + b * LM + k, (unsigned long long)__float2ll_rn(y[k] * FIX_SCALE));
+        for (int k = 0; k < LM; ++k) {
+            const float v = __shfl_sync(0xffffffffu, y[k], e);
+            if (lane == k) mine = __float2ll_rn(v * FIX_SCALE);
+        }
+        if (lane < LM) wacc[be * LM + lane] += mine;
+    }
 }
 
-// moments of given events: block-local accumulators flushed into acc [n_bins][25] (int64)
+// The warps' accumulators of the block summed and added to acc (integer atomics).
+__device__ __forceinline__ void block_flush(const long long* swacc, int nf, unsigned long long* __restrict__ acc) {
+    constexpr int NW = PWA_THREADS / 32;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += swacc[w * nf + i];
+        if (t) atomicAdd(acc + i, (unsigned long long)t);
+    }
+}
+
+// moments of given events: per-warp accumulators, flushed into acc [n_bins][25] (int64)
 __global__ void __launch_bounds__(PWA_THREADS) k_moments(const float* __restrict__ kin, int64_t n, int64_t ld,
                                                          int n_bins, float m_lo, float inv_w,
                                                          unsigned long long* __restrict__ acc) {
-    extern __shared__ unsigned long long sacc[];  // [n_bins * 25]
+    extern __shared__ long long swacc[];  // [PWA_THREADS / 32][n_bins * 25]
     __shared__ float sN[LM];
+    const int nf = n_bins * LM, lane = threadIdx.x & 31;
     ylm_norms(sN);
-    for (int i = threadIdx.x; i < n_bins * LM; i += blockDim.x) sacc[i] = 0ull;
+    for (int i = threadIdx.x; i < (PWA_THREADS / 32) * nf; i += blockDim.x) swacc[i] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    long long* wacc = swacc + (threadIdx.x >> 5) * nf;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform loop: the warp's first event decides, lanes past n idle
+    for (int64_t iw = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); iw < n; iw += stride) {
+        const int64_t i = iw + lane;
+        const bool has = i < n;
         float y[LM];
-        ylm25(__ldg(kin + ld + i), __ldg(kin + 2 * ld + i), sN, y);
-        add_event(sacc, mass_bin(__ldg(kin + i), n_bins, m_lo, inv_w), y);
+        int b = 0;
+        if (has) {
+            ylm25(__ldg(kin + ld + i), __ldg(kin + 2 * ld + i), sN, y);
+            b = mass_bin(__ldg(kin + i), n_bins, m_lo, inv_w);
+        } else {
+#pragma unroll
+            for (int k = 0; k < LM; ++k) y[k] = 0.f;
+        }
+        warp_add_events(wacc, __ballot_sync(0xffffffffu, has), b, y);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n_bins * LM; i += blockDim.x)
-        if (sacc[i]) atomicAdd(acc + i, sacc[i]);
+    block_flush(swacc, nf, acc);
 }
 
 // feat = acc * 2^-36 / count (count from a device counter, or the given n)
@@ -172,16 +212,18 @@ __global__ void __launch_bounds__(PWA_THREADS) k_toy_moments(ToyWaves tw, const 
                                                              uint32_t stream_base, int n_bins,
                                                              unsigned long long* __restrict__ acc,
                                                              long long* __restrict__ n_acc) {
-    extern __shared__ unsigned long long sacc[];  // [n_bins * 25]
+    extern __shared__ long long swacc[];  // [PWA_THREADS / 32][n_bins * 25]
     __shared__ float sN[LM];
     __shared__ float2 sV[PWA_MAX_WAVES];
     __shared__ int scount[PWA_THREADS / 32];
     const int t = blockIdx.x;
     const int K = tw.wt.K;
+    const int nf = n_bins * LM, lane = threadIdx.x & 31;
     ylm_norms(sN);
     if (threadIdx.x < K) sV[threadIdx.x] = V[(int64_t)t * K + threadIdx.x];
-    for (int i = threadIdx.x; i < n_bins * LM; i += blockDim.x) sacc[i] = 0ull;
+    for (int i = threadIdx.x; i < (PWA_THREADS / 32) * nf; i += blockDim.x) swacc[i] = 0;
     __syncthreads();
+    long long* wacc = swacc + (threadIdx.x >> 5) * nf;
     const long long nc = n_cand[t];
     const float Cf = (float)C[t];
     const long long chunk = (nc + gridDim.y - 1) / gridDim.y;
@@ -190,28 +232,44 @@ __global__ void __launch_bounds__(PWA_THREADS) k_toy_moments(ToyWaves tw, const 
     if (j1 > nc) j1 = nc;
     const float inv_w = (float)((double)n_bins / (3.0 - 0.99));
     int cnt = 0;
-    for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const Candidate cd = candidate(seed, stream_base + (uint32_t)t, j);
-        if (cd.u * Cf < intensity(tw.wt, sV, cd)) {
+    // warp-uniform loop: the warp's first candidate decides, lanes past j1 idle
+    for (long long jw = j0 + (threadIdx.x & ~31); jw < j1; jw += blockDim.x) {
+        const long long j = jw + lane;
+        bool take = false;
+        Candidate cd;
+        if (j < j1) {
+            cd = candidate(seed, stream_base + (uint32_t)t, j);
+            take = cd.u * Cf < intensity(tw.wt, sV, cd);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        if (mask) {
             float y[LM];
-            ylm25(cd.ct, cd.ph, sN, y);
-            add_event(sacc, mass_bin(cd.m, n_bins, 0.99f, inv_w), y);
-            ++cnt;
+            int b = 0;
+            if (take) {
+                ylm25(cd.ct, cd.ph, sN, y);
+                b = mass_bin(cd.m, n_bins, 0.99f, inv_w);
+            } else {
+#pragma unroll
+                for (int k = 0; k < LM; ++k) y[k] = 0.f;
+            }
+            warp_add_events(wacc, mask, b, y);
+            cnt += take ? 1 : 0;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0) scount[threadIdx.x >> 5] = cnt;
+    if (lane == 0) scount[threadIdx.x >> 5] = cnt;
     __syncthreads();
-    unsigned long long* at = acc + (int64_t)t * n_bins * LM;
-    for (int i = threadIdx.x; i < n_bins * LM; i += blockDim.x)
-        if (sacc[i]) atomicAdd(at + i, sacc[i]);
+    block_flush(swacc, nf, acc + (int64_t)t * nf);
     if (threadIdx.x == 0) {
         long long c = 0;
         for (int w = 0; w < PWA_THREADS / 32; ++w) c += scount[w];
         atomicAdd(reinterpret_cast<unsigned long long*>(n_acc + t), (unsigned long long)c);
     }
 }
+
+// per-warp accumulators of the moments kernels (n_bins <= 64: at most 102,400 bytes)
+size_t moments_smem(int n_bins) { return sizeof(long long) * (PWA_THREADS / 32) * (size_t)n_bins * LM; }
 
 }  // namespace
 
@@ -225,7 +283,8 @@ cudaError_t launch_moments(const float* kin, int64_t n, int64_t ld, int n_bins, 
     int64_t blocks = (n + PWA_THREADS - 1) / PWA_THREADS;
     if (blocks > (int64_t)sm_count * 4) blocks = (int64_t)sm_count * 4;
     if (blocks < 1) blocks = 1;
-    const size_t smem = sizeof(unsigned long long) * n_bins * LM;
+    const size_t smem = moments_smem(n_bins);
+    cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_moments<<<(unsigned)blocks, PWA_THREADS, smem, st>>>(kin, n, ld, n_bins, (float)m_lo,
                                                            (float)(n_bins / (m_hi - m_lo)), acc);
     e = cudaGetLastError();
@@ -256,7 +315,8 @@ cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const doub
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int bpt = 16;  // blocks per toy
-    const size_t smem = sizeof(unsigned long long) * n_bins * LM;
+    const size_t smem = moments_smem(n_bins);
+    cudaFuncSetAttribute(k_toy_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_toy_moments<<<dim3(T, bpt), PWA_THREADS, smem, st>>>(tw, V, C, nc, seed, stream_base, n_bins, acc, n_acc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

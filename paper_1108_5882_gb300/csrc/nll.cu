@@ -12,9 +12,9 @@
 //  * k_nll_stream  (one parameter set): HBM-bound stream over A (8K bytes per event).  Each
 //    thread takes two events per 16-byte load per wave, holds V in shared memory, and keeps
 //    FP32 gradient partials in registers.  Warp partials are combined by a reduce-scatter
-//    (31 shuffles for 32 values), blocks write double-single partials, and the last block to
-//    finish (completion counter) sums the partials in block order and adds the FP64
-//    normalisation term: one launch per evaluation, deterministic.
+//    (31 shuffles for 32 values) and then summed exactly in fixed point; the last block of the
+//    grid adds the normalisation term (nll_common.cuh): one launch per evaluation,
+//    deterministic.
 //  * k_nll_batched (P > 1 parameter sets, multi-start): the event x wave x start complex
 //    contraction U = A V^T, W = U / |U|^2, G = A^H W on FP32 FMA pipes, tiled through shared
 //    memory (an A tile of E events feeds both contractions), with per-start compensated
@@ -22,8 +22,10 @@
 //    the normalisation term in FP64.
 //
 // Sec. 2 precision remark: amplitudes in single precision, the final sum in double
-// precision with a tree-like summation order; here every long sum is carried as a
-// double-single pair and combined along a fixed tree (thread -> warp -> block -> grid).
+// precision with a tree-like summation order.  Here the per-thread sums are FP32 (gradient) or
+// double-single (ln I) over a bounded number of events, warp sums a fixed tree; across warps
+// and blocks the single-set kernels sum exactly (integer fixed point) and the batched kernel
+// carries double-single pairs in a fixed order.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -52,6 +54,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
 
     const int tid = threadIdx.x;
     if (tid < KMAX) sV[tid] = tid < K ? V[tid] : make_float2(0.f, 0.f);
+    stream_reduce_init<KMAX, PWA_THREADS>(red, Psi, K);
     __syncthreads();
 
     float g[NG];
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(TmaCfg<KMAX>::E) k_nll_tma(
         for (int st = 0; st < S; ++st) mbar_init(&full[st], 1);
         fence_mbar_init();
     }
+    stream_reduce_init<KMAX, E>(red, Psi, K);
     __syncthreads();
     auto issue = [&](int64_t j) {  // tile index j of this block -> stage j % S
         const int st = (int)(j % S);
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(TmaCfg<KMAX>::E) k_nll_tma(
 }
 
 // Second half of the unfused variant: one block sums the G block partials in block order and
-// adds the FP64 normalisation term (same arithmetic and order as the fused last block).
+// adds the FP64 normalisation term.
 template <int KMAX, bool GRAD>
 __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream_final(
     const float2* __restrict__ part, int G, int K, const float2* __restrict__ V, const double2* __restrict__ Psi,

@@ -4,12 +4,12 @@
 // own, host code under a memory manager that forbids allocations after start-up, or plug-ins
 // of a larger program that owns all device memory.  pwa_nll_grad needs a handle, and both the
 // handle and its workspace are allocated with cudaMalloc.  pwa_nll_grad_noalloc needs neither:
-// its scratch (block partial sums, the completion counter, the non-finite flag) lives in the
+// its scratch (block partial sums, the completion counter, flags and fixed-point sums) lives in the
 // file-scope device array below, which every GPU that loads the library holds until exit.
 //
 // Limits: K <= PWA_MAX_WAVES and at most NOALLOC_MAX_BLOCKS blocks per launch (the launch is
 // capped there; any n is accepted).  The scratch is shared by every call on a device and keeps
-// the last call's contents: each call clears the counter and flag words on its stream before
+// the last call's contents: each call clears the control words on its stream before
 // its kernel runs, so calls ordered on one stream are safe, while calls that overlap on the
 // GPU (different streams, different host threads) race on the scratch and give wrong results.
 #include <cstring>
@@ -21,9 +21,11 @@ namespace {
 
 constexpr int NOALLOC_MAX_BLOCKS = 1024;
 constexpr int NOALLOC_MAX_DEVICES = 64;
-constexpr size_t NOALLOC_HEADER = 256;  // counter, flag, status words
+constexpr size_t NOALLOC_HEADER = 8448;  // control words of the launch, then the status word
+constexpr size_t NOALLOC_STATUS_OFFSET = pwa::STREAM_CTRL_BYTES;
+static_assert(NOALLOC_STATUS_OFFSET + sizeof(int) <= NOALLOC_HEADER, "noalloc header");
 constexpr size_t NOALLOC_PART_BYTES = sizeof(float2) * (size_t)NOALLOC_MAX_BLOCKS * (1 + 2 * PWA_MAX_WAVES);
-constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_PART_BYTES;  // 1,056,768 + 256 bytes
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_PART_BYTES;  // 1,056,768 + 8448 bytes
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -87,10 +89,10 @@ extern "C" PWA_API pwa_status pwa_nll_grad_noalloc(const float* A, int K, int64_
     unsigned char* b = reinterpret_cast<unsigned char*>(base);
     unsigned* counter = reinterpret_cast<unsigned*>(b);
     int* badw = reinterpret_cast<int*>(b + 4);
-    int* status = reinterpret_cast<int*>(b + 8);
+    int* status = reinterpret_cast<int*>(b + NOALLOC_STATUS_OFFSET);
     float2* part = reinterpret_cast<float2*>(b + NOALLOC_HEADER);
     // the previous call's words may be left set (e.g. the status bit of a non-finite set)
-    e = cudaMemsetAsync(b, 0, 16, st);
+    e = cudaMemsetAsync(b, 0, NOALLOC_STATUS_OFFSET + sizeof(int), st);
     if (e == cudaSuccess)
         e = pwa::launch_nll_grad_scratch(reinterpret_cast<const float2*>(A), K, n, ld,
                                          reinterpret_cast<const float2*>(V), reinterpret_cast<const double2*>(Psi),

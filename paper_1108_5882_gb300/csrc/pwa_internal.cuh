@@ -119,6 +119,31 @@ __device__ __forceinline__ ff ff_sum_strided(const float2* __restrict__ x, int64
 // Non-finite or non-positive intensity test (the likelihood needs ln I_i).
 __device__ __forceinline__ bool intensity_ok(float I) { return I > 0.f && I < INFINITY; }
 
+// Control words of a one-parameter-set likelihood launch (device memory; the words marked
+// "zero" are zero between launches: the launch's last block clears them):
+//   byte 0                   completion ticket (zero)
+//   byte 4                   flag word, STREAM_FLAG_* (zero)
+//   STREAM_CTRL_LIMB_OFFSET  fixed-point words [STREAM_NV_MAX + 1][FIX_WORDS] (int64, zero) of the
+//                            grid sums of ln I (value 0), of the 2K gradient components (values
+//                            1..2K) and of S = sum_c Re(conj(V_c) t_c) (value STREAM_NV_MAX)
+//   STREAM_CTRL_T_OFFSET     t_c = sum_a Psi_ac V_a, double2 [PWA_MAX_WAVES] (written each launch)
+constexpr int STREAM_FLAG_NONFINITE = 1;  // some intensity was <= 0 or not finite
+constexpr int STREAM_NV_MAX = 1 + 2 * PWA_MAX_WAVES;
+constexpr int FIX_WORDS = 6;              // two tiers of three 42-bit limbs per value
+constexpr size_t STREAM_CTRL_LIMB_OFFSET = 256;
+constexpr size_t STREAM_CTRL_T_OFFSET = 6656;
+constexpr size_t STREAM_CTRL_BYTES = 8192;
+constexpr size_t HANDLE_COUNTER_BYTES = 8192;  // the handle's control words
+static_assert(STREAM_CTRL_LIMB_OFFSET + 8 * FIX_WORDS * (STREAM_NV_MAX + 1) <= STREAM_CTRL_T_OFFSET, "control words");
+static_assert(STREAM_CTRL_T_OFFSET + 16 * PWA_MAX_WAVES <= STREAM_CTRL_BYTES, "control words");
+static_assert(STREAM_CTRL_BYTES <= HANDLE_COUNTER_BYTES, "control words");
+__host__ __device__ inline long long* stream_limbs(unsigned* counter) {
+    return reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(counter) + STREAM_CTRL_LIMB_OFFSET);
+}
+__host__ __device__ inline double2* stream_psi_t(unsigned* counter) {
+    return reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(counter) + STREAM_CTRL_T_OFFSET);
+}
+
 // ---------------------------------------------------------------- launchers --------------
 // All launchers validate nothing: the C ABI layer has done it.  They return the CUDA launch
 // error (cudaSuccess on success).

@@ -197,14 +197,20 @@ def test_learned_proposer_trains_and_competes_with_random_starts():
     outs = []
     Psi_np = Psi.cpu().numpy()
     for t in range(6):
-        o = learned.evaluate_toy(hh, waves, Psi, prop, Vh[t], 100_000, seed + 1, 7 + t, P_rand=64)
-        if len(o["reps"]) >= 2:
+        o = learned.evaluate_toy(hh, waves, Psi, prop, Vh[t], 100_000, seed + 1, 7 + t, P_rand=64, max_seq=16)
+        reps, _ = learned.cluster_minima(o["Vs"], o["fs"], o["ok"])
+        assert reps and abs(o["fs"][reps[0]] - o["f_best"]) == 0.0
+        if len(reps) >= 2:
             A = o["A"].cpu().numpy()
-            f_or = [oracle.nll_grad(A, o["Vs"][r].astype(np.complex64)[None, :], Psi_np)[0][0] for r in o["reps"][:4]]
+            f_or = [oracle.nll_grad(A, o["Vs"][r].astype(np.complex64)[None, :], Psi_np)[0][0] for r in reps[:4]]
             assert int(np.argmin(f_or)) == 0 or abs(min(f_or) - f_or[0]) < 1e-3 * abs(f_or[0]) * 1e-3, f_or
+        # a sequential method stops at its first fit that reaches the global minimum, or after
+        # its last start
+        assert o["plain_hit"] or o["n_plain"] == 16
+        assert o["learned_seq_hit"] or o["n_learned_seq"] == prop.C + 16
         o.pop("A")
-        o.pop("kin")
         outs.append(o)
     s = learned.summarize(outs)
     print("learned-vs-random (reduced):", s)
-    assert s["toys"] >= 4
+    assert s["toys"] == 6
+    assert s["learned_sequential_reached"] >= 5 / 6 and s["plain_reached"] >= 0.5

@@ -184,6 +184,27 @@ def test_deterministic_bitwise(h):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def test_gradient_sums_in_the_coarse_fixed_point_tier(h):
+    # One parameter set: the grid sums are exact fixed point in two tiers, trunc(|x| 2^64) for
+    # warp sums |x| < 2^61 and |x| 2^-37 above.  |V| = 1e-18 makes every event's gradient term
+    # 1e18, so the warp sums of this sample (>= 32 events each) land in the coarse tier.  The
+    # result must agree with the oracle, and the words must be clean for the next evaluation.
+    K, n = 2, 40_000
+    A = np.zeros((K, n), np.complex64)
+    A[0] = 1.0
+    A[1] = 0.5j * np.exp(1j * np.linspace(0, 6, n)).astype(np.complex64)
+    Psi = oracle.normint((np.random.default_rng(2).normal(size=(K, 64)) + 0j).astype(np.complex64))
+    p = make_problem(16, 20_000, 20_000, SEED + 510, accept_reject=False)
+    V16 = p.V_true[None, :]
+    before = gpu_nll_grad(h, p.A, p.n, V16, p.Psi)
+    V = np.array([[1e-18, 3e-19 - 2e-19j]], np.complex64)
+    f, g = gpu_nll_grad(h, A, n, V, Psi)
+    check_nll(f, g, A, V, Psi)
+    assert np.abs(g).max() > 2.0 ** 61 * 32
+    after = gpu_nll_grad(h, p.A, p.n, V16, p.Psi)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+
+
 def test_padding_is_never_read_as_events(h):
     # NaN in every padding column must not change the result
     p = make_problem(16, 9_999, 9_999, SEED + 500, accept_reject=False)

@@ -313,6 +313,18 @@ def test_table_storage_matches_paper():
     assert abs(size / 2 ** 30 - gold["paper_gb"]) < gold["tolerance_gb"]
 
 
+def test_philox_matches_published_known_answers():
+    # The toy generator's counter-based generator, Philox4x32-10 (Salmon et al., SC'11), against
+    # the known-answer vectors published with its reference library.  The GPU generator is tied
+    # to this oracle candidate by candidate (test_generator_matches_oracle).
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.json")) as fh:
+        gold = json.load(fh)
+    for v in gold["vectors"]:
+        ctr = tuple(int(x, 16) for x in v["ctr"])
+        key = tuple(int(x, 16) for x in v["key"])
+        assert list(oracle.philox4x32(ctr, key)) == [int(x, 16) for x in v["out"]]
+
+
 def test_tree_sum_beats_sequential_fp32_sum():
     # Sec. 2 precision remark: a sequential single-precision loop sum of ln I drifts at 1e6
     # terms while a pairwise (tree) sum stays close to the FP64 sum.  Demonstration.
