@@ -126,8 +126,11 @@ void orc_normint(int K, int64_t n, const float* A, int64_t ld, const float* w, d
 /* f(V) and g(V) for P parameter sets.  A: complex64 interleaved [K][ld]; V: complex double
  * [P][K]; Psi: complex double [K][K].  Outputs nll[P], grad[P][2K] = (Re g_c, Im g_c).
  * cond_f[P] = max(|f|, sum_i |ln I_i|, n_factor*|S|) and cond_g[P][K] =
- * 2 sum_i |A_ic||u_i|/I_i + 2 n_factor sum_a |Psi_ac||V_a| are the scales the parity
- * tolerances are taken relative to (either may be NULL).
+ * 2 sum_i |A_ic| s_i / I_i + 2 n_factor sum_a |Psi_ac||V_a|, s_i = sum_a |V_a||A_ia| >= |u_i|,
+ * are the scales the parity tolerances are taken relative to (either may be NULL).  s_i is the
+ * forward-error scale of the sum u_i: a single-precision evaluation of u_i (Sec. 2 precision
+ * remark) is off by about eps * s_i, which moves the term conj(A_ic)/conj(u_i) by about
+ * |A_ic| eps s_i / I_i, large where u_i nearly cancels (s_i >> |u_i|).
  * Returns the number of parameter sets with a non-positive or non-finite intensity at some
  * event; those get nll = +inf and a zero gradient. */
 int orc_nll_grad(int K, int64_t n, const float* A, int64_t ld, int P, const double* Vd,
@@ -148,9 +151,11 @@ int orc_nll_grad(int K, int64_t n, const float* A, int64_t ld, int P, const doub
         for (int c = 0; c < K; ++c) { gre[c].s = gre[c].c = gim[c].s = gim[c].c = 0.0; gsc[c] = 0.0; }
         for (int64_t i = 0; i < n; ++i) {
             cplx u = 0.0;
+            double su = 0.0;
             for (int a = 0; a < K; ++a) {
                 Ai[a] = A[2 * ((int64_t)a * ld + i)] + I * A[2 * ((int64_t)a * ld + i) + 1];
                 u += Vp[a] * Ai[a];
+                su += cabs(Vp[a]) * cabs(Ai[a]);
             }
             double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
             if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; continue; }
@@ -162,7 +167,7 @@ int orc_nll_grad(int K, int64_t n, const float* A, int64_t ld, int P, const doub
                 cplx t = conj(Ai[c]) * u / Ii;
                 nsum_add(&gre[c], -2.0 * creal(t));
                 nsum_add(&gim[c], -2.0 * cimag(t));
-                gsc[c] += 2.0 * cabs(Ai[c]) * cabs(u) / Ii;
+                gsc[c] += 2.0 * cabs(Ai[c]) * su / Ii;
             }
         }
         /* normalisation term S = sum_ab V_a conj(V_b) Psi_ab and its gradient 2 n sum_a Psi_ac V_a */

@@ -548,6 +548,272 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
         if (sBad[p]) bad[p0 + p] = 1;
 }
 
+// ----------------------------------------------------------------------- P sets, pipelined
+// The same contraction with larger register tiles and the amplitude tile staged by bulk copies
+// (K <= 32): tiles of E = 128 events x PB = 64 starts per block, one block per SM.
+//  * U = A V^T: thread (te, tp) holds 8 events x 4 starts (events 2 te + {0,1} + 32 r, starts
+//    2 tp + {0,1} + 32 s): per wave 6 shared 16-byte loads feed 128 FMAs.
+//  * G = A^H W: the four event quarters of the tile are summed by four groups of 64 threads;
+//    thread (q, ta, tg) holds waves ta + 8 k (k < K/8) x starts tg + 8 s (s < 8) over its
+//    quarter's events: per event pair 4 + 8 loads feed 256 FMAs (K = 32).  The groups' FP32
+//    partials are added to the block's double-single G in four phases every FLUSH tiles.
+//  * Rows of the shared tiles are padded to E + 2 (a stride of 4 banks), so the eight wave
+//    rows (or the four start rows) that a warp reads hit distinct banks.
+//  * Thread 0 keeps two stages of K row copies in flight (cp.async.bulk, completion counted
+//    on each stage's mbarrier); every wait is bounded (a timeout flags the error and leaves).
+template <int KMAX>
+struct Batched2Cfg {
+    static constexpr int E = 128, PB = 64, NT = PWA_THREADS;
+    static constexpr int EA = E + 2;  // float2 row stride of sA and sW
+    static constexpr int S = 2;       // amplitude stages
+    static constexpr int GW = KMAX / 8;  // G waves per thread
+    static constexpr int FLUSH = 4;   // tiles between flushes of G
+    static constexpr size_t OFF_A = 64;  // after the stage mbarriers
+    static constexpr size_t OFF_V = OFF_A + sizeof(float2) * S * KMAX * EA;
+    static constexpr size_t OFF_W = OFF_V + sizeof(float2) * KMAX * PB;
+    static constexpr size_t OFF_G = OFF_W + sizeof(float2) * PB * EA;
+    static constexpr size_t OFF_L = OFF_G + sizeof(float4) * KMAX * PB;
+    static constexpr size_t OFF_B = OFF_L + sizeof(ff) * PB;
+    static constexpr size_t SMEM = OFF_B + sizeof(int) * (PB + 4);
+    static_assert(KMAX % 8 == 0 && KMAX <= 32, "pipelined batched kernel: K <= 32");
+};
+
+template <int KMAX>
+__global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
+    const float2* __restrict__ A, int K, int64_t n, int64_t ld, const float2* __restrict__ V, int P,
+    int64_t ev_per_chunk, float2* __restrict__ part, int* __restrict__ bad, int with_grad, int* __restrict__ status) {
+    using C = Batched2Cfg<KMAX>;
+    constexpr int E = C::E, PB = C::PB, EA = C::EA, S = C::S, GW = C::GW;
+    extern __shared__ __align__(128) unsigned char bsm[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(bsm);
+    float2* sA = reinterpret_cast<float2*>(bsm + C::OFF_A);  // [S][KMAX][EA]
+    float2* sV = reinterpret_cast<float2*>(bsm + C::OFF_V);  // [KMAX][PB]
+    float2* sW = reinterpret_cast<float2*>(bsm + C::OFF_W);  // [PB][EA]
+    float4* sG = reinterpret_cast<float4*>(bsm + C::OFF_G);  // [KMAX][PB] complex double-single
+    ff* sL = reinterpret_cast<ff*>(bsm + C::OFF_L);          // [PB]
+    int* sBad = reinterpret_cast<int*>(bsm + C::OFF_B);      // [PB], then the timeout word
+
+    const int tid = threadIdx.x;
+    const int p0 = blockIdx.y * PB;
+    const int NV = 1 + 2 * K;
+    const int K4 = (K + 3) & ~3;
+    const int64_t e_begin = (int64_t)blockIdx.x * ev_per_chunk;
+    int64_t e_end = e_begin + ev_per_chunk;
+    if (e_end > n) e_end = n;
+    const int64_t ntile = e_begin < e_end ? (e_end - e_begin + E - 1) / E : 0;
+
+    for (int i = tid; i < S * KMAX * EA; i += PWA_THREADS) sA[i] = make_float2(0.f, 0.f);
+    for (int idx = tid; idx < KMAX * PB; idx += PWA_THREADS) {
+        const int a = idx / PB, p = idx % PB;
+        sV[idx] = (a < K && p0 + p < P) ? V[(int64_t)(p0 + p) * K + a] : make_float2(0.f, 0.f);
+        sG[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int p = tid; p < PB; p += PWA_THREADS) {
+        sL[p] = ff_zero();
+        sBad[p] = 0;
+    }
+    if (tid == 0) {
+        sBad[PB] = 0;
+        for (int st = 0; st < S; ++st) mbar_init(&mbar[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // tile j -> stage j % S: K row copies of its (even) event count
+    auto issue = [&](int64_t j) {
+        const int st = (int)(j % S);
+        const int64_t e0 = e_begin + j * E;
+        int64_t ev = e_end - e0;
+        if (ev > E) ev = E;
+        ev = (ev + 1) & ~(int64_t)1;  // ld is even: the extra column is padding inside the row
+        const uint32_t row_bytes = (uint32_t)(ev * sizeof(float2));
+        mbar_arrive_expect_tx(&mbar[st], row_bytes * (uint32_t)K);
+        for (int a = 0; a < K; ++a)
+            bulk_copy_g2s(sA + ((size_t)st * KMAX + a) * EA, A + a * ld + e0, row_bytes, &mbar[st]);
+    };
+    if (tid == 0) {
+        fence_proxy_async_smem();  // the zero fill above precedes the copies into the stages
+        for (int64_t j = 0; j < ntile && j < S; ++j) issue(j);
+    }
+
+    // GEMM1 coordinates
+    const int te = tid & 15, tp = tid >> 4;
+    // GEMM2 coordinates
+    const int q = tid >> 6, ta = tid & 7, tg = (tid >> 3) & 7;
+
+    ff lsum[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) lsum[s] = ff_zero();
+    float gacc[GW][8][2];
+#pragma unroll
+    for (int k = 0; k < GW; ++k)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) gacc[k][s][0] = gacc[k][s][1] = 0.f;
+
+    auto flush_g = [&]() {
+        for (int ph = 0; ph < 4; ++ph) {
+            if (q == ph) {
+#pragma unroll
+                for (int k = 0; k < GW; ++k)
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        float4* dst = sG + (ta + 8 * k) * PB + (tg + 8 * s);
+                        const float4 cur = *dst;
+                        const ff re = ff_add_f(ff{cur.x, cur.y}, gacc[k][s][0]);
+                        const ff im = ff_add_f(ff{cur.z, cur.w}, gacc[k][s][1]);
+                        *dst = make_float4(re.hi, re.lo, im.hi, im.lo);
+                        gacc[k][s][0] = gacc[k][s][1] = 0.f;
+                    }
+            }
+            __syncthreads();
+        }
+    };
+
+    int64_t timeout_at = -1;
+    for (int64_t j = 0; j < ntile; ++j) {
+        const int st = (int)(j % S);
+        const uint32_t parity = (uint32_t)((j / S) & 1);
+        const bool ok = mbar_wait_bounded(&mbar[st], parity, 2000000000ull);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            timeout_at = j;
+            break;
+        }
+        const int64_t e0 = e_begin + j * E;
+        const int nvalid = (int)((e_end - e0) < E ? (e_end - e0) : E);
+        const float2* sAs = sA + (size_t)st * KMAX * EA;
+        // an odd event count copies one padding column: clear it before use (NaN-safe)
+        if ((nvalid & 1) && tid < K) sA[((size_t)st * KMAX + tid) * EA + nvalid] = make_float2(0.f, 0.f);
+        if (nvalid & 1) __syncthreads();
+
+        // ---- GEMM1: U[e][p] = sum_a A[a][e] V[p][a]
+        float u[8][4][2];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) u[i][s][0] = u[i][s][1] = 0.f;
+        const float2* pA = sAs + 2 * te;
+        const float2* pV = sV + 2 * tp;
+        for (int a0 = 0; a0 < K4; a0 += 4)
+#pragma unroll
+            for (int da = 0; da < 4; ++da) {
+                const int a = a0 + da;
+                float4 av[4], vv[2];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) av[r] = *reinterpret_cast<const float4*>(pA + a * EA + 32 * r);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) vv[s] = *reinterpret_cast<const float4*>(pV + a * PB + 32 * s);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        // events (2r: av.x,av.y) (2r+1: av.z,av.w); starts (2s: vv.x,vv.y) (2s+1: vv.z,vv.w)
+                        u[2 * r][2 * s][0] += av[r].x * vv[s].x - av[r].y * vv[s].y;
+                        u[2 * r][2 * s][1] += av[r].x * vv[s].y + av[r].y * vv[s].x;
+                        u[2 * r][2 * s + 1][0] += av[r].x * vv[s].z - av[r].y * vv[s].w;
+                        u[2 * r][2 * s + 1][1] += av[r].x * vv[s].w + av[r].y * vv[s].z;
+                        u[2 * r + 1][2 * s][0] += av[r].z * vv[s].x - av[r].w * vv[s].y;
+                        u[2 * r + 1][2 * s][1] += av[r].z * vv[s].y + av[r].w * vv[s].x;
+                        u[2 * r + 1][2 * s + 1][0] += av[r].z * vv[s].z - av[r].w * vv[s].w;
+                        u[2 * r + 1][2 * s + 1][1] += av[r].z * vv[s].w + av[r].w * vv[s].z;
+                    }
+            }
+        // ---- epilogue: I = |U|^2, ln I, W = U / I -> sW[p][e]
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int p = 2 * tp + (s & 1) + 32 * (s >> 1);
+            const bool pv = p0 + p < P;
+            float lpart = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = 2 * te + 32 * r;
+                float w[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float ur = u[2 * r + h][s][0], ui = u[2 * r + h][s][1];
+                    const float I = ur * ur + ui * ui;
+                    float wr = 0.f, wi = 0.f;
+                    if (pv && e + h < nvalid) {
+                        if (intensity_ok(I)) {
+                            lpart += __logf(I);
+                            const float rc = __frcp_rn(I);
+                            wr = ur * rc;
+                            wi = ui * rc;
+                        } else {
+                            sBad[p] = 1;
+                        }
+                    }
+                    w[2 * h] = wr;
+                    w[2 * h + 1] = wi;
+                }
+                *reinterpret_cast<float4*>(sW + p * EA + e) = make_float4(w[0], w[1], w[2], w[3]);
+            }
+            lsum[s] = ff_add_f(lsum[s], lpart);
+        }
+        __syncthreads();
+        // ---- GEMM2: G[a][p] += sum_e conj(A[a][e]) W[p][e] over this thread's event quarter
+        if (with_grad) {
+            const float2* qA = sAs + ta * EA + 32 * q;
+            const float2* qW = sW + tg * EA + 32 * q;
+#pragma unroll 2
+            for (int e = 0; e < 32; e += 2) {
+                float4 av[GW], wv[8];
+#pragma unroll
+                for (int k = 0; k < GW; ++k) av[k] = *reinterpret_cast<const float4*>(qA + 8 * k * EA + e);
+#pragma unroll
+                for (int s = 0; s < 8; ++s) wv[s] = *reinterpret_cast<const float4*>(qW + 8 * s * EA + e);
+#pragma unroll
+                for (int k = 0; k < GW; ++k)
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        gacc[k][s][0] += av[k].x * wv[s].x + av[k].y * wv[s].y + av[k].z * wv[s].z + av[k].w * wv[s].w;
+                        gacc[k][s][1] += av[k].x * wv[s].y - av[k].y * wv[s].x + av[k].z * wv[s].w - av[k].w * wv[s].z;
+                    }
+            }
+        }
+        __syncthreads();  // every thread is done with stage st and sW
+        if (tid == 0 && j + S < ntile) {
+            fence_proxy_async_smem();
+            issue(j + S);
+        }
+        if (with_grad && (j % C::FLUSH) == C::FLUSH - 1) flush_g();
+    }
+    if (timeout_at >= 0) {
+        // a stage never completed: flag the error, then wait (bounded) for the copies still in
+        // flight (tiles timeout_at .. timeout_at + S - 1) so that none lands after the block exits
+        if (tid == 0) {
+            atomicOr(status, 2);
+            sBad[PB] = 1;
+            for (int64_t jj = timeout_at; jj < ntile && jj < timeout_at + S; ++jj)
+                mbar_wait_bounded(&mbar[jj % S], (uint32_t)((jj / S) & 1), 100000000ull);
+        }
+        __syncthreads();
+    }
+    if (with_grad) flush_g();
+    // ln I: reduce the 16 GEMM1 event groups (lanes te = 0..15 of a half warp) per start
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        ff v = lsum[s];
+#pragma unroll
+        for (int m = 8; m > 0; m >>= 1) v = ff_add(v, ff_shfl_xor(v, m));
+        if (te == 0) sL[2 * tp + (s & 1) + 32 * (s >> 1)] = v;
+    }
+    __syncthreads();
+    const int np = (P - p0) < PB ? (P - p0) : PB;
+    const int NVu = with_grad ? NV : 1;
+    for (int idx = tid; idx < np * NVu; idx += PWA_THREADS) {
+        const int p = idx / NVu, v = idx % NVu;
+        float2 out;
+        if (v == 0) {
+            out = make_float2(sL[p].hi, sL[p].lo);
+        } else {
+            const float4 gv = sG[((v - 1) >> 1) * PB + p];
+            out = ((v - 1) & 1) ? make_float2(gv.z, gv.w) : make_float2(gv.x, gv.y);
+        }
+        part[((int64_t)blockIdx.x * P + p0 + p) * NV + v] = out;
+    }
+    for (int p = tid; p < np; p += PWA_THREADS)
+        if (sBad[p] || sBad[PB]) bad[p0 + p] = 1;
+}
+
 // Per parameter set: sum the chunk partials in chunk order, add the FP64 normalisation term.
 __global__ void __launch_bounds__(PWA_THREADS) k_nll_finalize(
     const float2* __restrict__ part, int nchunk, int K, int P, const float2* __restrict__ V,
@@ -700,17 +966,19 @@ cudaError_t stream_dispatch(const float2* A, int K, int64_t n, int64_t ld, const
 struct Shape {
     int E, PB;
 };
-const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}};
-constexpr int kNumShapes = 3;
+// shapes 0-2: k_nll_batched<KMAX, E, PB>; shape 3: the pipelined k_nll_batched2 (K <= 32)
+const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}, {128, 64}};
+constexpr int kNumShapes = 4;
 
 template <int KMAX, int E, int PB>
 bool shape_feasible() {
     return BatchedCfg<KMAX, E, PB>::SMEM <= 113 * 1024;
 }
 
-void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int* nchunk, int64_t* ev_per_chunk) {
+void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int* nchunk, int64_t* ev_per_chunk,
+                      int blocks_per_sm = 2) {
     const int ntp = (P + PB - 1) / PB;
-    int64_t target = ((int64_t)sm_count * 2) / ntp;
+    int64_t target = ((int64_t)sm_count * blocks_per_sm) / ntp;
     if (target < 1) target = 1;
     int64_t tiles = (n + E - 1) / E;
     if (tiles < 1) tiles = 1;
@@ -742,12 +1010,39 @@ cudaError_t batched_launch_shape(const float2* A, int K, int64_t n, int64_t ld, 
 }
 
 template <int KMAX>
+cudaError_t batched2_launch(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
+                            size_t ws_bytes, int* bad, int* status, int with_grad, int sm_count, cudaStream_t st,
+                            int* nchunk_out) {
+    if constexpr (KMAX <= 32 && KMAX % 8 == 0) {
+        using C = Batched2Cfg<KMAX>;
+        auto kern = k_nll_batched2<KMAX>;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            attr = true;
+        }
+        int nchunk;
+        int64_t epc;
+        batched_geometry(n, P, C::PB, C::E, sm_count, &nchunk, &epc, 1);
+        if ((size_t)nchunk * (size_t)P * (1 + 2 * (size_t)K) * sizeof(float2) > ws_bytes) return cudaErrorInvalidValue;
+        dim3 grid(nchunk, (P + C::PB - 1) / C::PB);
+        kern<<<grid, PWA_THREADS, C::SMEM, st>>>(A, K, n, ld, V, P, epc, (float2*)ws, bad, with_grad, status);
+        *nchunk_out = nchunk;
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int KMAX>
 cudaError_t batched_launch(int shape, const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
-                           size_t ws_bytes, int* bad, int with_grad, int sm_count, cudaStream_t st, int* nchunk) {
+                           size_t ws_bytes, int* bad, int* status, int with_grad, int sm_count, cudaStream_t st,
+                           int* nchunk) {
     switch (shape) {
         case 0: return batched_launch_shape<KMAX, 64, 64>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
         case 1: return batched_launch_shape<KMAX, 64, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        default: return batched_launch_shape<KMAX, 128, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 2: return batched_launch_shape<KMAX, 128, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        default: return batched2_launch<KMAX>(A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, nchunk);
     }
 }
 
@@ -756,7 +1051,8 @@ bool batched_shape_ok(int shape) {
     switch (shape) {
         case 0: return shape_feasible<KMAX, 64, 64>();
         case 1: return shape_feasible<KMAX, 64, 32>();
-        default: return shape_feasible<KMAX, 128, 32>();
+        case 2: return shape_feasible<KMAX, 128, 32>();
+        default: return KMAX <= 32 && KMAX % 8 == 0;
     }
 }
 
@@ -771,14 +1067,17 @@ bool shape_ok(int kmax, int shape) {
 }
 
 cudaError_t batched_dispatch(int shape, const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
-                             void* ws, size_t ws_bytes, int* bad, int with_grad, int sm_count, cudaStream_t st, int* nchunk) {
+                             void* ws, size_t ws_bytes, int* bad, int* status, int with_grad, int sm_count,
+                             cudaStream_t st, int* nchunk) {
+#define PWA_BD(KM) batched_launch<KM>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, nchunk)
     switch (kmax_batched(K)) {
-        case 8: return batched_launch<8>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        case 16: return batched_launch<16>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        case 32: return batched_launch<32>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        case 48: return batched_launch<48>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        default: return batched_launch<64>(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
+        case 8: return PWA_BD(8);
+        case 16: return PWA_BD(16);
+        case 32: return PWA_BD(32);
+        case 48: return PWA_BD(48);
+        default: return PWA_BD(64);
     }
+#undef PWA_BD
 }
 
 // ---- autotuner: per (KMAX, P bucket, n bucket) time every feasible shape once, keep the fastest
@@ -792,7 +1091,7 @@ int bucket_log2(int64_t x) {
 }
 
 int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const float2* V, void* ws, size_t ws_bytes, int* bad,
-                 int with_grad, int sm_count, cudaStream_t st) {
+                 int* status, int with_grad, int sm_count, cudaStream_t st) {
     const int kmax = kmax_batched(K);
     const char* env = getenv("PWA_BATCHED_SHAPE");
     if (env) {
@@ -822,7 +1121,8 @@ int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const flo
         bool ok = true;
         for (int rep = 0; rep < 3 && ok; ++rep) {
             cudaEventRecord(e0, st);
-            ok = batched_dispatch(s, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, &nc) == cudaSuccess;
+            ok = batched_dispatch(s, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, &nc) ==
+                 cudaSuccess;
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -899,9 +1199,10 @@ cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const floa
         return stream_dispatch<false>(A, K, n, ld, V, Psi, nfac, nll, nullptr, ws, ws_bytes, counter, badw, status, sm_count, st);
     }
     const int with_grad = grad != nullptr;
-    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, with_grad, sm_count, st);
+    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, status, with_grad, sm_count, st);
     int nchunk = 1;
-    cudaError_t e = batched_dispatch(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, &nchunk);
+    cudaError_t e = batched_dispatch(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st,
+                                     &nchunk);
     if (e != cudaSuccess) return e;
     k_nll_finalize<<<P, PWA_THREADS, 0, st>>>((const float2*)ws, nchunk, K, P, V, Psi, nfac, bad, status, nll, grad,
                                               with_grad);

@@ -149,30 +149,44 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     }
 }
 
-// Sum the block partials in block order and finalise Psi in FP64 (full Hermitian matrix).
+// Sum the block partials and finalise Psi in FP64 (full Hermitian matrix).  One warp per upper
+// entry (a <= b): lane l sums the partials of blocks l, l + 32, ... in order (all of its loads
+// in flight at once), then the lanes are combined by a fixed xor-shuffle tree, so the order of
+// every addition is fixed and the result deterministic.
 template <int KMAX>
 __global__ void __launch_bounds__(PWA_THREADS) k_normint_final(const float4* __restrict__ part, int nblocks,
                                                                int K, double inv_ngen, double2* __restrict__ Psi) {
-    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < K * K; o += gridDim.x * blockDim.x) {
+    constexpr int PER_LANE = 16;  // loads in flight per lane and batch
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < K * K; o += nwarps) {
         const int a = o / K, b = o % K;
-        if (a > b) continue;
-        // block partials in block order, 16 independent loads in flight
+        if (a > b) continue;  // warp-uniform
         ff re = ff_zero(), im = ff_zero();
-        for (int b0 = 0; b0 < nblocks; b0 += 16) {
-            float4 v[16];
+        for (int b0 = lane; b0 < nblocks; b0 += 32 * PER_LANE) {
+            float4 v[PER_LANE];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                v[j] = (b0 + j < nblocks) ? part[(int64_t)(b0 + j) * KMAX * KMAX + a * KMAX + b]
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < PER_LANE; ++j) {
+                const int blk = b0 + 32 * j;
+                v[j] = blk < nblocks ? __ldg(part + (int64_t)blk * KMAX * KMAX + a * KMAX + b)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < PER_LANE; ++j) {
                 re = ff_add(re, ff{v[j].x, v[j].y});
                 im = ff_add(im, ff{v[j].z, v[j].w});
             }
         }
-        const double r = ff_to_double(re) * inv_ngen, i = ff_to_double(im) * inv_ngen;
-        Psi[a * K + b] = make_double2(r, a == b ? 0.0 : i);
-        if (a != b) Psi[b * K + a] = make_double2(r, -i);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            re = ff_add(re, ff_shfl_xor(re, m));
+            im = ff_add(im, ff_shfl_xor(im, m));
+        }
+        if (lane == 0) {
+            const double r = ff_to_double(re) * inv_ngen, i = ff_to_double(im) * inv_ngen;
+            Psi[a * K + b] = make_double2(r, a == b ? 0.0 : i);
+            if (a != b) Psi[b * K + a] = make_double2(r, -i);
+        }
     }
 }
 
@@ -204,8 +218,8 @@ cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float
         ku<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, nullptr, ev_per_block, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_normint_final<KMAX><<<(K * K + PWA_THREADS - 1) / PWA_THREADS, PWA_THREADS, 0, st>>>(part, (int)nb, K,
-                                                                                       1.0 / n_gen, Psi);
+    const int fin_blocks = (K * K * 32 + PWA_THREADS - 1) / PWA_THREADS;  // one warp per entry
+    k_normint_final<KMAX><<<fin_blocks, PWA_THREADS, 0, st>>>(part, (int)nb, K, 1.0 / n_gen, Psi);
     return cudaGetLastError();
 }
 

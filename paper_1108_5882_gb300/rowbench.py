@@ -1,0 +1,238 @@
+"""Per-step measurement of the hot path: every kernel family at its workload size, timed with
+CUDA events on the launching stream after warm-up, with the L2 flushed (a 512 MiB read) before
+every timed launch, and compared with the roofline that bounds it.
+
+    python -m paper_1108_5882_gb300.rowbench [--reps R] [--rows a1,a3,...] [--json out.json]
+
+Peaks: HBM = the measured copy bandwidth of MEASURED_PEAKS.json; FP32 = the FFMA rate measured
+now by libpwa_peaks.so (the library's microbenchmark).  For a kernel bound by both, the roofline
+time is max(bytes / HBM, flop / FP32), and frac = roofline time / measured time.  Inputs are the
+seeded synthetic workloads of paper_1108_5882_gb300.inputs (flat phase space; Sec. 2 of the
+paper for the quantities).  Prints one line per measurement and, with --json, writes them all.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import build, inputs, learned, pwa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def hbm_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def ffma_peak(sm_count: int) -> float:
+    lib = ctypes.CDLL(build.PEAKS_LIB)
+    lib.pwa_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    best = 0.0
+    for _ in range(3):
+        ms, fl = ctypes.c_float(0), ctypes.c_double(0)
+        if lib.pwa_peak_fma(0, 4 * sm_count, 2048, 20, ctypes.byref(ms), ctypes.byref(fl), None) != 0:
+            raise RuntimeError("pwa_peak_fma failed")
+        best = max(best, fl.value / (ms.value * 1e-3) / 1e12)
+    return best
+
+
+class Timer:
+    def __init__(self):
+        self.flush = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        self.out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def __call__(self, fn, reps=20, warmup=3, flush=True):
+        st = torch.cuda.current_stream()
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda._sleep(int(2e9 * 0.02))
+        for i in range(reps):
+            if flush:
+                torch.sum(self.flush, dim=0, out=self.out)
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ev])) * 1e-3  # seconds
+
+
+def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None):
+    t_roof = max(nbytes / (hbm * 1e9), flops / (f32 * 1e12))
+    bound = "hbm" if nbytes / (hbm * 1e9) >= flops / (f32 * 1e12) else "fp32"
+    d = {"row": row, "what": what, "us": sec * 1e6, "GB/s": nbytes / sec / 1e9 if nbytes else None,
+         "TFLOP/s": flops / sec / 1e12 if flops else None, "bound": bound, "frac": t_roof / sec}
+    if extra:
+        d.update(extra)
+    gbs = f"{d['GB/s']:8.1f} GB/s" if d["GB/s"] else " " * 13
+    tfs = f"{d['TFLOP/s']:7.2f} TF/s" if d["TFLOP/s"] else " " * 12
+    print(f"{row:3s} {what:58s} {sec * 1e6:10.1f} us {gbs} {tfs}  {bound:4s} frac {d['frac']:.3f}", flush=True)
+    return d
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--rows", default="a1,a2,a3,a4,a5,a7,a8,a9")
+    ap.add_argument("--json", default=None)
+    args = ap.parse_args()
+    rows = set(args.rows.split(","))
+    build.build()
+    torch.cuda.set_device(0)
+    h = pwa.Handle(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    HBM, F32 = hbm_peak(), ffma_peak(sms)
+    print(f"peaks: HBM {HBM:.1f} GB/s (measured copy), FP32 {F32:.2f} TFLOP/s (FFMA microbenchmark, now)", flush=True)
+    T = Timer()
+    out = {"peaks": {"hbm_gbs": HBM, "fp32_tflops": F32}, "rows": []}
+    R = args.reps
+
+    def add(*a, **k):
+        out["rows"].append(line(*a, hbm=HBM, f32=F32, **k))
+
+    seed = inputs.SEED_BASE + 2
+    ws16 = inputs.wave_set_spread(16, seed)
+    w16 = pwa.waves_from(ws16)
+    if rows & {"a1", "a2", "a3", "a5"}:
+        n_mc = 5_000_000
+        kin_mc = torch.from_numpy(inputs.kinematics(n_mc, seed, 5)).cuda()
+        A_mc = torch.empty((16, n_mc), dtype=torch.complex64, device="cuda")
+    if "a1" in rows:
+        sec = T(lambda: h.pwa_amplitudes(w16, kin_mc, n_mc, A_mc), R)
+        add("a1", "amplitudes K=16, 5e6 events", sec, nbytes=n_mc * (12 + 8 * 16),
+            flops=n_mc * 16 * 30.0)
+        dM = torch.empty_like(A_mc)
+        dG = torch.empty_like(A_mc)
+        sec = T(lambda: h.pwa_amplitudes(w16, kin_mc, n_mc, A_mc, dM, dG), R)
+        add("a1", "amplitudes + dA/dM + dA/dG, K=16, 5e6 events", sec, nbytes=n_mc * (12 + 3 * 8 * 16),
+            flops=n_mc * 16 * 50.0)
+        del dM, dG
+    Psi16 = torch.empty((16, 16), dtype=torch.complex128, device="cuda")
+    if rows & {"a2", "a3", "a5"}:
+        h.pwa_amplitudes(w16, kin_mc, n_mc, A_mc)
+        h.pwa_normint(A_mc, n_mc, Psi16)
+    if "a2" in rows:
+        sec = T(lambda: h.pwa_normint(A_mc, n_mc, Psi16), R)
+        add("a2", "normint K=16, 5e6 MC events", sec, nbytes=n_mc * 8 * 16, flops=n_mc * 8.0 * 16 * 17 / 2)
+    if "a3" in rows:
+        for K, N in ((4, 1_000_000), (16, 1_000_000), (16, 4_000_000), (32, 1_000_000)):
+            wsK = inputs.wave_set_spread(K, seed)
+            kin = torch.from_numpy(inputs.kinematics(N, seed, 4)).cuda()
+            A = torch.empty((K, N), dtype=torch.complex64, device="cuda")
+            h.pwa_amplitudes(pwa.waves_from(wsK), kin, N, A)
+            V = torch.from_numpy(inputs.production_amplitudes(K, seed)[None, :]).cuda()
+            Psi = torch.eye(K, dtype=torch.complex128, device="cuda")
+            nll = torch.empty(1, dtype=torch.float64, device="cuda")
+            g = torch.empty((1, 2 * K), dtype=torch.float64, device="cuda")
+            sec = T(lambda: h.pwa_nll_grad(A, N, V, Psi, float(N), nll, g), R)
+            add("a3", f"-lnL+grad one set (stream, a5+a6 fused), K={K}, N={N:.0e}", sec, nbytes=N * K * 8,
+                flops=N * (16 * K + 12.0))
+            del A, kin
+    if "a5" in rows:
+        # floating shape: data 1e6 + MC 5e6 events, 4 floating parameters (2 masses, 2 widths)
+        K, N, F = 16, 1_000_000, 4
+        kin = torch.from_numpy(inputs.kinematics(N, seed, 4)).cuda()
+        A = torch.empty((K, N), dtype=torch.complex64, device="cuda")
+        h.pwa_amplitudes(w16, kin, N, A)
+        dA = torch.zeros((F, N), dtype=torch.complex64, device="cuda")
+        dAm = torch.zeros((F, n_mc), dtype=torch.complex64, device="cuda")
+        V = torch.from_numpy(inputs.production_amplitudes(K, seed)).cuda()
+        nll = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(2 * K + F, dtype=torch.float64, device="cuda")
+        fw = [3, 3, 9, 9]
+        sec = T(lambda: h.pwa_nll_grad_shape(A, dA, N, A_mc, dAm, n_mc, fw, V, float(N), nll, g), R)
+        add("a5", "streamed-normalisation -lnL + V and (M,G) gradient, K=16, 1e6+5e6", sec,
+            nbytes=(N + n_mc) * (K + F) * 8, flops=(N + n_mc) * (16 * K + 4 * F + 12.0))
+        del A, dA, dAm, kin
+    if rows & {"a1", "a2", "a3", "a5"}:
+        del A_mc, kin_mc
+    if rows & {"a4", "a7"}:
+        K, N, P = 32, 2_000_000, 256
+        ws32 = inputs.wave_set_spread(K, seed + 1)
+        kin = torch.from_numpy(inputs.kinematics(N, seed + 1, 4)).cuda()
+        A = torch.empty((K, N), dtype=torch.complex64, device="cuda")
+        h.pwa_amplitudes(pwa.waves_from(ws32), kin, N, A)
+        del kin
+        kin_mc = torch.from_numpy(inputs.kinematics(2_000_000, seed + 1, 5)).cuda()
+        A_mc = torch.empty((K, 2_000_000), dtype=torch.complex64, device="cuda")
+        h.pwa_amplitudes(pwa.waves_from(ws32), kin_mc, 2_000_000, A_mc)
+        Psi = torch.empty((K, K), dtype=torch.complex128, device="cuda")
+        h.pwa_normint(A_mc, 2_000_000, Psi)
+        del A_mc, kin_mc
+        V = torch.from_numpy(inputs.starts(P, K, seed + 1)).cuda()
+        nll = torch.empty(P, dtype=torch.float64, device="cuda")
+        g = torch.empty((P, 2 * K), dtype=torch.float64, device="cuda")
+        h.pwa_reserve(K, N, P)
+        if "a4" in rows:
+            sec = T(lambda: h.pwa_nll_grad(A, N, V, Psi, float(N), nll, g), max(5, R // 2))
+            add("a4", f"batched -lnL+grad, K={K}, N={N:.0e}, P={P} (autotuned shape)", sec, nbytes=N * K * 8,
+                flops=N * P * (16 * K + 12.0))
+        if "a7" in rows:
+            Vout = torch.empty((P, K), dtype=torch.complex128, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = h.pwa_fit_batch([dict(A=A, n=N, Psi=Psi, n_factor=N, V0=V, V_out=Vout)])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            iters = max(r["iterations"] for r in res)
+            evals = sum(r["evaluations"] for r in res) / P
+            conv = sum(r["status"] == 0 for r in res)
+            out["rows"].append({"row": "a7", "what": f"batched L-BFGS fit K={K}, N={N:.0e}, P={P}", "wall_s": wall,
+                                "iterations_max": iters, "evaluations_per_start": evals, "converged": conv})
+            print(f"a7  batched L-BFGS fit K={K}, N={N:.0e}, P={P}: {wall:.3f} s, {iters} iterations (max), "
+                  f"{evals:.1f} evaluations/start, {conv}/{P} converged", flush=True)
+        del A
+    if "a8" in rows:
+        sd = inputs.SEED_BASE + 5
+        wsl = inputs.wave_set_spread(16, sd)
+        wl = pwa.waves_from(wsl)
+        Psi_flat = learned.flat_psi(h, wl)
+        Tt, n_t = 1024, 200_000
+        V = learned.random_truths(Tt, 16, sd)
+        Vd = torch.from_numpy(V).cuda()
+        feats = torch.empty((Tt, 1000), dtype=torch.float64, device="cuda")
+        nacc = torch.empty(Tt, dtype=torch.int64, device="cuda")
+        sec = T(lambda: h.pwa_toy_moments(wl, Vd, Psi_flat, n_t, sd, 100_000, feats, nacc), 3, warmup=1, flush=False)
+        s_nll = torch.empty(Tt, dtype=torch.float64, device="cuda")
+        h.pwa_nll(torch.zeros((16, 2), dtype=torch.complex64, device="cuda"), 0, Vd, Psi_flat, 1.0, s_nll)
+        S = s_nll.cpu().numpy()
+        C = np.array([pwa.pwa_envelope(wl, V[t]) for t in range(Tt)])
+        n_cand = float(np.sum(np.ceil(n_t * C / S)))
+        acc = float(nacc.sum())
+        # flop estimate per candidate: K waves x ~24 (Breit-Wigner, angular factor, complex
+        # products) + ~40 angles; Philox integer work not counted
+        add("a8", f"toy generation + moments, {Tt} toys x {n_t:.0e} events, K=16", sec,
+            flops=n_cand * (16 * 24 + 40.0),
+            extra={"accepted_per_s": acc / sec, "candidates_per_s": n_cand / sec, "candidates_per_accepted": n_cand / acc})
+        print(f"      {acc / sec / 1e9:.3f} G accepted events/s, {n_cand / sec / 1e9:.2f} G candidates/s, "
+              f"{n_cand / acc:.1f} candidates per event", flush=True)
+    if "a9" in rows:
+        prop = learned.Proposer(h)
+        B = 256
+        X = torch.randn((B, 1000), device="cuda").to(torch.bfloat16)
+        tgt = torch.randn((B, 32), device="cuda")
+        sec = T(lambda: prop.train_step(X, tgt), R, flush=False)
+        macs = sum(prop.dims[i] * prop.dims[i + 1] for i in range(len(prop.dims) - 1))
+        flops = 2.0 * B * macs * 3  # forward, input gradient, weight gradient
+        add("a9", f"MLP training step (fwd+bwd+WTA+Adam), batch {B}", sec, flops=flops,
+            nbytes=4.0 * macs * 5)
+    if args.json:
+        with open(args.json, "w") as fh:
+            json.dump(out, fh, indent=1)
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,23 @@ def test_nll_grad_batched(h, K, P):
     check_nll(f, g, p.A, V, p.Psi)
 
 
+@pytest.mark.parametrize("K,P,n", [(4, 3, 3001), (8, 64, 40_001), (13, 100, 9_999), (16, 64, 20_000),
+                                   (32, 256, 200_001), (32, 7, 1)])
+def test_nll_grad_batched_pipelined_shape(h, K, P, n, monkeypatch):
+    # the pipelined batched kernel (shape 3: 128-event tiles staged by bulk copies, K <= 32)
+    # forced by the tuning override: ragged odd tails (NaN in the padding column), several
+    # chunks and tiles per block, more tiles than the G flush window, P not a multiple of 64
+    monkeypatch.setenv("PWA_BATCHED_SHAPE", "3")
+    p = make_problem(K, n, max(2 * n, 1000), SEED + 700 + K, accept_reject=False)
+    V = inputs.starts(P, K, SEED + P + 1)
+    V[0] = p.V_true
+    ld = n + 1 if n % 2 else n + 2
+    f, g = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), n, V, p.Psi)
+    check_nll(f, g, p.A, V, p.Psi)
+    f2, g2 = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi)
+    assert np.array_equal(f, f2) and np.array_equal(g, g2)
+
+
 def test_batched_equals_separate_sets(h):
     # per-set independence: P sets in one launch vs each set alone (within tolerance), and
     # permuting the sets permutes the outputs exactly

@@ -302,6 +302,35 @@ def test_condition_scales_bound_the_terms():
     assert np.all(cg[0] >= gc * (1 - 1e-12))
 
 
+def test_gradient_scale_covers_single_precision_cancellation():
+    # An event whose u = sum_a V_a A_a nearly cancels: a single-precision evaluation of the
+    # event's gradient term (Sec. 2 precision remark: amplitudes and per-event arithmetic in
+    # single precision) stays within 1e-4 of the scale built from s = sum_a |V_a||A_a|, while
+    # it exceeds 1e-4 of the cancellation-blind scale built from |u|.
+    K = 8
+    g = np.random.default_rng(84)
+    A = (g.normal(size=(K, 1)) + 1j * g.normal(size=(K, 1))).astype(np.complex64)
+    V = (g.normal(size=K) + 1j * g.normal(size=K)).astype(np.complex128)
+    # make u(event 0) tiny relative to its terms by adjusting the last production amplitude
+    V[-1] = -(V[:-1] @ A[:-1, 0].astype(np.complex128)) / complex(A[-1, 0]) * (1 + 3e-6)
+    V = V.astype(np.complex64)
+    Psi = np.eye(K, dtype=np.complex128)
+    _, g64, _, cg, _ = oracle.nll_grad(A, V[None, :], Psi, n_factor=0.0, with_cond=True)
+    u32 = np.complex64(0)
+    for a in range(K):
+        u32 = np.complex64(u32 + np.complex64(V[a] * A[a, 0]))
+    I32 = np.float32(u32.real * u32.real + u32.imag * u32.imag)
+    t32 = (-2.0 * np.conj(A[:, 0]) * u32 / I32).astype(np.complex64)
+    err = np.abs(np.stack([t32.real, t32.imag], axis=-1).reshape(-1) - g64[0])
+    u64 = V.astype(np.complex128) @ A[:, 0].astype(np.complex128)
+    old_scale = 2 * np.abs(A[:, 0]) * abs(u64) / abs(u64) ** 2
+    s = np.sum(np.abs(V) * np.abs(A[:, 0]).astype(np.float64))
+    assert s > 1e4 * abs(u64)  # the constructed cancellation
+    assert np.all(cg[0] >= old_scale * (1 - 1e-12))
+    assert np.all(err <= 1e-4 * np.repeat(cg[0], 2))
+    assert np.any(err > 1e-4 * np.repeat(old_scale, 2))
+
+
 # ---------------------------------------------------------------- the paper's one number --
 
 def test_table_storage_matches_paper():
