@@ -331,6 +331,15 @@ def run_ours(args, world, rank, local):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e, world)
     h2d = kin_h.numel() * 4 + kin_mc_h.numel() * 4 + V_h.numel() * 8
     d2h = nll_h.numel() * 8 + grad_h.numel() * 8
+    # the copy part of an e2e step alone (the same three host-to-device copies), for the breakdown
+    e0.record(stream)
+    for _ in range(n_e2e):
+        kin_d.copy_(kin_h, non_blocking=True)
+        kin_mc_d.copy_(kin_mc_h, non_blocking=True)
+        V_d.copy_(V_h, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = e0.elapsed_time(e1) / n_e2e
 
     if P == 1:
         peak, peak_kind = measured_peaks()
@@ -363,7 +372,7 @@ def run_ours(args, world, rank, local):
                    "K": K, "N_data": N, "N_MC": wl["NMC"], "P": P, "l2": "flushed before every step (512 MiB read)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * N * P / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "h2d_ms_per_step": h2d_ms,
                 "what": "pinned H2D of data+MC kinematics, amplitudes(data, MC), Psi, -lnL+grad, D2H of nll+grad"},
         "gpu_launches": launches,
         "roofline": roofline,

@@ -20,8 +20,8 @@ __device__ __forceinline__ void event_angles(float ct, float ph, EventAngles& t)
     t.P[0] = 1.f;
     t.P[1] = ct;
 #pragma unroll
-    for (int j = 1; j < AMP_JMAX; ++j)
-        t.P[j + 1] = ((2.f * j + 1.f) * ct * t.P[j] - (float)j * t.P[j - 1]) / (float)(j + 1);
+    for (int j = 1; j < AMP_JMAX; ++j)  // Bonnet: (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}
+        t.P[j + 1] = ((2.f * j + 1.f) * ct * t.P[j] - (float)j * t.P[j - 1]) * (1.f / (float)(j + 1));
     float s1, c1;
     sincosf(ph, &s1, &c1);
     t.zr[0] = 1.f;

@@ -112,6 +112,17 @@ pwa_status fill_waves(pwa_handle* h, const pwa_wave* waves, int K, pwa::WaveTabl
         wt->W[a] = (float)w.width;
         wt->MW[a] = (float)(w.mass * w.width);
     }
+    // group the waves by (J, lambda), keeping the given order inside a group
+    int n = 0;
+    wt->ng = 0;
+    for (int a = 0; a < K; ++a) {
+        bool seen = false;
+        for (int b = 0; b < a; ++b) seen = seen || (wt->J[b] == wt->J[a] && wt->lam[b] == wt->lam[a]);
+        if (seen) continue;
+        for (int b = a; b < K; ++b)
+            if (wt->J[b] == wt->J[a] && wt->lam[b] == wt->lam[a]) wt->gord[n++] = b;
+        wt->gend[wt->ng++] = n;
+    }
     return PWA_OK;
 }
 
@@ -540,7 +551,7 @@ pwa_status pwa_mlp_gemm(pwa_handle* h, int M, int N, int Kc, const void* A, int 
     if (sam < 0 || sak < 0 || sbn < 0 || sbk < 0) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: negative stride");
     DeviceGuard dg(h->device);
     cudaError_t e = pwa::launch_mlp_gemm(M, N, Kc, A, a_type, sam, sak, B, b_type, sbn, sbk, bias, relu, accumulate, C,
-                                         C_bf16, ldc, (cudaStream_t)stream);
+                                         C_bf16, ldc, h->sm_count, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mlp gemm");
     return PWA_OK;
 }

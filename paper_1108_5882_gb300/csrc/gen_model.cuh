@@ -42,19 +42,30 @@ __device__ __forceinline__ Candidate candidate(uint64_t seed, uint32_t stream, i
     return cd;
 }
 
+// I(Omega) = |sum_g Y_g(Omega) sum_{a in g} V_a BW_a(m)|^2: the waves of a group share the
+// angular factor Y_g = P_J(cos theta) exp(i lambda phi), selected once per group; the
+// Breit-Wigner denominator uses the fast reciprocal (relative error of a few ulp).
 __device__ __forceinline__ float intensity(const WaveTable& wt, const float2* sV, const Candidate& cd) {
     EventAngles t;
     event_angles(cd.ct, cd.ph, t);
     float ur = 0.f, ui = 0.f;
-    for (int a = 0; a < wt.K; ++a) {
-        float dr;
-        const float2 id = bw_inv_den(wt, a, cd.m, &dr);
-        const float2 amp = cmul(make_float2(wt.MW[a] * id.x, wt.MW[a] * id.y), wave_angle(wt, a, t));
-        const float2 p = cmul(sV[a], amp);
-        ur += p.x;
-        ui += p.y;
+    int s = 0;
+    for (int g = 0; g < wt.ng; ++g) {
+        const int end = wt.gend[g];
+        float wr = 0.f, wi = 0.f;
+        for (; s < end; ++s) {
+            const int a = wt.gord[s];
+            const float Mh = wt.Mhi[a], Ml = wt.Mlo[a], MW = wt.MW[a];
+            const float dr = ((Mh - cd.m) + Ml) * ((Mh + cd.m) + Ml);  // M^2 - m^2
+            const float inv = __fdividef(MW, dr * dr + MW * MW);        // MW / |D|^2
+            const float br = dr * inv, bi = MW * inv;                   // BW = MW / D
+            const float2 v = sV[a];
+            cmac(wr, wi, v.x, v.y, br, bi);
+        }
+        const float2 y = wave_angle(wt, wt.gord[end - 1], t);
+        cmac(ur, ui, y.x, y.y, wr, wi);
     }
-    return ur * ur + ui * ui;
+    return fmaf(ur, ur, ui * ui);
 }
 
 }  // namespace pwa

@@ -4,9 +4,9 @@
 //
 //  * k_gemm: C[m][n] = sum_k A(m, k) B(n, k) (+ bias[n]) (ReLU), with arbitrary element strides
 //    for A and B, so one kernel serves the forward product (X W^T), the data gradient (dY W)
-//    and the weight gradient (dY^T X).  64 x 64 output tiles, 16-deep k tiles staged through
-//    shared memory as FP32, 4 x 4 outputs per thread; sequential k order per output, so the
-//    result is deterministic.
+//    and the weight gradient (dY^T X).  64 x 64 (or 32 x 32) output tiles, 16-deep k tiles
+//    staged through shared memory as FP32 along the operand's contiguous dimension, 4 x 4
+//    outputs per thread; sequential k order per output, so the result is deterministic.
 //  * k_wta_loss: winner-takes-all over C candidate V vectors per sample (one warp per sample,
 //    one lane per candidate): d_c = |V_c|^2 + |T|^2 - 2 |sum_a conj(V_ca) T_a| is the distance
 //    after the optimal global phase (the likelihood does not see a global phase, Eq. 1);
@@ -24,42 +24,56 @@ namespace {
 __device__ __forceinline__ float ld_elem(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ld_elem(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
 
-constexpr int GM = 64, GN = 64, GK = 16;
+constexpr int GK = 16;
 
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int Kc, const TA* __restrict__ A, int64_t sam, int64_t sak,
-                                              const TB* __restrict__ B, int64_t sbn, int64_t sbk,
-                                              const float* __restrict__ bias, int relu, int accumulate,
-                                              float* __restrict__ C, __nv_bfloat16* __restrict__ Cb, int64_t ldc) {
-    __shared__ float sA[GK][GM + 4];
-    __shared__ float sB[GK][GN + 4];
+// Output tiles of TM x TN (TM = TN = 64 with 256 threads, or 32 with 64 threads for grids too
+// small to fill the GPU), 4 x 4 outputs per thread, 16-deep k tiles staged through shared
+// memory as FP32.  The staging loads run along whichever of (m, k) -- and (n, k) -- is
+// contiguous in memory, so every operand layout is read with coalesced loads.
+template <int TM, typename TA, typename TB>
+__global__ void __launch_bounds__(TM * TM / 16) k_gemm(int M, int N, int Kc, const TA* __restrict__ A, int64_t sam,
+                                                       int64_t sak, const TB* __restrict__ B, int64_t sbn, int64_t sbk,
+                                                       const float* __restrict__ bias, int relu, int accumulate,
+                                                       float* __restrict__ C, __nv_bfloat16* __restrict__ Cb,
+                                                       int64_t ldc) {
+    constexpr int NT = TM * TM / 16;     // threads
+    constexpr int TS = TM / 4;           // threads along m (and along n)
+    constexpr int LOADS = TM * GK / NT;  // staged elements per thread and operand
+    __shared__ float sA[GK][TM + 4];
+    __shared__ float sB[GK][TM + 4];
     const int tid = threadIdx.x;
-    const int tm = tid % 16, tn = tid / 16;  // outputs m = m0 + tm + 16 i, n = n0 + tn + 16 j
-    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
+    const int tm = tid % TS, tn = tid / TS;  // outputs m = m0 + tm + TS i, n = n0 + tn + TS j
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TM;
+    const bool a_mfast = sam == 1 && sak != 1;  // A contiguous along m
+    const bool b_nfast = sbn == 1 && sbk != 1;  // B contiguous along n
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < Kc; k0 += GK) {
-        // stage: 64 x 16 of A and of B, 4 elements per thread each
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = tid + 256 * r;
-            const int mm = idx / GK, kk = idx % GK;
-            const int gm = m0 + mm, gk = k0 + kk;
-            sA[kk][mm] = (gm < M && gk < Kc) ? ld_elem(A, (int64_t)gm * sam + (int64_t)gk * sak) : 0.f;
-            const int gn = n0 + mm;
-            sB[kk][mm] = (gn < N && gk < Kc) ? ld_elem(B, (int64_t)gn * sbn + (int64_t)gk * sbk) : 0.f;
+        for (int r = 0; r < LOADS; ++r) {
+            const int idx = tid + NT * r;
+            {
+                const int mm = a_mfast ? idx % TM : idx / GK, kk = a_mfast ? idx / TM : idx % GK;
+                const int gm = m0 + mm, gk = k0 + kk;
+                sA[kk][mm] = (gm < M && gk < Kc) ? ld_elem(A, (int64_t)gm * sam + (int64_t)gk * sak) : 0.f;
+            }
+            {
+                const int nn = b_nfast ? idx % TM : idx / GK, kk = b_nfast ? idx / TM : idx % GK;
+                const int gn = n0 + nn, gk = k0 + kk;
+                sB[kk][nn] = (gn < N && gk < Kc) ? ld_elem(B, (int64_t)gn * sbn + (int64_t)gk * sbk) : 0.f;
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
             float a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sA[kk][tm + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = sA[kk][tm + TS * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sB[kk][tn + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = sB[kk][tn + TS * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -69,11 +83,11 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int Kc, const TA* __
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + tm + 16 * i;
+        const int gm = m0 + tm + TS * i;
         if (gm >= M) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tn + 16 * j;
+            const int gn = n0 + tn + TS * j;
             if (gn >= N) continue;
             float v = acc[i][j];
             if (bias) v += bias[gn];
@@ -182,24 +196,36 @@ unsigned grid1d(int64_t n, int sm_count) {
 
 }  // namespace
 
-cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
-                            int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
-                            uint16_t* Cb, int64_t ldc, cudaStream_t st) {
-    dim3 grid((M + GM - 1) / GM, (N + GN - 1) / GN);
-    __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(Cb);
+template <int TM>
+cudaError_t mlp_gemm_tiles(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
+                           int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
+                           __nv_bfloat16* cb, int64_t ldc, cudaStream_t st) {
+    dim3 grid((M + TM - 1) / TM, (N + TM - 1) / TM);
+    constexpr int NT = TM * TM / 16;
     if (a_bf16 && b_bf16)
-        k_gemm<__nv_bfloat16, __nv_bfloat16><<<grid, 256, 0, st>>>(
+        k_gemm<TM, __nv_bfloat16, __nv_bfloat16><<<grid, NT, 0, st>>>(
             M, N, Kc, (const __nv_bfloat16*)A, sam, sak, (const __nv_bfloat16*)B, sbn, sbk, bias, relu, accumulate, C, cb, ldc);
     else if (a_bf16)
-        k_gemm<__nv_bfloat16, float><<<grid, 256, 0, st>>>(M, N, Kc, (const __nv_bfloat16*)A, sam, sak, (const float*)B,
-                                                          sbn, sbk, bias, relu, accumulate, C, cb, ldc);
+        k_gemm<TM, __nv_bfloat16, float><<<grid, NT, 0, st>>>(M, N, Kc, (const __nv_bfloat16*)A, sam, sak,
+                                                              (const float*)B, sbn, sbk, bias, relu, accumulate, C, cb, ldc);
     else if (b_bf16)
-        k_gemm<float, __nv_bfloat16><<<grid, 256, 0, st>>>(M, N, Kc, (const float*)A, sam, sak, (const __nv_bfloat16*)B,
-                                                          sbn, sbk, bias, relu, accumulate, C, cb, ldc);
+        k_gemm<TM, float, __nv_bfloat16><<<grid, NT, 0, st>>>(M, N, Kc, (const float*)A, sam, sak,
+                                                              (const __nv_bfloat16*)B, sbn, sbk, bias, relu, accumulate, C,
+                                                              cb, ldc);
     else
-        k_gemm<float, float><<<grid, 256, 0, st>>>(M, N, Kc, (const float*)A, sam, sak, (const float*)B, sbn, sbk, bias,
-                                                  relu, accumulate, C, cb, ldc);
+        k_gemm<TM, float, float><<<grid, NT, 0, st>>>(M, N, Kc, (const float*)A, sam, sak, (const float*)B, sbn, sbk,
+                                                      bias, relu, accumulate, C, cb, ldc);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
+                            int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
+                            uint16_t* Cb, int64_t ldc, int sm_count, cudaStream_t st) {
+    __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(Cb);
+    const int64_t tiles64 = (int64_t)((M + 63) / 64) * ((N + 63) / 64);
+    if (tiles64 < 2 * (int64_t)sm_count)  // too few 64 x 64 tiles to fill the GPU
+        return mlp_gemm_tiles<32>(M, N, Kc, A, a_bf16, sam, sak, B, b_bf16, sbn, sbk, bias, relu, accumulate, C, cb, ldc, st);
+    return mlp_gemm_tiles<64>(M, N, Kc, A, a_bf16, sam, sak, B, b_bf16, sbn, sbk, bias, relu, accumulate, C, cb, ldc, st);
 }
 
 cudaError_t launch_mlp_relu_bwd(const uint16_t* Y, float* dY, int64_t n, int sm_count, cudaStream_t st) {

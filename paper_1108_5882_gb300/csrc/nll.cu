@@ -81,13 +81,11 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
 #pragma unroll
             for (int c = 0; c < KMAX; ++c) {
                 const float2 v = sV[c];
-                u0r += v.x * a[c].x - v.y * a[c].y;
-                u0i += v.x * a[c].y + v.y * a[c].x;
-                u1r += v.x * a[c].z - v.y * a[c].w;
-                u1i += v.x * a[c].w + v.y * a[c].z;
+                cmac(u0r, u0i, v.x, v.y, a[c].x, a[c].y);
+                cmac(u1r, u1i, v.x, v.y, a[c].z, a[c].w);
             }
-            const float I0 = u0r * u0r + u0i * u0i;
-            const float I1 = u1r * u1r + u1i * u1i;
+            const float I0 = fmaf(u0r, u0r, u0i * u0i);  // one contraction, the same in every variant
+            const float I1 = fmaf(u1r, u1r, u1i * u1i);  // one contraction, the same in every variant
             float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f;
             if (intensity_ok(I0)) {
                 lacc = ff_add_f(lacc, __logf(I0));
@@ -115,8 +113,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
                         x = (c < K) ? __ldg(A4 + c * ld2 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                         if (!has1) x.z = x.w = 0.f;
                     }
-                    g[2 * c] += x.x * w0r + x.y * w0i + x.z * w1r + x.w * w1i;
-                    g[2 * c + 1] += x.x * w0i - x.y * w0r + x.z * w1i - x.w * w1r;
+                    cmac_conj(g[2 * c], g[2 * c + 1], x.x, x.y, w0r, w0i);
+                    cmac_conj(g[2 * c], g[2 * c + 1], x.z, x.w, w1r, w1i);
                 }
             }
         }
@@ -129,10 +127,9 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
                 const float2 x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
                 if (HOLD) a[c] = x;
                 const float2 v = sV[c];
-                ur += v.x * x.x - v.y * x.y;
-                ui += v.x * x.y + v.y * x.x;
+                cmac(ur, ui, v.x, v.y, x.x, x.y);
             }
-            const float I0 = ur * ur + ui * ui;
+            const float I0 = fmaf(ur, ur, ui * ui);  // one contraction, the same in every variant
             float wr = 0.f, wi = 0.f;
             if (intensity_ok(I0)) {
                 lacc = ff_add_f(lacc, __logf(I0));
@@ -148,8 +145,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_stream(
                     float2 x;
                     if (HOLD) x = a[c];
                     else x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
-                    g[2 * c] += x.x * wr + x.y * wi;
-                    g[2 * c + 1] += x.x * wi - x.y * wr;
+                    cmac_conj(g[2 * c], g[2 * c + 1], x.x, x.y, wr, wi);
                 }
             }
         }
@@ -234,10 +230,9 @@ __global__ void __launch_bounds__(TmaCfg<KMAX>::E) k_nll_tma(
             for (int c = 0; c < KMAX; ++c) {
                 a[c] = (c < K) ? col[c * E] : make_float2(0.f, 0.f);
                 const float2 v = sV[c];
-                ur += v.x * a[c].x - v.y * a[c].y;
-                ui += v.x * a[c].y + v.y * a[c].x;
+                cmac(ur, ui, v.x, v.y, a[c].x, a[c].y);
             }
-            const float I0 = ur * ur + ui * ui;
+            const float I0 = fmaf(ur, ur, ui * ui);  // one contraction, the same in every variant
             if (intensity_ok(I0)) {
                 lacc = ff_add_f(lacc, __logf(I0));
                 if (GRAD) {
@@ -245,8 +240,7 @@ __global__ void __launch_bounds__(TmaCfg<KMAX>::E) k_nll_tma(
                     const float wr = ur * r, wi = ui * r;
 #pragma unroll
                     for (int c = 0; c < KMAX; ++c) {
-                        g[2 * c] += a[c].x * wr + a[c].y * wi;
-                        g[2 * c + 1] += a[c].x * wi - a[c].y * wr;
+                        cmac_conj(g[2 * c], g[2 * c + 1], a[c].x, a[c].y, wr, wi);
                     }
                 }
             } else {
@@ -454,14 +448,10 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
 #pragma unroll
                 for (int s = 0; s < C::TP / 2; ++s) {
                     // events (2r: av.x,av.y) (2r+1: av.z,av.w); starts (2s: vv.x,vv.y) (2s+1: vv.z,vv.w)
-                    u[2 * r][2 * s][0] += av[r].x * vv[s].x - av[r].y * vv[s].y;
-                    u[2 * r][2 * s][1] += av[r].x * vv[s].y + av[r].y * vv[s].x;
-                    u[2 * r][2 * s + 1][0] += av[r].x * vv[s].z - av[r].y * vv[s].w;
-                    u[2 * r][2 * s + 1][1] += av[r].x * vv[s].w + av[r].y * vv[s].z;
-                    u[2 * r + 1][2 * s][0] += av[r].z * vv[s].x - av[r].w * vv[s].y;
-                    u[2 * r + 1][2 * s][1] += av[r].z * vv[s].y + av[r].w * vv[s].x;
-                    u[2 * r + 1][2 * s + 1][0] += av[r].z * vv[s].z - av[r].w * vv[s].w;
-                    u[2 * r + 1][2 * s + 1][1] += av[r].z * vv[s].w + av[r].w * vv[s].z;
+                    cmac(u[2 * r][2 * s][0], u[2 * r][2 * s][1], av[r].x, av[r].y, vv[s].x, vv[s].y);
+                    cmac(u[2 * r][2 * s + 1][0], u[2 * r][2 * s + 1][1], av[r].x, av[r].y, vv[s].z, vv[s].w);
+                    cmac(u[2 * r + 1][2 * s][0], u[2 * r + 1][2 * s][1], av[r].z, av[r].w, vv[s].x, vv[s].y);
+                    cmac(u[2 * r + 1][2 * s + 1][0], u[2 * r + 1][2 * s + 1][1], av[r].z, av[r].w, vv[s].z, vv[s].w);
                 }
         }
         // ---- epilogue: I = |U|^2, ln I, W = U / I  -> sW[p][e]
@@ -477,7 +467,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float ur = u[r + h][s][0], ui = u[r + h][s][1];
-                    const float I = ur * ur + ui * ui;
+                    const float I = fmaf(ur, ur, ui * ui);  // one contraction, the same in every variant
                     float wr = 0.f, wi = 0.f;
                     if (pv && e0 + e + h < e_end) {
                         if (intensity_ok(I)) {
@@ -510,8 +500,8 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
                 for (int k = 0; k < C::KA; ++k)
 #pragma unroll
                     for (int s = 0; s < C::PP; ++s) {
-                        gacc[k][s][0] += av[k].x * wv[s].x + av[k].y * wv[s].y + av[k].z * wv[s].z + av[k].w * wv[s].w;
-                        gacc[k][s][1] += av[k].x * wv[s].y - av[k].y * wv[s].x + av[k].z * wv[s].w - av[k].w * wv[s].z;
+                        cmac_conj(gacc[k][s][0], gacc[k][s][1], av[k].x, av[k].y, wv[s].x, wv[s].y);
+                        cmac_conj(gacc[k][s][0], gacc[k][s][1], av[k].z, av[k].w, wv[s].z, wv[s].w);
                     }
             }
             if (++since_flush == C::FLUSH) {
@@ -706,14 +696,10 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
                         // events (2r: av.x,av.y) (2r+1: av.z,av.w); starts (2s: vv.x,vv.y) (2s+1: vv.z,vv.w)
-                        u[2 * r][2 * s][0] += av[r].x * vv[s].x - av[r].y * vv[s].y;
-                        u[2 * r][2 * s][1] += av[r].x * vv[s].y + av[r].y * vv[s].x;
-                        u[2 * r][2 * s + 1][0] += av[r].x * vv[s].z - av[r].y * vv[s].w;
-                        u[2 * r][2 * s + 1][1] += av[r].x * vv[s].w + av[r].y * vv[s].z;
-                        u[2 * r + 1][2 * s][0] += av[r].z * vv[s].x - av[r].w * vv[s].y;
-                        u[2 * r + 1][2 * s][1] += av[r].z * vv[s].y + av[r].w * vv[s].x;
-                        u[2 * r + 1][2 * s + 1][0] += av[r].z * vv[s].z - av[r].w * vv[s].w;
-                        u[2 * r + 1][2 * s + 1][1] += av[r].z * vv[s].w + av[r].w * vv[s].z;
+                        cmac(u[2 * r][2 * s][0], u[2 * r][2 * s][1], av[r].x, av[r].y, vv[s].x, vv[s].y);
+                        cmac(u[2 * r][2 * s + 1][0], u[2 * r][2 * s + 1][1], av[r].x, av[r].y, vv[s].z, vv[s].w);
+                        cmac(u[2 * r + 1][2 * s][0], u[2 * r + 1][2 * s][1], av[r].z, av[r].w, vv[s].x, vv[s].y);
+                        cmac(u[2 * r + 1][2 * s + 1][0], u[2 * r + 1][2 * s + 1][1], av[r].z, av[r].w, vv[s].z, vv[s].w);
                     }
             }
         // ---- epilogue: I = |U|^2, ln I, W = U / I -> sW[p][e]
@@ -729,7 +715,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float ur = u[2 * r + h][s][0], ui = u[2 * r + h][s][1];
-                    const float I = ur * ur + ui * ui;
+                    const float I = fmaf(ur, ur, ui * ui);  // one contraction, the same in every variant
                     float wr = 0.f, wi = 0.f;
                     if (pv && e + h < nvalid) {
                         if (intensity_ok(I)) {
@@ -764,8 +750,8 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
                 for (int k = 0; k < GW; ++k)
 #pragma unroll
                     for (int s = 0; s < 8; ++s) {
-                        gacc[k][s][0] += av[k].x * wv[s].x + av[k].y * wv[s].y + av[k].z * wv[s].z + av[k].w * wv[s].w;
-                        gacc[k][s][1] += av[k].x * wv[s].y - av[k].y * wv[s].x + av[k].z * wv[s].w - av[k].w * wv[s].z;
+                        cmac_conj(gacc[k][s][0], gacc[k][s][1], av[k].x, av[k].y, wv[s].x, wv[s].y);
+                        cmac_conj(gacc[k][s][0], gacc[k][s][1], av[k].z, av[k].w, wv[s].z, wv[s].w);
                     }
             }
         }

@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        acc[(r * 4 + c) * 2 + 0] += xa[r].x * xb[c].x + xa[r].y * xb[c].y;
-                        acc[(r * 4 + c) * 2 + 1] += xa[r].y * xb[c].x - xa[r].x * xb[c].y;
+                        cmac_conj(acc[(r * 4 + c) * 2], acc[(r * 4 + c) * 2 + 1], xb[c].x, xb[c].y, xa[r].x, xa[r].y);
                     }
             }
         }

@@ -116,6 +116,23 @@ __device__ __forceinline__ ff ff_sum_strided(const float2* __restrict__ x, int64
     return s;
 }
 
+// Complex multiply-accumulate into an (re, im) float pair as chains of FMAs into the
+// accumulator: acc += a b (cmac) and acc += conj(a) b (cmac_conj).  Written this way each real
+// part costs two FMAs; the expression acc += x y - z w would round x y - z w first and cost
+// an extra multiply and add (no reassociation without fast-math).
+__device__ __forceinline__ void cmac(float& re, float& im, float ar, float ai, float br, float bi) {
+    re = fmaf(ar, br, re);
+    re = fmaf(-ai, bi, re);
+    im = fmaf(ar, bi, im);
+    im = fmaf(ai, br, im);
+}
+__device__ __forceinline__ void cmac_conj(float& re, float& im, float ar, float ai, float br, float bi) {
+    re = fmaf(ar, br, re);
+    re = fmaf(ai, bi, re);
+    im = fmaf(ar, bi, im);
+    im = fmaf(-ai, br, im);
+}
+
 // Non-finite or non-positive intensity test (the likelihood needs ln I_i).
 __device__ __forceinline__ bool intensity_ok(float I) { return I > 0.f && I < INFINITY; }
 
@@ -154,6 +171,10 @@ struct WaveTable {
     float Mhi[PWA_MAX_WAVES], Mlo[PWA_MAX_WAVES];
     float W[PWA_MAX_WAVES];
     float MW[PWA_MAX_WAVES];
+    // waves grouped by (J, lambda) (same angular factor): group g is gord[gend[g-1] .. gend[g]-1]
+    int ng;
+    int gend[PWA_MAX_WAVES];
+    int gord[PWA_MAX_WAVES];
 };
 
 cudaError_t launch_amplitudes(const WaveTable& wt, const float* kin, int64_t n, int64_t ld,
@@ -211,7 +232,7 @@ cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const doub
 
 cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
                             int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
-                            uint16_t* Cb, int64_t ldc, cudaStream_t st);
+                            uint16_t* Cb, int64_t ldc, int sm_count, cudaStream_t st);
 cudaError_t launch_mlp_relu_bwd(const uint16_t* Y, float* dY, int64_t n, int sm_count, cudaStream_t st);
 cudaError_t launch_mlp_bias_grad(const float* dY, int B, int N, float* db, cudaStream_t st);
 cudaError_t launch_mlp_wta(const float* out, const float* target, int B, int C, int K, float eps, float* loss,

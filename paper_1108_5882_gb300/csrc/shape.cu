@@ -81,10 +81,9 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_shape(ShapeArgs s, const fl
         for (int c = 0; c < KMAX; ++c) {
             const float2 x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
             if (HOLD) a[c] = x;
-            ur += sV[c].x * x.x - sV[c].y * x.y;
-            ui += sV[c].x * x.y + sV[c].y * x.x;
+            cmac(ur, ui, sV[c].x, sV[c].y, x.x, x.y);
         }
-        const float I0 = ur * ur + ui * ui;
+        const float I0 = fmaf(ur, ur, ui * ui);  // one contraction, the same in every variant
         float wr, wi;
         if (is_data) {
             if (!intensity_ok(I0)) {
@@ -106,8 +105,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_shape(ShapeArgs s, const fl
             float2 x;
             if (HOLD) x = a[c];
             else x = (c < K) ? __ldg(A + c * ld + i) : make_float2(0.f, 0.f);
-            g[2 * c] += x.x * wr + x.y * wi;
-            g[2 * c + 1] += x.x * wi - x.y * wr;
+            cmac_conj(g[2 * c], g[2 * c + 1], x.x, x.y, wr, wi);
         }
 #pragma unroll
         for (int q = 0; q < SH_FMAX; ++q) {
@@ -115,7 +113,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_shape(ShapeArgs s, const fl
                 const float2 d = __ldg(dA + q * ld + i);
                 // Re(conj(w) * V_r * dA)
                 const float2 vd = make_float2(sVr[q].x * d.x - sVr[q].y * d.y, sVr[q].x * d.y + sVr[q].y * d.x);
-                g[2 * KMAX + q] += wr * vd.x + wi * vd.y;
+                g[2 * KMAX + q] = fmaf(wr, vd.x, g[2 * KMAX + q]);
+                g[2 * KMAX + q] = fmaf(wi, vd.y, g[2 * KMAX + q]);
             }
         }
     }
@@ -203,6 +202,9 @@ __global__ void __launch_bounds__(PWA_THREADS) k_amp_floating(int J, int lam, co
     wt.Mlo[0] = (float)(M - (double)wt.Mhi[0]);
     wt.W[0] = (float)G;
     wt.MW[0] = (float)(M * G);
+    wt.ng = 1;
+    wt.gend[0] = 1;
+    wt.gord[0] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += stride) {
         if (i >= n) {

@@ -31,21 +31,44 @@ FEAT_SCALE = 100.0  # features (event averages of Y_LM per bin, ~1e-2) -> O(1) n
 
 
 class Proposer:
-    """MLP with FP32 master weights, BF16 working copies and Adam state on the device."""
+    """MLP with FP32 master weights, BF16 working copies and Adam state on the device.
+
+    All parameters live in one flat FP32 buffer (weights and biases of every layer are views
+    into it), and so do their gradients, the Adam moments and the BF16 copies, so one Adam
+    launch updates the whole network.  train_step replays the forward pass, the loss and the
+    backward pass as one captured CUDA graph (static input/target buffers of the batch size it
+    was captured for), then takes the Adam step."""
 
     def __init__(self, handle: pwa.Handle, K: int = 16, C: int = 32, hidden=(256, 256, 256), n_feat: int = 1000,
                  seed: int = inputs.SEED_BASE + 5):
         self.h, self.K, self.C = handle, K, C
         self.dims = [n_feat, *hidden, C * 2 * K]
         Ws, bs = inputs.mlp_weights(self.dims, seed)
-        self.W = [torch.from_numpy(w).cuda() for w in Ws]
-        self.b = [torch.from_numpy(b).cuda() for b in bs]
-        self.Wb = [w.to(torch.bfloat16) for w in self.W]
-        self.mW = [torch.zeros_like(w) for w in self.W]
-        self.vW = [torch.zeros_like(w) for w in self.W]
-        self.mb = [torch.zeros_like(b) for b in self.b]
-        self.vb = [torch.zeros_like(b) for b in self.b]
+        sizes = []
+        for w, b in zip(Ws, bs):
+            sizes += [w.size, b.size]
+        n = int(sum(sizes))
+        self.P = torch.zeros(n, dtype=torch.float32, device="cuda")
+        self.G = torch.zeros(n, dtype=torch.float32, device="cuda")
+        self.M1 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        self.M2 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        self.Pb = torch.zeros(n, dtype=torch.bfloat16, device="cuda")
+        self.W, self.b, self.Wb, self.gW, self.gb = [], [], [], [], []
+        off = 0
+        for w, b in zip(Ws, bs):
+            shp = w.shape
+            self.W.append(self.P[off:off + w.size].view(shp))
+            self.Wb.append(self.Pb[off:off + w.size].view(shp))
+            self.gW.append(self.G[off:off + w.size].view(shp))
+            self.W[-1].copy_(torch.from_numpy(w))
+            off += w.size
+            self.b.append(self.P[off:off + b.size])
+            self.gb.append(self.G[off:off + b.size])
+            self.b[-1].copy_(torch.from_numpy(b))
+            off += b.size
+        self.Pb.copy_(self.P.to(torch.bfloat16))
         self.step = 0
+        self._graph = None
 
     # ---------------------------------------------------------------- forward / backward
     def forward(self, X):
@@ -68,39 +91,60 @@ class Proposer:
         return acts, out
 
     def backward(self, acts, dout):
-        """Weight and bias gradients from d loss / d output (fp32 [B][C*2K])."""
+        """Weight and bias gradients (into the flat gradient buffer) from d loss / d output."""
         B = dout.shape[0]
         L = len(self.W)
-        gW = [None] * L
-        gb = [None] * L
         dY = dout
         for i in reversed(range(L)):
             n_in, n_out = self.dims[i], self.dims[i + 1]
             if i < L - 1:
                 self.h.pwa_mlp_relu_backward(acts[i + 1], dY)
-            gW[i] = torch.empty((n_out, n_in), dtype=torch.float32, device="cuda")
-            gb[i] = torch.empty(n_out, dtype=torch.float32, device="cuda")
             # dW[o][k] = sum_b dY[b][o] X[b][k]
-            self.h.pwa_mlp_gemm(n_out, n_in, B, dY, (1, n_out), acts[i], (1, n_in), C=gW[i])
-            self.h.pwa_mlp_bias_grad(dY, gb[i])
+            self.h.pwa_mlp_gemm(n_out, n_in, B, dY, (1, n_out), acts[i], (1, n_in), C=self.gW[i])
+            self.h.pwa_mlp_bias_grad(dY, self.gb[i])
             if i > 0:
                 dX = torch.empty((B, n_in), dtype=torch.float32, device="cuda")
                 # dX[b][k] = sum_o dY[b][o] W[o][k]
                 self.h.pwa_mlp_gemm(B, n_in, n_out, dY, (n_out, 1), self.Wb[i], (1, n_in), C=dX)
                 dY = dX
-        return gW, gb
+        return self.gW, self.gb
 
-    def train_step(self, X, target, lr=1e-3, eps=0.05):
+    def _loss_and_grads(self, X, target, eps):
         acts, out = self.forward(X)
         B = X.shape[0]
         loss = torch.empty(B, dtype=torch.float32, device="cuda")
         dout = torch.empty_like(out)
         self.h.pwa_mlp_wta_loss(out, target, self.C, self.K, eps, loss, dout)
-        gW, gb = self.backward(acts, dout)
+        self.backward(acts, dout)
+        return loss
+
+    def train_step(self, X, target, lr=1e-3, eps=0.05, graph=True):
+        """One Adam step on the batch (X bf16 [B][n_feat], target fp32 [B][2K]); returns the
+        per-sample loss (a view of a static buffer when graph=True)."""
+        if graph:
+            B = X.shape[0]
+            if self._graph is None or self._graph_key != (B, eps):
+                self._sX = torch.empty_like(X)
+                self._sT = torch.empty_like(target)
+                self._sX.copy_(X)
+                self._sT.copy_(target)
+                side = torch.cuda.Stream()
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(side):  # warm-up outside the capture
+                    self._loss_and_grads(self._sX, self._sT, eps)
+                torch.cuda.current_stream().wait_stream(side)
+                self._graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self._graph):
+                    self._sLoss = self._loss_and_grads(self._sX, self._sT, eps)
+                self._graph_key = (B, eps)
+            self._sX.copy_(X)
+            self._sT.copy_(target)
+            self._graph.replay()
+            loss = self._sLoss
+        else:
+            loss = self._loss_and_grads(X, target, eps)
         self.step += 1
-        for i in range(len(self.W)):
-            self.h.pwa_mlp_adam(self.W[i], gW[i], self.mW[i], self.vW[i], self.Wb[i], lr, self.step)
-            self.h.pwa_mlp_adam(self.b[i], gb[i], self.mb[i], self.vb[i], None, lr, self.step)
+        self.h.pwa_mlp_adam(self.P, self.G, self.M1, self.M2, self.Pb, lr, self.step)
         return loss
 
     def propose(self, feat):
@@ -166,14 +210,14 @@ def train(prop, feats, targets, epochs=20, batch=256, lr=1e-3, seed=0, log=None)
     history = []
     for ep in range(epochs):
         perm = torch.from_numpy(g.permutation(T)).cuda()
-        tot = 0.0
+        tot = torch.zeros((), dtype=torch.float64, device="cuda")
         nb = 0
         for b0 in range(0, T - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             loss = prop.train_step(X[idx].contiguous(), targets[idx].contiguous(), lr=lr)
-            tot += float(loss.mean())
+            tot += loss.sum(dtype=torch.float64)  # stays on the device: no sync per step
             nb += 1
-        history.append(tot / max(nb, 1))
+        history.append(float(tot) / max(nb * batch, 1))
         if log:
             log(f"epoch {ep}: loss {history[-1]:.4f}")
     return history
