@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
     float2* sV = reinterpret_cast<float2*>(smem);  // [KMAX][PB]
     float2* sA = sV + KMAX * PB;                    // [KMAX][EA]
     float2* sW = sA + KMAX * C::EA;                 // [PB][EW]
-    float4* sG = reinterpret_cast<float4*>(sW + PB * C::EW);  // [KMAX][PB] complex double-single
+    float4* sG = reinterpret_cast<float4*>(sW + PB * C::EW);  // [PB][KMAX] complex double-single
     ff* sL = reinterpret_cast<ff*>(sG + KMAX * PB);            // [PB]
     int* sBad = reinterpret_cast<int*>(sL + PB);               // [PB]
 
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
         for (int k = 0; k < C::KA; ++k)
 #pragma unroll
             for (int s = 0; s < C::PP; ++s) {
-                float4* dst = sG + (ta + C::TA * k) * PB + (tg + C::TPG * s);
+                float4* dst = sG + (tg + C::TPG * s) * KMAX + (ta + C::TA * k);
                 float4 cur = *dst;
                 ff re = ff_add_f(ff{cur.x, cur.y}, gacc[k][s][0]);
                 ff im = ff_add_f(ff{cur.z, cur.w}, gacc[k][s][1]);
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
                     if (pv && e0 + e + h < e_end) {
                         if (intensity_ok(I)) {
                             lpart += __logf(I);
-                            const float rc = __frcp_rn(I);
+                            const float rc = __fdividef(1.f, I);
                             wr = ur * rc;
                             wi = ui * rc;
                         } else {
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 2) k_nll_batched(
         if (v == 0) {
             out = make_float2(sL[p].hi, sL[p].lo);
         } else {
-            const float4 gv = sG[((v - 1) >> 1) * PB + p];
+            const float4 gv = sG[p * KMAX + ((v - 1) >> 1)];
             out = ((v - 1) & 1) ? make_float2(gv.z, gv.w) : make_float2(gv.x, gv.y);
         }
         part[((int64_t)chunk * P + p0 + p) * NV + v] = out;
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
     float2* sA = reinterpret_cast<float2*>(bsm + C::OFF_A);  // [S][KMAX][EA]
     float2* sV = reinterpret_cast<float2*>(bsm + C::OFF_V);  // [KMAX][PB]
     float2* sW = reinterpret_cast<float2*>(bsm + C::OFF_W);  // [PB][EA]
-    float4* sG = reinterpret_cast<float4*>(bsm + C::OFF_G);  // [KMAX][PB] complex double-single
+    float4* sG = reinterpret_cast<float4*>(bsm + C::OFF_G);  // [PB][KMAX] complex double-single
     ff* sL = reinterpret_cast<ff*>(bsm + C::OFF_L);          // [PB]
     int* sBad = reinterpret_cast<int*>(bsm + C::OFF_B);      // [PB], then the timeout word
 
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
                 for (int k = 0; k < GW; ++k)
 #pragma unroll
                     for (int s = 0; s < 8; ++s) {
-                        float4* dst = sG + (ta + 8 * k) * PB + (tg + 8 * s);
+                        float4* dst = sG + (tg + 8 * s) * KMAX + (ta + 8 * k);
                         const float4 cur = *dst;
                         const ff re = ff_add_f(ff{cur.x, cur.y}, gacc[k][s][0]);
                         const ff im = ff_add_f(ff{cur.z, cur.w}, gacc[k][s][1]);
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
                     if (pv && e + h < nvalid) {
                         if (intensity_ok(I)) {
                             lpart += __logf(I);
-                            const float rc = __frcp_rn(I);
+                            const float rc = __fdividef(1.f, I);
                             wr = ur * rc;
                             wi = ui * rc;
                         } else {
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 1) k_nll_batched2(
         if (v == 0) {
             out = make_float2(sL[p].hi, sL[p].lo);
         } else {
-            const float4 gv = sG[((v - 1) >> 1) * PB + p];
+            const float4 gv = sG[p * KMAX + ((v - 1) >> 1)];
             out = ((v - 1) & 1) ? make_float2(gv.z, gv.w) : make_float2(gv.x, gv.y);
         }
         part[((int64_t)blockIdx.x * P + p0 + p) * NV + v] = out;
