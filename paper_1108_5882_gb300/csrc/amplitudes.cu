@@ -23,18 +23,23 @@ namespace {
 
 constexpr int AMP_EV = 4;  // events per thread (consecutive: two 16-byte stores per wave)
 
-// Legendre P_J(x) by Bonnet's recurrence; J is the same for the whole launch (uniform loop).
-__device__ __forceinline__ float legendre_rec(int J, float x) {
-    if (J == 0) return 1.f;
-    float pm = 1.f, p = x;
-    for (int j = 1; j < J; ++j) {
-        const float pn = ((2.f * j + 1.f) * x * p - (float)j * pm) * __frcp_rn((float)(j + 1));
-        pm = p;
-        p = pn;
+__constant__ float c_inv_int[AMP_JMAX + 1] = {1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9};
+
+__device__ __forceinline__ void store4(float2* row, int64_t i0, int64_t ld, bool full, const float2 (&v)[AMP_EV]) {
+    if (full) {
+        reinterpret_cast<float4*>(row)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4*>(row)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else {
+#pragma unroll
+        for (int k = 0; k < AMP_EV; ++k)
+            if (i0 + k < ld) row[k] = v[k];
     }
-    return p;
 }
 
+// Waves are visited group by group (groups of equal (J, lambda) in ascending J, see WaveTable):
+// the Legendre recurrence (Bonnet, (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}) advances from one
+// group's J to the next, exp(i lambda phi) is formed once per group, and each wave of the group
+// only adds its Breit-Wigner factor.
 template <bool DERIV>
 __global__ void __launch_bounds__(PWA_THREADS) k_amplitudes(WaveTable wt, const float* __restrict__ kin,
                                                             int64_t n, int64_t ld, float2* __restrict__ A,
@@ -52,56 +57,65 @@ __global__ void __launch_bounds__(PWA_THREADS) k_amplitudes(WaveTable wt, const 
             sincosf(ph, &s1[k], &c1[k]);
         }
         const bool full = i0 + AMP_EV <= ld;  // ld is even: pairs never straddle it
-        for (int a = 0; a < wt.K; ++a) {
-            const int J = wt.J[a], lam = wt.lam[a];
+        float pcur[AMP_EV], pprev[AMP_EV];     // P_jc, P_{jc-1}
+#pragma unroll
+        for (int k = 0; k < AMP_EV; ++k) {
+            pcur[k] = 1.f;
+            pprev[k] = 0.f;
+        }
+        int jc = 0, s = 0;
+        for (int g = 0; g < wt.ng; ++g) {
+            const int end = wt.gend[g];
+            const int a0 = wt.gord[s];
+            const int J = wt.J[a0], lam = wt.lam[a0];
             const int al = lam < 0 ? -lam : lam;
-            const float Mh = wt.Mhi[a], Ml = wt.Mlo[a], MW = wt.MW[a], G = wt.W[a];
-            float2 out[AMP_EV], oM[AMP_EV], oW[AMP_EV];
+            for (; jc < J; ++jc) {
+                const float c2 = 2.f * jc + 1.f, cj = (float)jc, rj = c_inv_int[jc];
+#pragma unroll
+                for (int k = 0; k < AMP_EV; ++k) {
+                    const float pn = (c2 * ct[k] * pcur[k] - cj * pprev[k]) * rj;
+                    pprev[k] = pcur[k];
+                    pcur[k] = pn;
+                }
+            }
+            float2 ang[AMP_EV];  // P_J(cos theta) exp(i lambda phi)
 #pragma unroll
             for (int k = 0; k < AMP_EV; ++k) {
-                // angular factor P_J(cos theta) exp(i lambda phi)
                 float er = 1.f, ei = 0.f;
                 for (int j = 0; j < al; ++j) {
-                    const float t = er * c1[k] - ei * s1[k];
+                    const float tr = er * c1[k] - ei * s1[k];
                     ei = er * s1[k] + ei * c1[k];
-                    er = t;
+                    er = tr;
                 }
                 if (lam < 0) ei = -ei;
-                const float pj = legendre_rec(J, ct[k]);
-                const float2 ang = make_float2(pj * er, pj * ei);
-                // 1/D, D = M^2 - m^2 - i M G, with M - m from the two-float mass
-                const float dr = ((Mh - m[k]) + Ml) * ((Mh + m[k]) + Ml);
-                const float inv = __frcp_rn(dr * dr + MW * MW);
-                const float2 id = make_float2(dr * inv, MW * inv);
-                const bool in = i0 + k < n;
-                const float2 bw = make_float2(MW * id.x, MW * id.y);
-                out[k] = in ? cmul(bw, ang) : make_float2(0.f, 0.f);
-                if (DERIV) {
-                    const float2 id2 = cmul(id, id);                         // 1/D^2
-                    const float cm = -G * (Mh * Mh + m[k] * m[k]);           // -G (M^2 + m^2)
-                    const float cw = (Mh + Ml) * dr;                         // M (M^2 - m^2)
-                    oM[k] = in ? cmul(make_float2(cm * id2.x, cm * id2.y), ang) : make_float2(0.f, 0.f);
-                    oW[k] = in ? cmul(make_float2(cw * id2.x, cw * id2.y), ang) : make_float2(0.f, 0.f);
-                }
+                ang[k] = make_float2(pcur[k] * er, pcur[k] * ei);
             }
-            float2* row = A + a * ld + i0;
-            if (full) {
-                reinterpret_cast<float4*>(row)[0] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
-                reinterpret_cast<float4*>(row)[1] = make_float4(out[2].x, out[2].y, out[3].x, out[3].y);
-            } else {
+            for (; s < end; ++s) {
+                const int a = wt.gord[s];
+                const float Mh = wt.Mhi[a], Ml = wt.Mlo[a], MW = wt.MW[a], G = wt.W[a];
+                float2 out[AMP_EV], oM[AMP_EV], oW[AMP_EV];
 #pragma unroll
-                for (int k = 0; k < AMP_EV; ++k)
-                    if (i0 + k < ld) row[k] = out[k];
-            }
-            if (DERIV) {
-                float2* rm = dAdM + a * ld + i0;
-                float2* rw = dAdW + a * ld + i0;
-#pragma unroll
-                for (int k = 0; k < AMP_EV; ++k)
-                    if (i0 + k < ld) {
-                        rm[k] = oM[k];
-                        rw[k] = oW[k];
+                for (int k = 0; k < AMP_EV; ++k) {
+                    // 1/D, D = M^2 - m^2 - i M G, with M - m from the two-float mass
+                    const float dr = ((Mh - m[k]) + Ml) * ((Mh + m[k]) + Ml);
+                    const float inv = __fdividef(1.f, fmaf(dr, dr, MW * MW));
+                    const float2 id = make_float2(dr * inv, MW * inv);
+                    const bool in = i0 + k < n;
+                    const float2 bw = make_float2(MW * id.x, MW * id.y);
+                    out[k] = in ? cmul(bw, ang[k]) : make_float2(0.f, 0.f);
+                    if (DERIV) {
+                        const float2 id2 = cmul(id, id);                // 1/D^2
+                        const float cm = -G * (Mh * Mh + m[k] * m[k]);  // -G (M^2 + m^2)
+                        const float cw = (Mh + Ml) * dr;                // M (M^2 - m^2)
+                        oM[k] = in ? cmul(make_float2(cm * id2.x, cm * id2.y), ang[k]) : make_float2(0.f, 0.f);
+                        oW[k] = in ? cmul(make_float2(cw * id2.x, cw * id2.y), ang[k]) : make_float2(0.f, 0.f);
                     }
+                }
+                store4(A + a * ld + i0, i0, ld, full, out);
+                if (DERIV) {
+                    store4(dAdM + a * ld + i0, i0, ld, full, oM);
+                    store4(dAdW + a * ld + i0, i0, ld, full, oW);
+                }
             }
         }
     }

@@ -112,17 +112,17 @@ pwa_status fill_waves(pwa_handle* h, const pwa_wave* waves, int K, pwa::WaveTabl
         wt->W[a] = (float)w.width;
         wt->MW[a] = (float)(w.mass * w.width);
     }
-    // group the waves by (J, lambda), keeping the given order inside a group
+    // group the waves by (J, lambda): groups in ascending (J, lambda), waves of a group in the
+    // given order (the amplitude kernel advances its Legendre recurrence from group to group)
     int n = 0;
     wt->ng = 0;
-    for (int a = 0; a < K; ++a) {
-        bool seen = false;
-        for (int b = 0; b < a; ++b) seen = seen || (wt->J[b] == wt->J[a] && wt->lam[b] == wt->lam[a]);
-        if (seen) continue;
-        for (int b = a; b < K; ++b)
-            if (wt->J[b] == wt->J[a] && wt->lam[b] == wt->lam[a]) wt->gord[n++] = b;
-        wt->gend[wt->ng++] = n;
-    }
+    for (int J = 0; J <= 8; ++J)
+        for (int lam = -8; lam <= 8; ++lam) {
+            const int n0 = n;
+            for (int a = 0; a < K; ++a)
+                if (wt->J[a] == J && wt->lam[a] == lam) wt->gord[n++] = a;
+            if (n > n0) wt->gend[wt->ng++] = n;
+        }
     return PWA_OK;
 }
 
