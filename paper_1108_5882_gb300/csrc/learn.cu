@@ -94,13 +94,15 @@ __device__ __forceinline__ void warp_add_events(long long* wacc, unsigned mask, 
         const int e = __ffs(mask) - 1;
         mask &= mask - 1;
         const int be = __shfl_sync(0xffffffffu, b, e);
-        long long mine = 0;
+        float mine = 0.f;
 #pragma unroll
         for (int k = 0; k < LM; ++k) {
             const float v = __shfl_sync(0xffffffffu, y[k], e);
-            if (lane == k) mine = __float2ll_rn(v * FIX_SCALE);
+            if (lane == k) mine = v;
         }
-        if (lane < LM) wacc[be * LM + lane] += mine;
+        // one float -> int64 conversion per lane (GB300 runs 64-bit conversions on its narrow
+        // FP64 pipe, so converting inside the loop above would cost 25 of them per event)
+        if (lane < LM) wacc[be * LM + lane] += __float2ll_rn(mine * FIX_SCALE);
     }
 }
 

@@ -8,8 +8,8 @@
 // so the work is a reduction over events, not a GEMM with reuse in the output: the kernel
 // streams event tiles of E = 256 events through shared memory (the next tile is prefetched
 // into registers while the current one is consumed) and gives each thread a 4 x 4 block of
-// the upper triangle of Psi and an event phase.  Per event a thread issues 8 shared loads for
-// 16 complex multiply-adds (64 FFMA).
+// the upper triangle of Psi and an event phase.  The tile is stored event-major, so per event
+// a thread issues 4 shared 16-byte loads for 16 complex multiply-adds (64 FFMA).
 //
 // Accumulation: FP32 per thread over a window of about 64 events, then folded into a
 // per-thread double-single accumulator held in shared memory (v-major, conflict-free); the
@@ -22,7 +22,10 @@ namespace pwa {
 namespace {
 
 constexpr int NI_E = 256;  // events per tile
-constexpr int NI_ES = NI_E + 1;  // padded row stride (float2)
+// the tile is held event-major, sA[e][a] with a row stride of KMAX + 2 float2 (even, so that a
+// thread's four consecutive waves of one event are two 16-byte loads)
+template <int KMAX>
+__host__ __device__ constexpr int ni_rs() { return KMAX + 2; }
 
 // block partial layout: part[block][KMAX*KMAX] of complex ff = 4 floats (re.hi, re.lo, im.hi, im.lo)
 template <int KMAX, bool WEIGHTED>
@@ -35,9 +38,10 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     constexpr int EPT = (NI_E + NPH - 1) / NPH;  // events per thread and tile
     constexpr int FLUSH = (64 + EPT - 1) / EPT;  // tiles per FP32 accumulation window (~64 events)
     constexpr int LD2 = KMAX * NI_E / PWA_THREADS;  // float2 tile loads per thread
+    constexpr int RS = ni_rs<KMAX>();
     extern __shared__ float4 smem4[];
-    float2* sA = reinterpret_cast<float2*>(smem4);              // [KMAX][NI_ES]
-    float* sw = reinterpret_cast<float*>(sA + KMAX * NI_ES);    // [NI_E]
+    float2* sA = reinterpret_cast<float2*>(smem4);              // [NI_E][RS], event-major
+    float* sw = reinterpret_cast<float*>(sA + NI_E * RS);       // [NI_E]
     float* sacc = sw + NI_E;  // [64][PWA_THREADS]: 16 complex ff per thread, v-major
 
     const int tid = threadIdx.x;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
 #pragma unroll
         for (int j = 0; j < LD2; ++j) {
             const int idx = tid + PWA_THREADS * j;
-            sA[(idx / NI_E) * NI_ES + idx % NI_E] = pre[j];
+            sA[(idx % NI_E) * RS + idx / NI_E] = pre[j];
         }
         if (WEIGHTED) sw[tid] = prew;
         __syncthreads();
@@ -91,10 +95,18 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
 #pragma unroll 2
             for (int e = ph; e < NI_E; e += NPH) {
                 float2 xa[4], xb[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    xa[r] = sA[(4 * ti + r) * NI_ES + e];
-                    xb[r] = sA[(4 * tj + r) * NI_ES + e];
+                {
+                    const float4* ra = reinterpret_cast<const float4*>(sA + e * RS + 4 * ti);
+                    const float4* rb = reinterpret_cast<const float4*>(sA + e * RS + 4 * tj);
+                    const float4 a01 = ra[0], a23 = ra[1], b01 = rb[0], b23 = rb[1];
+                    xa[0] = make_float2(a01.x, a01.y);
+                    xa[1] = make_float2(a01.z, a01.w);
+                    xa[2] = make_float2(a23.x, a23.y);
+                    xa[3] = make_float2(a23.z, a23.w);
+                    xb[0] = make_float2(b01.x, b01.y);
+                    xb[1] = make_float2(b01.z, b01.w);
+                    xb[2] = make_float2(b23.x, b23.y);
+                    xb[3] = make_float2(b23.z, b23.w);
                 }
                 if (WEIGHTED) {
                     const float we = sw[e];
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint_final(const float4* __r
 
 template <int KMAX>
 size_t ni_smem() {
-    return sizeof(float2) * KMAX * NI_ES + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
+    return sizeof(float2) * NI_E * ni_rs<KMAX>() + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
 }
 
 template <int KMAX>
