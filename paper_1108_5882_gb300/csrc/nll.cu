@@ -952,28 +952,16 @@ cudaError_t stream_dispatch(const float2* A, int K, int64_t n, int64_t ld, const
 struct Shape {
     int E, PB;
 };
-// shapes 0-2: k_nll_batched<KMAX, E, PB>; shape 3: the pipelined k_nll_batched2 (K <= 32)
-const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}, {128, 64}};
-constexpr int kNumShapes = 4;
+// shapes 0-2: k_nll_batched<KMAX, E, PB>; shape 3: the pipelined k_nll_batched2 (K <= 32);
+// shape 4: the tensor-core kernel k_nll_tc (3xTF32, K <= 32)
+const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}, {128, 64}, {64, 128}};
+constexpr int kNumShapes = 5;
 
 template <int KMAX, int E, int PB>
 bool shape_feasible() {
     return BatchedCfg<KMAX, E, PB>::SMEM <= 113 * 1024;
 }
 
-void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int* nchunk, int64_t* ev_per_chunk,
-                      int blocks_per_sm = 2) {
-    const int ntp = (P + PB - 1) / PB;
-    int64_t target = ((int64_t)sm_count * blocks_per_sm) / ntp;
-    if (target < 1) target = 1;
-    int64_t tiles = (n + E - 1) / E;
-    if (tiles < 1) tiles = 1;
-    if (target > tiles) target = tiles;
-    const int64_t tpc = (tiles + target - 1) / target;
-    *ev_per_chunk = tpc * E;
-    int64_t nc = (n + *ev_per_chunk - 1) / *ev_per_chunk;
-    *nchunk = (int)(nc < 1 ? 1 : nc);
-}
 
 template <int KMAX, int E, int PB>
 cudaError_t batched_launch_shape(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
@@ -1028,7 +1016,8 @@ cudaError_t batched_launch(int shape, const float2* A, int K, int64_t n, int64_t
         case 0: return batched_launch_shape<KMAX, 64, 64>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
         case 1: return batched_launch_shape<KMAX, 64, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
         case 2: return batched_launch_shape<KMAX, 128, 32>(A, K, n, ld, V, P, ws, ws_bytes, bad, with_grad, sm_count, st, nchunk);
-        default: return batched2_launch<KMAX>(A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, nchunk);
+        case 3: return batched2_launch<KMAX>(A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, nchunk);
+        default: return tc_batched_launch(KMAX, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st, nchunk);
     }
 }
 
@@ -1038,7 +1027,8 @@ bool batched_shape_ok(int shape) {
         case 0: return shape_feasible<KMAX, 64, 64>();
         case 1: return shape_feasible<KMAX, 64, 32>();
         case 2: return shape_feasible<KMAX, 128, 32>();
-        default: return KMAX <= 32 && KMAX % 8 == 0;
+        case 3: return KMAX <= 32 && KMAX % 8 == 0;
+        default: return tc_batched_ok(KMAX);
     }
 }
 

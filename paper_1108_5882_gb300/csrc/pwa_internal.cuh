@@ -246,4 +246,26 @@ cudaError_t launch_generate(const WaveTable& wt, const float2* V, uint64_t seed,
                             int64_t n_cand, double envelope, float* kin, int64_t ld_out, int64_t max_out,
                             long long* n_acc, void* ws, cudaStream_t st);
 
+// Batched evaluation geometry: the events are cut into nchunk chunks of ev_per_chunk events (a
+// multiple of the tile E) so that chunks x ceil(P / PB) blocks fill blocks_per_sm blocks per SM.
+inline void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int* nchunk, int64_t* ev_per_chunk,
+                             int blocks_per_sm = 2) {
+    const int ntp = (P + PB - 1) / PB;
+    int64_t target = ((int64_t)sm_count * blocks_per_sm) / ntp;
+    if (target < 1) target = 1;
+    int64_t tiles = (n + E - 1) / E;
+    if (tiles < 1) tiles = 1;
+    if (target > tiles) target = tiles;
+    const int64_t tpc = (tiles + target - 1) / target;
+    *ev_per_chunk = tpc * E;
+    int64_t nc = (n + *ev_per_chunk - 1) / *ev_per_chunk;
+    *nchunk = (int)(nc < 1 ? 1 : nc);
+}
+
+// The tensor-core tile shape of the batched evaluation (3xTF32 emulated FP32, K <= 32).
+bool tc_batched_ok(int kmax);
+cudaError_t tc_batched_launch(int kmax, const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P, void* ws,
+                              size_t ws_bytes, int* bad, int* status, int with_grad, int sm_count, cudaStream_t st,
+                              int* nchunk);
+
 }  // namespace pwa

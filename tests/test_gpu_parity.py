@@ -177,6 +177,26 @@ def test_nll_grad_batched_pipelined_shape(h, K, P, n, monkeypatch):
     assert np.array_equal(f, f2) and np.array_equal(g, g2)
 
 
+@pytest.mark.parametrize("K,P,n", [(4, 3, 3001), (8, 64, 40_001), (13, 130, 9_999), (16, 64, 20_000),
+                                   (32, 256, 200_001), (32, 7, 1), (29, 300, 70_001)])
+def test_nll_grad_batched_tensor_core_shape(h, K, P, n, monkeypatch):
+    # the tensor-core kernel (shape 4: 3xTF32 products accumulated in FP32 in tensor memory,
+    # 64-event tiles, 128 sets per block) forced by the tuning override: ragged odd tails (NaN
+    # in the padding column), more tiles per block than the G accumulation window, several
+    # blocks of sets with a partial last one, K padded to 8, 16 or 32 waves
+    monkeypatch.setenv("PWA_BATCHED_SHAPE", "4")
+    p = make_problem(K, n, max(2 * n, 1000), SEED + 900 + K, accept_reject=False)
+    V = inputs.starts(P, K, SEED + P + 2)
+    V[0] = p.V_true
+    ld = n + 1 if n % 2 else n + 2
+    f, g = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), n, V, p.Psi)
+    check_nll(f, g, p.A, V, p.Psi)
+    f2, g2 = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi)
+    assert np.array_equal(f, f2) and np.array_equal(g, g2)
+    f3, _ = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi, grad=False)
+    assert np.array_equal(f3, f)  # the -lnL pass without the gradient GEMM gives the same bits
+
+
 def test_batched_equals_separate_sets(h):
     # per-set independence: P sets in one launch vs each set alone (within tolerance), and
     # permuting the sets permutes the outputs exactly
