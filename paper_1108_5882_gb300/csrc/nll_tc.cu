@@ -2,9 +2,9 @@
 // batched evaluation, chosen by the autotuner when it is the fastest): the event x wave x start
 // contraction of Eq. 3 as two real GEMMs per tile of E = 64 events, in FP32-accurate
 // arithmetic emulated with three TF32 products, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
-// (each operand split as x = hi + lo, both TF32; the dropped a_lo b_lo and the rounding of lo
-// leave a relative error of ~2^-21 per product, and the products accumulate in FP32 in tensor
-// memory).
+// (each operand split as x = hi + lo: hi the nearest TF32 value, lo = x - hi exactly, of which the
+// tensor cores use the leading 11 bits; the dropped a_lo b_lo and the truncation of lo leave a
+// relative error below 2^-20 per product, and the products accumulate in FP32 in tensor memory).
 //
 // Block: PB = 128 parameter sets (one per tensor-memory lane and per thread) x one chunk of
 // events, one block per SM.  Complex numbers are expanded into real rows and columns so that
@@ -325,8 +325,11 @@ __global__ void __launch_bounds__(256, 1) k_nll_tc(const float2* __restrict__ A,
                 mybad |= valid && !ok;
                 const bool use = valid && ok;
                 const float Iu = use ? I : 1.f;
-                lt += use ? __logf(Iu) : 0.f;
-                const float rc = use ? __fdividef(1.f, Iu) : 0.f;
+                // both functions evaluated unconditionally (a select, not a branch, picks the result)
+                const float lgu = __logf(Iu);
+                const float rcu = __fdividef(1.f, Iu);
+                lt += use ? lgu : 0.f;
+                const float rc = use ? rcu : 0.f;
                 tf32_split(use ? ur[k] * rc : 0.f, yrh[k], yrl[k]);
                 tf32_split(use ? ui[k] * rc : 0.f, yih[k], yil[k]);
             }

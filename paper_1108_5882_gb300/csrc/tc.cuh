@@ -104,11 +104,13 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// x = hi + lo + O(2^-22 |x|) with hi, lo TF32: the operand split of the three-product
-// emulation of an FP32 product, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
+// The operand split of the three-product emulation of an FP32 product, a b ~ a_hi b_hi +
+// a_hi b_lo + a_lo b_hi: hi = the nearest TF32 value, lo = x - hi (exact in FP32, |lo| <=
+// 2^-11 |x|).  The tensor cores read the leading 11 bits of lo, so x is represented to within
+// 2^-21 |x|.
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
     hi = tf32_round(x);
-    lo = tf32_round(x - hi);
+    lo = x - hi;
 }
 
 }  // namespace pwa
