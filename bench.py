@@ -365,17 +365,32 @@ def run_ours(args, world, rank, local):
                     "bytes_per_launch": alg_bytes, "kernel_us": kernel_ms * 1e3,
                     "peak_kind": f"{peak_kind} (copy bandwidth)"}
     else:
-        # the batched contraction is bound by FP32 FMA issue: per (event, start) 4K complex
-        # multiply-adds for U = A V^T and 4K for G = A^H W (16K flop) + ~12 for |U|^2, 1/I, ln I
+        # per (event, start): 4K complex multiply-adds for U = A V^T and 4K for G = A^H W (16K
+        # flop) + ~12 for |U|^2, 1/I, ln I
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = fma_peak_tflops(sms)
         flops = float(N) * P * (16 * K + 12)
         achieved = flops / (kernel_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "k_nll_batched + k_nll_finalize (one step)",
-                    "flops_per_launch": flops, "kernel_us": kernel_ms * 1e3,
-                    "peak_kind": "measured now: FFMA microbenchmark (libpwa_peaks.so), FP32 SIMT",
-                    "peak_derived": sms * 128 * 2 * 2.07e9 / 1e12}
+        ffma = fma_peak_tflops(sms)
+        shape = h.pwa_batched_shape(K, N, P)
+        if shape == 4:
+            # tensor cores: each FP32 product is three TF32 products, so the FP32-emulated peak is
+            # the TF32 dense peak / 3; the TF32 peak is the measured bf16 burst x the nominal
+            # TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                bf16 = float(json.load(fh)["bf16_tflops"])
+            peak = bf16 * (1.1 / 2.25) / 3.0
+            roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_nll_tc (tcgen05 3xTF32) + k_nll_finalize (one step)",
+                        "flops_per_launch": flops, "kernel_us": kernel_ms * 1e3,
+                        "peak_kind": "of measured: bf16 burst x 1.1/2.25 (TF32 dense) / 3 (FP32 emulation)",
+                        "fp32_simt_peak": ffma, "frac_of_fp32_simt": achieved / ffma}
+        else:
+            roofline = {"bound": "alu", "achieved": achieved, "peak": ffma, "unit": "TFLOP/s", "frac": achieved / ffma,
+                        "traffic": None, "kernel": f"k_nll_batched shape {shape} + k_nll_finalize (one step)",
+                        "flops_per_launch": flops, "kernel_us": kernel_ms * 1e3,
+                        "peak_kind": "measured now: FFMA microbenchmark (libpwa_peaks.so), FP32 SIMT",
+                        "peak_derived": sms * 128 * 2 * 2.07e9 / 1e12}
     launches = args.steps * (1 if P == 1 else 2)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -99,6 +99,14 @@ PWA_API size_t pwa_workspace_size(const pwa_handle* h, int K, int64_t n, int P);
  * (required before capturing those calls into a CUDA graph). */
 PWA_API pwa_status pwa_reserve(pwa_handle* h, int K, int64_t n, int P);
 
+/* Tile shape of the batched (P > 1) evaluation chosen for calls of this size: the autotuner
+ * times every feasible shape once per (K bucket, P bucket, n bucket) on the first call and keeps
+ * the fastest.  0-3: FP32 SIMT kernels (0-2: E x PB tiles of 64x64, 64x32, 128x32 events x sets,
+ * 3: 128x64 with bulk-copy staging); 4: the tensor-core kernel (tcgen05, FP32 products emulated
+ * with three TF32 products, K <= 32).  Returns -1 before the first call of that size (or the
+ * value forced by the PWA_BATCHED_SHAPE environment variable, if set and valid).  Host only. */
+PWA_API int pwa_batched_shape(int K, int64_t n, int P);
+
 /* Synchronise `stream`, then read and clear the device status word: PWA_OK, or
  * PWA_ERR_NONFINITE if any evaluation since the last check met I_i <= 0 / non-finite. */
 PWA_API pwa_status pwa_sync_status(pwa_handle* h, void* stream);
@@ -136,7 +144,13 @@ PWA_API pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t 
  *             extended likelihood; 1.0 gives Eq. 3 exactly as printed)
  *   nll    double [P] output (+inf for a set that met I_i <= 0 or a non-finite intensity)
  * Event sums run in single precision per thread, then double-single across threads and
- * blocks in a fixed order (deterministic: identical inputs give identical bits). */
+ * blocks in a fixed order (deterministic: identical inputs give identical bits).
+ * For P > 1 the autotuner may pick the tensor-core shape (pwa_batched_shape() == 4): FP32
+ * products emulated by three TF32 products and accumulated in FP32 in tensor memory.  It meets
+ * the same tolerances (1e-5 of the -lnL scale, 1e-4 of the gradient scale) but its error at a
+ * minimum, where the gradient cancels to ~1e-6 of its terms, is ~100x that of the SIMT shapes;
+ * pwa_fit_batch therefore evaluates with the SIMT shapes only, and PWA_BATCHED_SHAPE=0..3
+ * forces a SIMT shape for other callers. */
 PWA_API pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V,
                    int P, const double* Psi, double n_factor, double* nll, void* stream);
 

@@ -316,6 +316,11 @@ const char* pwa_last_error(const pwa_handle* h) {
     return g_create_err.c_str();
 }
 
+int pwa_batched_shape(int K, int64_t n, int P) {
+    if (K < 1 || K > PWA_MAX_WAVES || n < 0 || P < 2) return -1;
+    return pwa::batched_shape(K, n, P);
+}
+
 size_t pwa_workspace_size(const pwa_handle* h, int K, int64_t n, int P) {
     if (!h || K < 1 || K > PWA_MAX_WAVES || n < 0 || P < 1) return 0;
     size_t a = pwa::nll_workspace(K, n, P, h->sm_count);
@@ -690,7 +695,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
             cudaError_t ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
                                              reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll,
                                              eb[f].grad, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
-                                             h->sm_count, s);
+                                             h->sm_count, s, /*fp32_only=*/true);
             if (ee != cudaSuccess) return ee;
             ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
                                       o.gtol * std::fabs(d.n_factor), o.gauge_fix, o.max_iter, s);

@@ -190,9 +190,10 @@ cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t l
                                     const double2* Psi, double nfac, double* nll, double* grad, float2* part,
                                     size_t part_bytes, unsigned* counter, int* badw, int* status, int max_blocks,
                                     int sm_count, cudaStream_t st);
+// P > 1: autotuned tile shape; fp32_only restricts it to the FP32 SIMT shapes (the minimiser)
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
-                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st, bool fp32_only = false);
 
 // record a message for pwa_last_error(NULL) (calls without a handle)
 void record_global_error(const char* msg);
@@ -261,6 +262,9 @@ inline void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int*
     int64_t nc = (n + *ev_per_chunk - 1) / *ev_per_chunk;
     *nchunk = (int)(nc < 1 ? 1 : nc);
 }
+
+// The autotuned batched tile shape for (K, n, P), or -1 before the first evaluation of that size.
+int batched_shape(int K, int64_t n, int P);
 
 // The tensor-core tile shape of the batched evaluation (3xTF32 emulated FP32, K <= 32).
 bool tc_batched_ok(int kmax);

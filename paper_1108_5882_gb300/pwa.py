@@ -66,6 +66,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.pwa_workspace_size.restype = ctypes.c_size_t
         lib.pwa_reserve.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int]
         lib.pwa_reserve.restype = S
+        lib.pwa_batched_shape.argtypes = [ctypes.c_int, _i64, ctypes.c_int]
+        lib.pwa_batched_shape.restype = ctypes.c_int
         lib.pwa_sync_status.argtypes = [_vp, _vp]
         lib.pwa_sync_status.restype = S
         lib.pwa_amplitudes.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, _i64, _i64, _vp, _vp,
@@ -213,6 +215,9 @@ class Handle:
 
     def pwa_reserve(self, K, n, P):
         self._chk(self.lib.pwa_reserve(self.h, int(K), int(n), int(P)))
+
+    def pwa_batched_shape(self, K, n, P):
+        return int(self.lib.pwa_batched_shape(int(K), int(n), int(P)))
 
     def pwa_sync_status(self, stream=None):
         return int(self.lib.pwa_sync_status(self.h, _stream_ptr(stream)))

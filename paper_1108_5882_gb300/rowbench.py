@@ -186,8 +186,20 @@ def main():
         h.pwa_reserve(K, N, P)
         if "a4" in rows:
             sec = T(lambda: h.pwa_nll_grad(A, N, V, Psi, float(N), nll, g), max(5, R // 2))
-            add("a4", f"batched -lnL+grad, K={K}, N={N:.0e}, P={P} (autotuned shape)", sec, nbytes=N * K * 8,
-                flops=N * P * (16 * K + 12.0))
+            shape = h.pwa_batched_shape(K, N, P)
+            extra = {"shape": shape}
+            if shape == 4:
+                # tensor cores: FP32 products emulated by three TF32 products; peak = TF32 dense
+                # (measured bf16 burst x 1.1 / 2.25) / 3
+                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                    tpeak = float(json.load(fh)["bf16_tflops"]) * (1.1 / 2.25) / 3.0
+                extra.update({"tensor_emulated_fp32_peak": tpeak,
+                              "frac_tensor": N * P * (16 * K + 12.0) / sec / 1e12 / tpeak})
+            add("a4", f"batched -lnL+grad, K={K}, N={N:.0e}, P={P} (autotuned shape {shape})", sec, nbytes=N * K * 8,
+                flops=N * P * (16 * K + 12.0), extra=extra)
+            if shape == 4:
+                print(f"      tensor-core shape: {extra['frac_tensor']:.3f} of the 3xTF32 emulated-FP32 peak "
+                      f"({tpeak:.1f} TFLOP/s)", flush=True)
         if "a7" in rows:
             Vout = torch.empty((P, K), dtype=torch.complex128, device="cuda")
             torch.cuda.synchronize()

@@ -195,6 +195,7 @@ def test_nll_grad_batched_tensor_core_shape(h, K, P, n, monkeypatch):
     assert np.array_equal(f, f2) and np.array_equal(g, g2)
     f3, _ = gpu_nll_grad(h, padded(p.A, ld), n, V, p.Psi, grad=False)
     assert np.array_equal(f3, f)  # the -lnL pass without the gradient GEMM gives the same bits
+    assert h.pwa_batched_shape(K, n, P) == 4
 
 
 def test_batched_equals_separate_sets(h):
