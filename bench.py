@@ -297,36 +297,38 @@ def run_ours(args, world, rank, local):
     # ---- end to end from host buffers through the C ABI
     kin_h = wl["kin"].cpu().pin_memory()
     kin_mc_h = torch.from_numpy(wl["kin_mc_h"]).pin_memory()
-    kin_d = torch.empty_like(wl["kin"])
-    kin_mc_d = torch.empty_like(wl["kin_mc"])
+    # two device buffers per input: the copies of step t + 1 (on their own stream) overlap the
+    # kernels of step t; a buffer is refilled only after the step that read it is done with it
+    kin_d = [torch.empty_like(wl["kin"]) for _ in range(2)]
+    kin_mc_d = [torch.empty_like(wl["kin_mc"]) for _ in range(2)]
     V_h = wl["Vs"][0].cpu().pin_memory()
-    V_d = torch.empty_like(wl["Vs"][0])
+    V_d = [torch.empty_like(wl["Vs"][0]) for _ in range(2)]
     nll_h = torch.empty(P, dtype=torch.float64).pin_memory()
     grad_h = torch.empty((P, 2 * K), dtype=torch.float64).pin_memory()
     A, A_mc, Psi = torch.empty_like(wl["A"]), torch.empty_like(wl["A_mc"]), torch.empty_like(wl["Psi"])
     NMC = wl["NMC"]
-
-    # the MC kinematics travel on their own stream while the data sample is copied and its
-    # amplitudes computed; the next step's MC copy waits until this step's MC amplitudes
-    # have read the buffer
     copy_stream = torch.cuda.Stream()
-    mc_in = torch.cuda.Event()
-    mc_used = torch.cuda.Event()
-    mc_used.record(stream)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+    for ev in used:
+        ev.record(stream)
+    step_no = [0]
 
     def e2e_step():
-        copy_stream.wait_event(mc_used)
+        b = step_no[0] % 2
+        step_no[0] += 1
+        copy_stream.wait_event(used[b])
         with torch.cuda.stream(copy_stream):
-            kin_mc_d.copy_(kin_mc_h, non_blocking=True)
-            mc_in.record(copy_stream)
-        kin_d.copy_(kin_h, non_blocking=True)
-        V_d.copy_(V_h, non_blocking=True)
-        h.pwa_amplitudes(wl["waves"], kin_d, N, A)
-        stream.wait_event(mc_in)
-        h.pwa_amplitudes(wl["waves"], kin_mc_d, NMC, A_mc)
-        mc_used.record(stream)
+            kin_d[b].copy_(kin_h, non_blocking=True)
+            V_d[b].copy_(V_h, non_blocking=True)
+            kin_mc_d[b].copy_(kin_mc_h, non_blocking=True)
+            copied[b].record(copy_stream)
+        stream.wait_event(copied[b])
+        h.pwa_amplitudes(wl["waves"], kin_d[b], N, A)
+        h.pwa_amplitudes(wl["waves"], kin_mc_d[b], NMC, A_mc)
         h.pwa_normint(A_mc, NMC, Psi)
-        h.pwa_nll_grad(A, N, V_d, Psi, float(N), nll, grad)
+        h.pwa_nll_grad(A, N, V_d[b], Psi, float(N), nll, grad)
+        used[b].record(stream)
         nll_h.copy_(nll, non_blocking=True)
         grad_h.copy_(grad, non_blocking=True)
 
@@ -337,7 +339,8 @@ def run_ours(args, world, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     e0.record(stream)
-    mc_used.record(stream)  # the first timed MC copy starts after e0
+    for ev in used:  # the first timed copies start after e0
+        ev.record(stream)
     for _ in range(n_e2e):
         e2e_step()
     e1.record(stream)
@@ -348,9 +351,9 @@ def run_ours(args, world, rank, local):
     # the copy part of an e2e step alone (the same three host-to-device copies), for the breakdown
     e0.record(stream)
     for _ in range(n_e2e):
-        kin_d.copy_(kin_h, non_blocking=True)
-        kin_mc_d.copy_(kin_mc_h, non_blocking=True)
-        V_d.copy_(V_h, non_blocking=True)
+        kin_d[0].copy_(kin_h, non_blocking=True)
+        kin_mc_d[0].copy_(kin_mc_h, non_blocking=True)
+        V_d[0].copy_(V_h, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     h2d_ms = e0.elapsed_time(e1) / n_e2e
@@ -402,8 +405,8 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * N * P / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "h2d_ms_per_step": h2d_ms,
-                "what": "pinned H2D of data+MC kinematics (MC on a second stream, overlapping the data copy and "
-                        "data amplitudes), amplitudes(data, MC), Psi, -lnL+grad, D2H of nll+grad"},
+                "what": "pinned H2D of data+MC kinematics and V (copy stream, double-buffered: step t+1's copies "
+                        "overlap step t's kernels), amplitudes(data, MC), Psi, -lnL+grad, D2H of nll+grad"},
         "gpu_launches": launches,
         "roofline": roofline,
         "clocks": sampler.summary(),
