@@ -316,7 +316,10 @@ PWA_API pwa_status pwa_toy_moments(pwa_handle* h, const pwa_wave* waves, int K, 
  *   with A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk] (element strides; a_type/b_type
  *   0 = float32, 1 = bfloat16); writes C (float, row stride ldc) and/or C_bf16; accumulate adds
  *   the previous C.  Forward: A = X[B][in], B = W[out][in].  Data gradient: A = dY, B = W with
- *   (sbn, sbk) = (1, in).  Weight gradient: A = dY with (sam, sak) = (1, out), B = X with (1, in). */
+ *   (sbn, sbk) = (1, in).  Weight gradient: A = dY with (sam, sak) = (1, out), B = X with (1, in).
+ *   With B in BF16 the product runs on the tensor cores (BF16 MMA, FP32 accumulation in tensor
+ *   memory over chunks of 64, then FP32 in registers); an FP32 A is split into three BF16 parts
+ *   (24 significant bits), so its products are exact as in FP32.  With B in FP32: SIMT FP32. */
 PWA_API pwa_status pwa_mlp_gemm(pwa_handle* h, int M, int N, int Kc, const void* A, int a_type,
                                 int64_t sam, int64_t sak, const void* B, int b_type, int64_t sbn,
                                 int64_t sbk, const float* bias, int relu, int accumulate, float* C,

@@ -347,6 +347,7 @@ pwa_status pwa_sync_status(pwa_handle* h, void* stream) {
     if (s) {
         e = cudaMemset(h->status, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+        if (s & 2) return fail(h, PWA_ERR_TIMEOUT, "a bounded device-side wait gave up (results of that call are flagged)");
         return fail(h, PWA_ERR_NONFINITE, "an evaluation met an event with intensity <= 0 or not finite");
     }
     return PWA_OK;
@@ -555,8 +556,12 @@ pwa_status pwa_mlp_gemm(pwa_handle* h, int M, int N, int Kc, const void* A, int 
         return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: element type must be 0 (float32) or 1 (bfloat16)");
     if (sam < 0 || sak < 0 || sbn < 0 || sbk < 0) return fail(h, PWA_ERR_INVALID_ARG, "pwa_mlp_gemm: negative stride");
     DeviceGuard dg(h->device);
-    cudaError_t e = pwa::launch_mlp_gemm(M, N, Kc, A, a_type, sam, sak, B, b_type, sbn, sbk, bias, relu, accumulate, C,
-                                         C_bf16, ldc, h->sm_count, (cudaStream_t)stream);
+    // B in BF16 (every product of the proposer's network): tensor cores; B in FP32: SIMT kernel
+    cudaError_t e = b_type == 1
+                        ? pwa::launch_mlp_gemm_tc(M, N, Kc, A, a_type, sam, sak, B, sbn, sbk, bias, relu, accumulate,
+                                                  C, C_bf16, ldc, h->status, (cudaStream_t)stream)
+                        : pwa::launch_mlp_gemm(M, N, Kc, A, a_type, sam, sak, B, b_type, sbn, sbk, bias, relu,
+                                               accumulate, C, C_bf16, ldc, h->sm_count, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mlp gemm");
     return PWA_OK;
 }

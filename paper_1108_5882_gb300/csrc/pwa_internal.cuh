@@ -234,6 +234,11 @@ cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const doub
 cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
                             int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
                             uint16_t* Cb, int64_t ldc, int sm_count, cudaStream_t st);
+// The same product on the tensor cores (tcgen05 kind::f16) for a BF16 B; an FP32 A is split into
+// three BF16 parts.  A timeout of its bounded wait sets status bit 1.
+cudaError_t launch_mlp_gemm_tc(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak,
+                               const void* B, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate,
+                               float* C, uint16_t* Cb, int64_t ldc, int* status, cudaStream_t st);
 cudaError_t launch_mlp_relu_bwd(const uint16_t* Y, float* dY, int64_t n, int sm_count, cudaStream_t st);
 cudaError_t launch_mlp_bias_grad(const float* dY, int B, int N, float* db, cudaStream_t st);
 cudaError_t launch_mlp_wta(const float* out, const float* target, int B, int C, int K, float eps, float* loss,
