@@ -105,12 +105,25 @@ __global__ void k_relu_bwd(const __nv_bfloat16* __restrict__ Y, float* __restric
         if (!(__bfloat162float(Y[i]) > 0.f)) dY[i] = 0.f;
 }
 
-__global__ void k_bias_grad(const float* __restrict__ dY, int B, int N, float* __restrict__ db) {
-    const int nidx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nidx >= N) return;
+// db[n] = sum_b dY[b][n]: a block takes 32 columns; warp w sums rows w, w + 8, ... of them (lanes
+// along n, coalesced), then lane n of warp 0 adds the 8 warp sums in warp order (fixed order).
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ dY, int B, int N, float* __restrict__ db) {
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nidx = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dY[(int64_t)b * N + nidx];
-    db[nidx] = s;
+    if (nidx < N) {
+#pragma unroll 8
+        for (int b = w; b < B; b += 8) s += dY[(int64_t)b * N + nidx];
+    }
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && nidx < N) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += part[k][lane];
+        db[nidx] = t;
+    }
 }
 
 // one warp per sample; lane c = candidate c (C <= 32)
@@ -234,7 +247,7 @@ cudaError_t launch_mlp_relu_bwd(const uint16_t* Y, float* dY, int64_t n, int sm_
 }
 
 cudaError_t launch_mlp_bias_grad(const float* dY, int B, int N, float* db, cudaStream_t st) {
-    k_bias_grad<<<(N + 255) / 256, 256, 0, st>>>(dY, B, N, db);
+    k_bias_grad<<<(N + 31) / 32, 256, 0, st>>>(dY, B, N, db);
     return cudaGetLastError();
 }
 
