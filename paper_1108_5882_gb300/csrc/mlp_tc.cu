@@ -11,8 +11,7 @@
 //
 // Block: a 128 x 64 output tile (one tensor-memory lane per row, 64 FP32 columns), 256 threads.
 // The contraction runs in chunks of 64: the threads stage the chunk of A (each part) and B into
-// shared memory as K-major core matrices (8 rows x 16 bytes, no swizzle; the loads run along
-// whichever index is contiguous in memory), one thread issues 4 k-steps x (1 or 3) MMAs, and
+// shared memory as K-major core matrices (8 rows x 16 bytes, no swizzle), one thread issues 4 k-steps x (1 or 3) MMAs, and
 // after they complete every thread adds its row's 64 columns to FP32 registers (rounded to
 // nearest).  Keeping the tensor-memory accumulation to one chunk bounds the error of its
 // unrounded FP32 additions to ~12 steps.  The smaller parts go first.
@@ -26,7 +25,7 @@ namespace pwa {
 namespace {
 
 constexpr int MT_NT = 256, MT_BM = 128, MT_BN = 64, MT_BK = 64;
-constexpr int MT_RA = MT_BM * MT_BK / MT_NT, MT_RB = MT_BN * MT_BK / MT_NT;  // staged elements per thread
+constexpr int MT_IA = MT_BM * MT_BK / 8 / MT_NT, MT_IB = MT_BN * MT_BK / 8 / MT_NT;  // staging items per thread
 constexpr uint32_t MT_SBO = 8u * MT_BK * 2u;  // bytes between 8-row groups (rows of 64 BF16)
 constexpr uint32_t MT_A_BYTES = MT_BM * MT_BK * 2u, MT_B_BYTES = MT_BN * MT_BK * 2u;
 constexpr uint64_t MT_WAIT_NS = 1000000000ull;
@@ -55,7 +54,7 @@ __device__ __forceinline__ float ld_val(const __nv_bfloat16* p, int64_t i) { ret
 // 256 threads: warps w and w + 4 share tensor-memory lanes 32 (w % 4) + 0..31 (the tile's rows)
 // and take columns 0..31 and 32..63 of them.  Per chunk each thread loads its 32 elements of A
 // and 16 of B into registers (the loads of chunk c + 1 are issued while the MMAs of chunk c
-// run), then converts and stores them.
+// run), then converts and stores them as 16-byte rows of core matrices.
 template <typename TA>
 __global__ void __launch_bounds__(MT_NT) k_mlp_tc(int M, int N, int Kc, const TA* __restrict__ A, int64_t sam,
                                                   int64_t sak, const __nv_bfloat16* __restrict__ B, int64_t sbn,
@@ -73,8 +72,6 @@ __global__ void __launch_bounds__(MT_NT) k_mlp_tc(int M, int N, int Kc, const TA
     const int tid = threadIdx.x, warp = tid >> 5;
     const int lq = warp & 3, hh = warp >> 2;
     const int m0 = blockIdx.x * MT_BM, n0 = blockIdx.y * MT_BN;
-    const bool a_mfast = sam == 1 && sak != 1;
-    const bool b_nfast = sbn == 1 && sbk != 1;
 
     if (warp == 0) tmem_alloc(taddr_s, 64);
     if (tid == 0) {
@@ -89,46 +86,70 @@ __global__ void __launch_bounds__(MT_NT) k_mlp_tc(int M, int N, int Kc, const TA
     const uint32_t sbase = smem_u32(msm);
     constexpr uint32_t idesc = umma_idesc_bf16(MT_BM, MT_BN);
 
-    float xa[MT_RA];
-    __nv_bfloat16 xb[MT_RB];
+    // staging items: (row, 8 consecutive k) -> one 16-byte store per part into the K-major
+    // tile; the lanes of a warp take consecutive rows, so the 8 lanes of a store phase write 8
+    // rows of one core matrix (no bank conflict)
+    float xa[MT_IA][8];
+    __nv_bfloat16 xb[MT_IB][8];
     auto load_chunk = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < MT_RA; ++r) {
+        for (int r = 0; r < MT_IA; ++r) {
             const int idx = tid + MT_NT * r;
-            const int mm = a_mfast ? idx % MT_BM : idx / MT_BK, kk = a_mfast ? idx / MT_BM : idx % MT_BK;
-            const int gm = m0 + mm, gk = k0 + kk;
-            xa[r] = (gm < M && gk < Kc) ? ld_val(A, (int64_t)gm * sam + (int64_t)gk * sak) : 0.f;
-        }
+            const int mm = idx % MT_BM, ko = idx / MT_BM;
+            const int gm = m0 + mm;
 #pragma unroll
-        for (int r = 0; r < MT_RB; ++r) {
-            const int idx = tid + MT_NT * r;
-            const int nn = b_nfast ? idx % MT_BN : idx / MT_BK, kk = b_nfast ? idx / MT_BN : idx % MT_BK;
-            const int gn = n0 + nn, gk = k0 + kk;
-            xb[r] = (gn < N && gk < Kc) ? B[(int64_t)gn * sbn + (int64_t)gk * sbk] : __float2bfloat16_rn(0.f);
-        }
-    };
-    auto store_chunk = [&]() {
-#pragma unroll
-        for (int r = 0; r < MT_RA; ++r) {
-            const int idx = tid + MT_NT * r;
-            const int mm = a_mfast ? idx % MT_BM : idx / MT_BK, kk = a_mfast ? idx / MT_BM : idx % MT_BK;
-            const uint32_t o = bf_off(mm, kk);
-            const float x = xa[r];
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            *reinterpret_cast<__nv_bfloat16*>(sA + o) = hi;
-            if (SPLIT) {
-                const float rr = x - __bfloat162float(hi);
-                const __nv_bfloat16 mid = __float2bfloat16_rn(rr);
-                *reinterpret_cast<__nv_bfloat16*>(sA + MT_A_BYTES + o) = mid;
-                *reinterpret_cast<__nv_bfloat16*>(sA + 2 * MT_A_BYTES + o) =
-                    __float2bfloat16_rn(rr - __bfloat162float(mid));
+            for (int j = 0; j < 8; ++j) {
+                const int gk = k0 + 8 * ko + j;
+                xa[r][j] = (gm < M && gk < Kc) ? ld_val(A, (int64_t)gm * sam + (int64_t)gk * sak) : 0.f;
             }
         }
 #pragma unroll
-        for (int r = 0; r < MT_RB; ++r) {
+        for (int r = 0; r < MT_IB; ++r) {
             const int idx = tid + MT_NT * r;
-            const int nn = b_nfast ? idx % MT_BN : idx / MT_BK, kk = b_nfast ? idx / MT_BN : idx % MT_BK;
-            *reinterpret_cast<__nv_bfloat16*>(sB + bf_off(nn, kk)) = xb[r];
+            const int nn = idx % MT_BN, ko = idx / MT_BN;
+            const int gn = n0 + nn;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int gk = k0 + 8 * ko + j;
+                xb[r][j] = (gn < N && gk < Kc) ? B[(int64_t)gn * sbn + (int64_t)gk * sbk] : __float2bfloat16_rn(0.f);
+            }
+        }
+    };
+    auto pack8 = [](const __nv_bfloat16 (&v)[8]) {
+        uint4 u;
+        u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+        u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+        u.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
+        u.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
+        return u;
+    };
+    auto store_chunk = [&]() {
+#pragma unroll
+        for (int r = 0; r < MT_IA; ++r) {
+            const int idx = tid + MT_NT * r;
+            const int mm = idx % MT_BM, ko = idx / MT_BM;
+            const uint32_t o = bf_off(mm, 8 * ko);
+            __nv_bfloat16 hi[8], mid[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hi[j] = __float2bfloat16_rn(xa[r][j]);
+                if (SPLIT) {
+                    const float rr = xa[r][j] - __bfloat162float(hi[j]);
+                    mid[j] = __float2bfloat16_rn(rr);
+                    lo[j] = __float2bfloat16_rn(rr - __bfloat162float(mid[j]));
+                }
+            }
+            *reinterpret_cast<uint4*>(sA + o) = pack8(hi);
+            if (SPLIT) {
+                *reinterpret_cast<uint4*>(sA + MT_A_BYTES + o) = pack8(mid);
+                *reinterpret_cast<uint4*>(sA + 2 * MT_A_BYTES + o) = pack8(lo);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < MT_IB; ++r) {
+            const int idx = tid + MT_NT * r;
+            const int nn = idx % MT_BN, ko = idx / MT_BN;
+            *reinterpret_cast<uint4*>(sB + bf_off(nn, 8 * ko)) = pack8(xb[r]);
         }
     };
 
