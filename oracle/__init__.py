@@ -61,6 +61,9 @@ def _load():
             lib.orc_nll_grad.argtypes = [ctypes.c_int, _i64, _fp, _i64, ctypes.c_int, _dp, _dp,
                                          ctypes.c_double, _dp, _dp, _dp, _dp]
             lib.orc_nll_grad.restype = ctypes.c_int
+            lib.orc_nll_grad_incoherent.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _fp, _i64, ctypes.c_int, _dp,
+                                                    _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+            lib.orc_nll_grad_incoherent.restype = ctypes.c_int
             lib.orc_nll_double_sum.argtypes = [ctypes.c_int, _i64, _fp, _i64, _dp, _dp,
                                                ctypes.c_double]
             lib.orc_nll_double_sum.restype = ctypes.c_double
@@ -164,6 +167,38 @@ def nll_grad(A, V, Psi, n_factor=None, with_cond: bool = False):
     if with_cond:
         return nll, grad, cf, cg, bad
     return nll, grad
+
+
+def nll_grad_incoherent(A, V, Psi, n_factor=None, with_cond: bool = False):
+    """-lnL and gradient with the intensity summed incoherently over H states:
+    A complex64 [K][H][n], I_i = sum_h |sum_a V_a A[a][h][i]|^2, Psi = the normalisation
+    integral summed over h (normint_incoherent).  Outputs as nll_grad."""
+    lib = _load()
+    K, H, n = A.shape
+    Af = _c64_as_f32(np.ascontiguousarray(A).reshape(K, H * n)).reshape(-1)
+    V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.complex128)
+    P = V.shape[0]
+    assert V.shape[1] == K
+    Psi = np.ascontiguousarray(Psi, dtype=np.complex128)
+    if n_factor is None:
+        n_factor = float(n)
+    nll = np.zeros(P, dtype=np.float64)
+    grad = np.zeros((P, 2 * K), dtype=np.float64)
+    cf = np.zeros(P, dtype=np.float64)
+    cg = np.zeros((P, K), dtype=np.float64)
+    bad = lib.orc_nll_grad_incoherent(K, H, n, _ptr(Af, _fp), n, P, _ptr(V, _dp), _ptr(Psi, _dp), float(n_factor),
+                                      _ptr(nll, _dp), _ptr(grad, _dp), _ptr(cf, _dp), _ptr(cg, _dp))
+    if with_cond:
+        return nll, grad, cf, cg, bad
+    return nll, grad
+
+
+def normint_incoherent(A, n_gen=None, w=None):
+    """Psi summed over the H states of A complex64 [K][H][n]: the (event, state) pairs are the
+    terms of one MC sum, so this is normint over the K x (H n) array (weights repeat per state)."""
+    K, H, n = A.shape
+    ww = None if w is None else np.tile(np.asarray(w, dtype=np.float32), H)
+    return normint(np.ascontiguousarray(A).reshape(K, H * n), n_gen=float(n if n_gen is None else n_gen), w=ww)
 
 
 def nll_double_sum(A, V, Psi, n_factor=None) -> float:

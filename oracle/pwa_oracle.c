@@ -13,6 +13,9 @@
  *   - -lnL fed to the minimiser (Sec. 2, footnote 2), extended form
  *       f(V) = -sum_i ln I_i + n_factor * sum_ab V_a conj(V_b) Psi_ab
  *     and its gradient g_c = dF/dRe V_c + i dF/dIm V_c = 2 dF/dconj(V_c)
+ *   - the same with the intensity summed incoherently over unobserved states h,
+ *     I = sum_h |sum_a V_a A_{a,h}|^2 (Eq. 1 summed over h; the paper's own example, J/psi ->
+ *     gamma X, has such a state: the photon helicity)
  *   - the double-sum form of Eq. 3 in long double (used only to pin the O(K) form above)
  *   - the amplitude model A_a = BW_a(m) P_J(cos th) exp(i lambda phi) and its derivatives
  *     in the resonance mass and width (the paper gives no amplitude formula; the reading is
@@ -198,6 +201,94 @@ int orc_nll_grad(int K, int64_t n, const float* A, int64_t ld, int P, const doub
         bad_sets += bad;
     }
     free(Ai); free(gre); free(gim); free(gsc);
+    return bad_sets;
+}
+
+/* Incoherent sum over H unobserved states (e.g. the radiated photon's helicity in J/psi ->
+ * gamma X): the amplitudes carry a state index h, A_{a,h}(i) at A[2 ((a H + h) ld + i)], the
+ * production amplitudes V_a are shared by all h, and the intensity adds the states
+ * incoherently (a sum of Eq. 1 over h):
+ *   I_i = sum_h |u_ih|^2,  u_ih = sum_a V_a A_{a,h}(i).
+ * The extended -lnL keeps the form of Eq. 3 with the normalisation integral summed over h,
+ * Psi_ab = (1/N_gen) sum_j sum_h A_{a,h}(j) conj(A_{b,h}(j)) (the caller passes that Psi):
+ *   f = -sum_i ln I_i + n_factor sum_ab V_a conj(V_b) Psi_ab,
+ *   g_c = 2 df/dconj(V_c) = -2 sum_i sum_h conj(A_{c,h}(i)) u_ih / I_i + 2 n_factor sum_a Psi_ac V_a.
+ * cond_f / cond_g as in orc_nll_grad, with s_ih = sum_a |V_a| |A_{a,h}(i)| per state. */
+int orc_nll_grad_incoherent(int K, int H, int64_t n, const float* A, int64_t ld, int P, const double* Vd,
+                            const double* Psid, double n_factor, double* nll, double* grad,
+                            double* cond_f, double* cond_g) {
+    const cplx* V = (const cplx*)Vd;
+    const cplx* Psi = (const cplx*)Psid;
+    int bad_sets = 0;
+    cplx* Ai = (cplx*)malloc(sizeof(cplx) * (size_t)K * (size_t)H);
+    cplx* u = (cplx*)malloc(sizeof(cplx) * (size_t)H);
+    double* su = (double*)malloc(sizeof(double) * (size_t)H);
+    nsum* gre = (nsum*)malloc(sizeof(nsum) * (size_t)K);
+    nsum* gim = (nsum*)malloc(sizeof(nsum) * (size_t)K);
+    double* gsc = (double*)malloc(sizeof(double) * (size_t)K);
+    for (int p = 0; p < P; ++p) {
+        const cplx* Vp = V + (int64_t)p * K;
+        nsum lnsum = {0, 0};
+        double lnabs = 0.0;
+        int bad = 0;
+        for (int c = 0; c < K; ++c) { gre[c].s = gre[c].c = gim[c].s = gim[c].c = 0.0; gsc[c] = 0.0; }
+        for (int64_t i = 0; i < n; ++i) {
+            double Ii = 0.0;
+            for (int h = 0; h < H; ++h) {
+                u[h] = 0.0;
+                su[h] = 0.0;
+                for (int a = 0; a < K; ++a) {
+                    const int64_t o = 2 * (((int64_t)a * H + h) * ld + i);
+                    Ai[a * H + h] = A[o] + I * A[o + 1];
+                    u[h] += Vp[a] * Ai[a * H + h];
+                    su[h] += cabs(Vp[a]) * cabs(Ai[a * H + h]);
+                }
+                Ii += creal(u[h]) * creal(u[h]) + cimag(u[h]) * cimag(u[h]);
+            }
+            if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; continue; }
+            double l = log(Ii);
+            nsum_add(&lnsum, l);
+            lnabs += fabs(l);
+            for (int c = 0; c < K; ++c) {
+                cplx t = 0.0;
+                double ts = 0.0;
+                for (int h = 0; h < H; ++h) {
+                    t += conj(Ai[c * H + h]) * u[h];
+                    ts += cabs(Ai[c * H + h]) * su[h];
+                }
+                t /= Ii;
+                nsum_add(&gre[c], -2.0 * creal(t));
+                nsum_add(&gim[c], -2.0 * cimag(t));
+                gsc[c] += 2.0 * ts / Ii;
+            }
+        }
+        cplx S = 0.0;
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) S += Vp[a] * conj(Vp[b]) * Psi[a * K + b];
+        double f = -nsum_get(&lnsum) + n_factor * creal(S);
+        for (int c = 0; c < K; ++c) {
+            cplx nt = 0.0;
+            double nts = 0.0;
+            for (int a = 0; a < K; ++a) {
+                nt += Psi[a * K + c] * Vp[a];
+                nts += cabs(Psi[a * K + c]) * cabs(Vp[a]);
+            }
+            double gr = nsum_get(&gre[c]) + 2.0 * n_factor * creal(nt);
+            double gi = nsum_get(&gim[c]) + 2.0 * n_factor * cimag(nt);
+            grad[(int64_t)p * 2 * K + 2 * c] = bad ? 0.0 : gr;
+            grad[(int64_t)p * 2 * K + 2 * c + 1] = bad ? 0.0 : gi;
+            if (cond_g) cond_g[(int64_t)p * K + c] = gsc[c] + 2.0 * fabs(n_factor) * nts;
+        }
+        nll[p] = bad ? INFINITY : f;
+        if (cond_f) {
+            double cf = fabs(f);
+            if (lnabs > cf) cf = lnabs;
+            if (fabs(n_factor * creal(S)) > cf) cf = fabs(n_factor * creal(S));
+            cond_f[p] = cf;
+        }
+        bad_sets += bad;
+    }
+    free(Ai); free(u); free(su); free(gre); free(gim); free(gsc);
     return bad_sets;
 }
 

@@ -520,3 +520,103 @@ def test_bf16_rounding_is_round_to_nearest_even():
     back = mlp.bf16_to_f64(b)
     assert back[0] == 1.0 and back[1] == 1.0 and back[2] == 1.0078125 and back[3] == 1.015625  # ties to even
     assert np.all(np.abs(back - x) <= np.abs(x) * 2.0 ** -8)
+
+
+# ------------------------------------------------------------------ incoherent sums ----------
+# I_i = sum_h |sum_a V_a A_{a,h}(i)|^2 over H unobserved states (Eq. 1 summed over h), with the
+# normalisation integral summed over h as well.
+
+def _rand_AH(K, H, n, seed, scale=1.0):
+    g = np.random.default_rng(seed)
+    return (scale * (g.normal(size=(K, H, n)) + 1j * g.normal(size=(K, H, n)))).astype(np.complex64)
+
+
+def test_incoherent_normint_sums_the_states():
+    Amc = _rand_AH(5, 3, 700, 61)
+    ref = sum(oracle.normint(np.ascontiguousarray(Amc[:, h, :]), n_gen=700.0) for h in range(3))
+    assert np.allclose(oracle.normint_incoherent(Amc, n_gen=700.0), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_incoherent_one_state_is_the_coherent_likelihood():
+    A = _rand_AH(5, 1, 400, 62)
+    Psi = oracle.normint_incoherent(_rand_AH(5, 1, 1600, 63))
+    V = _rand_V(5, 64)
+    f1, g1 = oracle.nll_grad_incoherent(A, V[None, :], Psi)
+    f0, g0 = oracle.nll_grad(np.ascontiguousarray(A[:, 0, :]), V[None, :], Psi)
+    assert abs(f1[0] - f0[0]) <= 1e-12 * abs(f0[0])
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
+
+
+def test_incoherent_empty_state_adds_nothing():
+    # a state whose amplitudes vanish contributes to neither the data sum nor Psi
+    A = _rand_AH(4, 2, 400, 65)
+    A[:, 1, :] = 0
+    Amc = _rand_AH(4, 2, 1600, 66)
+    Amc[:, 1, :] = 0
+    V = _rand_V(4, 67)
+    f1, g1 = oracle.nll_grad_incoherent(A, V[None, :], oracle.normint_incoherent(Amc))
+    f0, g0 = oracle.nll_grad(np.ascontiguousarray(A[:, 0, :]), V[None, :],
+                             oracle.normint(np.ascontiguousarray(Amc[:, 0, :])))
+    assert abs(f1[0] - f0[0]) <= 1e-12 * abs(f0[0])
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
+
+
+def test_incoherent_phase_copies_closed_form():
+    # A_h = i^h A_0 (exact in complex64) for h < 4: I_i = 4 |u_i0|^2 and Psi = 4 Psi_0, so
+    # f = f_coherent(A_0, 4 Psi_0) - n ln 4 and the gradient is the coherent one with 4 Psi_0
+    K, n, H = 4, 500, 4
+    A0 = _rand_AH(K, 1, n, 68)[:, 0, :]
+    A0mc = _rand_AH(K, 1, 2000, 69)[:, 0, :]
+    A = np.stack([A0 * (1j ** h) for h in range(H)], axis=1).astype(np.complex64)
+    Amc = np.stack([A0mc * (1j ** h) for h in range(H)], axis=1).astype(np.complex64)
+    assert np.array_equal(np.abs(A[:, 3, :]), np.abs(A0))
+    V = _rand_V(K, 70)
+    Psi = oracle.normint_incoherent(Amc, n_gen=2000.0)
+    Psi0 = oracle.normint(A0mc, n_gen=2000.0)
+    assert np.allclose(Psi, 4 * Psi0, rtol=1e-13, atol=1e-13)
+    f, g = oracle.nll_grad_incoherent(A, V[None, :], Psi)
+    f0, g0 = oracle.nll_grad(A0, V[None, :], 4 * Psi0)
+    assert abs(f[0] - (f0[0] - n * math.log(4.0))) <= 1e-11 * abs(f0[0])
+    assert np.max(np.abs(g - g0)) <= 1e-11 * np.max(np.abs(g0))
+
+
+def test_incoherent_gradient_finite_differences():
+    A = _rand_AH(3, 2, 800, 71)
+    Psi = oracle.normint_incoherent(_rand_AH(3, 2, 3000, 72))
+    V = _rand_V(3, 73)
+    _, g = oracle.nll_grad_incoherent(A, V[None, :], Psi)
+    for c in range(3):
+        for part, unit in ((0, 1.0), (1, 1j)):
+            h = 1e-6 * max(1.0, abs(V[c]))
+            Vp, Vm = V.copy(), V.copy()
+            Vp[c] += unit * h
+            Vm[c] -= unit * h
+            fd = (oracle.nll_grad_incoherent(A, Vp[None, :], Psi)[0][0]
+                  - oracle.nll_grad_incoherent(A, Vm[None, :], Psi)[0][0]) / (2 * h)
+            assert abs(fd - g[0, 2 * c + part]) <= 2e-5 * max(1.0, abs(g[0, 2 * c + part]))
+
+
+def test_incoherent_brute_force_and_global_phase():
+    # the definition with plain Python loops on a tiny case, and f(e^{i alpha} V) = f(V)
+    K, H, n = 2, 3, 5
+    A = _rand_AH(K, H, n, 74)
+    Psi = oracle.normint_incoherent(_rand_AH(K, H, 9, 75))
+    V = _rand_V(K, 76)
+    f, g = oracle.nll_grad_incoherent(A, V[None, :], Psi, n_factor=2.5)
+    Ad = A.astype(np.complex128)
+    lnsum = 0.0
+    gd = [0j] * K
+    for i in range(n):
+        us = [sum(V[a] * Ad[a, h, i] for a in range(K)) for h in range(H)]
+        Ii = sum(abs(u) ** 2 for u in us)
+        lnsum += math.log(Ii)
+        for c in range(K):
+            gd[c] += -2 * sum(np.conj(Ad[c, h, i]) * us[h] for h in range(H)) / Ii
+    S = sum(V[a] * np.conj(V[b]) * Psi[a, b] for a in range(K) for b in range(K))
+    assert abs(f[0] - (-lnsum + 2.5 * S.real)) <= 1e-12 * abs(f[0])
+    for c in range(K):
+        gc = gd[c] + 2 * 2.5 * sum(Psi[a, c] * V[a] for a in range(K))
+        assert abs(g[0, 2 * c] - gc.real) <= 1e-12 * max(1.0, abs(gc))
+        assert abs(g[0, 2 * c + 1] - gc.imag) <= 1e-12 * max(1.0, abs(gc))
+    fr, _ = oracle.nll_grad_incoherent(A, (V * np.exp(0.7j))[None, :], Psi, n_factor=2.5)
+    assert abs(fr[0] - f[0]) <= 1e-12 * abs(f[0])
