@@ -48,6 +48,7 @@ extern "C" {
 
 #define PWA_ABI_VERSION 1
 #define PWA_MAX_WAVES 64
+#define PWA_MAX_STATES 4   /* incoherently summed states (pwa_nll_grad_incoherent) */
 #define PWA_MAX_FLOAT 8   /* floating shape parameters per likelihood (pwa_nll_grad_shape) */
 
 typedef enum pwa_status {
@@ -162,6 +163,24 @@ PWA_API pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int6
 PWA_API pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld,
                         const float* V, int P, const double* Psi, double n_factor, double* nll,
                         double* grad, void* stream);
+
+/* -lnL (and its gradient) with the intensity summed incoherently over H unobserved states, e.g.
+ * the helicity of the radiated photon in J/psi -> gamma X (the paper's example, Sec. 2): Eq. 1
+ * summed over h with the production amplitudes shared by all states,
+ *   I_i = sum_h |sum_a V[p][a] A_{a,h}(i)|^2,
+ *   nll[p] = -sum_i ln I_i + n_factor sum_ab V[p][a] conj(V[p][b]) Psi_ab,
+ *   g_c = -2 sum_i sum_h conj(A_{c,h}(i)) u_ih / I_i + 2 n_factor sum_a Psi_ac V[p][a].
+ *   A    complex float [K][H][ld]: A_{a,h}(i) at element (a H + h) ld + i; ld even, 16-byte aligned
+ *   H    1 <= H <= PWA_MAX_STATES
+ *   Psi  the normalisation integral summed over the states: pwa_normint over the MC amplitudes
+ *        viewed as [K][H ld] with n = H ld (the (event, state) pairs are the terms of one MC
+ *        sum; padding columns must be zero, as pwa_amplitudes writes them)
+ *   grad double [P][2K] output, or NULL for -lnL only.
+ * One parameter set per launch (the single-set kernel with a loop over h, exact fixed-point
+ * grid sums, deterministic); P sets are P launches on `stream`. */
+PWA_API pwa_status pwa_nll_grad_incoherent(pwa_handle* h, const float* A, int K, int H, int64_t n, int64_t ld,
+                                           const float* V, int P, const double* Psi, double n_factor,
+                                           double* nll, double* grad, void* stream);
 
 /* Bound C >= max over the flat phase space of I(Omega) = |sum_a V_a A_a(Omega)|^2 (Eq. 1)
  * for m in [m_lo, m_hi], used as the accept-reject envelope of pwa_generate.  HOST function

@@ -412,6 +412,33 @@ pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n, int64_t
     return nll_common(h, A, K, n, ld, V, P, Psi, n_factor, nll, grad, stream);
 }
 
+pwa_status pwa_nll_grad_incoherent(pwa_handle* h, const float* A, int K, int H, int64_t n, int64_t ld,
+                                   const float* V, int P, const double* Psi, double n_factor, double* nll,
+                                   double* grad, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (H < 1 || H > PWA_MAX_STATES) return fail(h, PWA_ERR_INVALID_ARG, "H = %d outside [1, %d]", H, PWA_MAX_STATES);
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    if (P < 1 || P > (1 << 24)) return fail(h, PWA_ERR_INVALID_ARG, "P = %d outside [1, 2^24]", P);
+    if ((n > 0 && !A) || !V || !Psi || !nll)
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array argument (A, V, Psi and nll are required)");
+    if (n > 0 && !aligned16(A)) return fail(h, PWA_ERR_INVALID_ARG, "A is not 16-byte aligned");
+    if (!aligned16(Psi)) return fail(h, PWA_ERR_INVALID_ARG, "Psi is not 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) != 0) return fail(h, PWA_ERR_INVALID_ARG, "V is not 8-byte aligned");
+    if (!std::isfinite(n_factor)) return fail(h, PWA_ERR_INVALID_ARG, "n_factor is not finite");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::nll_workspace(K, n, 1, h->sm_count), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_nll_incoherent(reinterpret_cast<const float2*>(A), K, H, n, ld,
+                                               reinterpret_cast<const float2*>(V), P,
+                                               reinterpret_cast<const double2*>(Psi), n_factor, nll, grad, h->ws,
+                                               h->counters, h->status, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "incoherent nll launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
 double pwa_envelope(const pwa_wave* waves, int K, const float* V, double m_lo, double m_hi, int n_intervals) {
     if (!waves || !V || K < 1 || K > PWA_MAX_WAVES || !(m_hi > m_lo) || n_intervals < 1) return -1.0;
     double best = 0.0;

@@ -268,6 +268,12 @@ inline void batched_geometry(int64_t n, int P, int PB, int E, int sm_count, int*
     *nchunk = (int)(nc < 1 ? 1 : nc);
 }
 
+// -lnL (+ gradient if grad) with the intensity summed incoherently over H states, A [K][H][ld];
+// one fused single-set launch per parameter set.
+cudaError_t launch_nll_incoherent(const float2* A, int K, int H, int64_t n, int64_t ld, const float2* V, int P,
+                                  const double2* Psi, double nfac, double* nll, double* grad, void* ws,
+                                  unsigned* counter, int* status, int sm_count, cudaStream_t st);
+
 // The autotuned batched tile shape for (K, n, P), or -1 before the first evaluation of that size.
 int batched_shape(int K, int64_t n, int P);
 

@@ -81,6 +81,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.pwa_nll_grad.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int, _vp,
                                      ctypes.c_double, _vp, _vp, _vp]
         lib.pwa_nll_grad.restype = S
+        lib.pwa_nll_grad_incoherent.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int,
+                                                _vp, ctypes.c_double, _vp, _vp, _vp]
+        lib.pwa_nll_grad_incoherent.restype = S
         _register_optional(lib)
         _lib = lib
         return lib
@@ -255,6 +258,21 @@ class Handle:
         P = V.shape[0]
         self._chk(self.lib.pwa_nll(self.h, _ptr(A), K, int(n), int(ld), _ptr(V), P, _ptr(Psi), float(n_factor),
                                    _ptr(nll), _stream_ptr(stream)))
+
+    def pwa_nll_grad_incoherent(self, A, n, V, Psi, n_factor, nll, grad=None, stream=None):
+        """A complex64 [K][H][ld] (intensity summed over the H states), V complex64 [P][K], Psi
+        complex128 [K][K] (summed over the states); nll float64 [P], grad float64 [P][2K] or None."""
+        _check_cuda(A, "A", torch.complex64)
+        _check_cuda(V, "V", torch.complex64)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(nll, "nll", torch.float64)
+        if grad is not None:
+            _check_cuda(grad, "grad", torch.float64)
+        K, H, ld = A.shape
+        P = V.shape[0]
+        self._chk(self.lib.pwa_nll_grad_incoherent(self.h, _ptr(A), K, H, int(n), int(ld), _ptr(V), P, _ptr(Psi),
+                                                   float(n_factor), _ptr(nll),
+                                                   _ptr(grad) if grad is not None else None, _stream_ptr(stream)))
 
     def pwa_nll_grad(self, A, n, V, Psi, n_factor, nll, grad, stream=None):
         """A complex64 [K][ld], V complex64 [P][K], Psi complex128 [K][K];

@@ -198,6 +198,46 @@ def test_nll_grad_batched_tensor_core_shape(h, K, P, n, monkeypatch):
     assert h.pwa_batched_shape(K, n, P) == 4
 
 
+def _incoherent_problem(K, H, n, n_mc, seed):
+    # state h: the amplitude model of a wave set of its own (J, lambda, M, Gamma drawn per state),
+    # on the same events: A [K][H][n] and the MC normalisation summed over the states
+    kin = inputs.kinematics(n, seed, 4)
+    kin_mc = inputs.kinematics(n_mc, seed, 5)
+    A = np.empty((K, H, n), dtype=np.complex64)
+    A_mc = np.empty((K, H, n_mc), dtype=np.complex64)
+    for st in range(H):
+        ws = inputs.wave_set_spread(K, seed + 17 * st)
+        A[:, st, :] = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin)
+        A_mc[:, st, :] = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc)
+    return A, oracle.normint_incoherent(A_mc, n_gen=float(n_mc))
+
+
+@pytest.mark.parametrize("K,H,n,P", [(4, 2, 3001, 1), (13, 3, 9_999, 3), (16, 2, 20_000, 2), (32, 4, 5001, 1),
+                                     (7, 1, 1, 1), (64, 2, 2001, 1)])
+def test_nll_grad_incoherent(h, K, H, n, P):
+    A, Psi = _incoherent_problem(K, H, n, max(2 * n, 1000), SEED + 1100 + K)
+    V = inputs.starts(P, K, SEED + 1200 + K)
+    ld = n + 1 if n % 2 else n + 2
+    Ap = np.full((K, H, ld), np.complex64(np.nan), dtype=np.complex64)  # padding never read
+    Ap[:, :, :n] = A
+    nll = torch.zeros(P, dtype=torch.float64, device="cuda")
+    g = torch.zeros(P, 2 * K, dtype=torch.float64, device="cuda")
+    h.pwa_nll_grad_incoherent(dev(Ap), n, dev(V), dev(Psi), float(n), nll, g)
+    nll2 = torch.zeros(P, dtype=torch.float64, device="cuda")
+    h.pwa_nll_grad_incoherent(dev(Ap), n, dev(V), dev(Psi), float(n), nll2)
+    torch.cuda.synchronize()
+    f_ref, g_ref, cf, cg, bad = oracle.nll_grad_incoherent(A, V, Psi, n_factor=float(n), with_cond=True)
+    assert bad == 0
+    f_gpu, g_gpu = nll.cpu().numpy(), g.cpu().numpy()
+    assert np.all(np.abs(f_gpu - f_ref) / cf <= 1e-5), (np.abs(f_gpu - f_ref) / cf).max()
+    assert np.all(np.abs(g_gpu - g_ref) / np.repeat(cg, 2, axis=1) <= 1e-4)
+    assert np.array_equal(nll2.cpu().numpy(), f_gpu)  # the pass without the gradient: the same bits
+    if H == 1:
+        # one state: the coherent kernels' arithmetic on the same events, within the tolerance
+        f1, g1 = gpu_nll_grad(h, padded(A[:, 0, :], ld), n, V, Psi)
+        assert np.all(np.abs(f1 - f_gpu) / cf <= 2e-5)
+
+
 def test_batched_equals_separate_sets(h):
     # per-set independence: P sets in one launch vs each set alone (within tolerance), and
     # permuting the sets permutes the outputs exactly
