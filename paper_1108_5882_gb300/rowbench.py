@@ -89,7 +89,7 @@ def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--rows", default="a1,a2,a3,a4,a5,a7,a8,a9")
+    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a8,a9")
     ap.add_argument("--json", default=None)
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and one timed launch per kernel, no peak microbenchmark and 64 toys "
@@ -149,6 +149,23 @@ def main():
             add("a3", f"-lnL+grad one set (stream, a5+a6 fused), K={K}, N={N:.0e}", sec, nbytes=N * K * 8,
                 flops=N * (16 * K + 12.0))
             del A, kin
+    if "a3i" in rows:
+        # incoherent sum over H = 2 states (two wave sets on the same events), K = 16, N = 1e6
+        K, N, H = 16, 1_000_000, 2
+        kin = torch.from_numpy(inputs.kinematics(N, seed, 4)).cuda()
+        A = torch.empty((K, H, N), dtype=torch.complex64, device="cuda")
+        for st in range(H):
+            A_st = torch.empty((K, N), dtype=torch.complex64, device="cuda")
+            h.pwa_amplitudes(pwa.waves_from(inputs.wave_set_spread(K, seed + 17 * st)), kin, N, A_st)
+            A[:, st, :] = A_st
+        V = torch.from_numpy(inputs.production_amplitudes(K, seed)[None, :]).cuda()
+        Psi = torch.eye(K, dtype=torch.complex128, device="cuda")
+        nll = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty((1, 2 * K), dtype=torch.float64, device="cuda")
+        sec = T(lambda: h.pwa_nll_grad_incoherent(A, N, V, Psi, float(N), nll, g), R)
+        add("a3i", f"incoherent -lnL+grad (H={H} states), K={K}, N={N:.0e}", sec, nbytes=N * K * H * 8,
+            flops=N * H * (16 * K + 4.0))
+        del A, kin
     if "a5" in rows:
         # floating shape: data 1e6 + MC 5e6 events, 4 floating parameters (2 masses, 2 widths)
         K, N, F = 16, 1_000_000, 4
