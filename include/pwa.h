@@ -136,6 +136,16 @@ PWA_API pwa_status pwa_amplitudes(pwa_handle* h, const pwa_wave* waves, int K, c
 PWA_API pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t n_mc, int64_t ld,
                        const float* w, double n_gen, double* Psi, void* stream);
 
+/* The same integral straight from the MC kinematics, with the amplitudes never stored: each
+ * tile of events has its amplitudes computed in on-chip memory with the arithmetic of
+ * pwa_amplitudes (equal to within FP32 rounding), then accumulated as pwa_normint accumulates
+ * them: pwa_amplitudes followed by pwa_normint, without the K x n_mc amplitude array in HBM.
+ *   waves  host array [K]; kin float [3][ld] (m_KK, cos theta, phi), 16-byte aligned
+ *   w, n_gen, Psi as in pwa_normint. */
+PWA_API pwa_status pwa_normint_from_kinematics(pwa_handle* h, const pwa_wave* waves, int K, const float* kin,
+                                               int64_t n_mc, int64_t ld, const float* w, double n_gen,
+                                               double* Psi, void* stream);
+
 /* Extended negative log-likelihood (Sec. 2, Eq. 3 and footnote 2) for P parameter sets:
  *   nll[p] = -sum_{i<n} ln |sum_a V[p][a] A_a(i)|^2 + n_factor * sum_ab V[p][a] conj(V[p][b]) Psi_ab
  *   A      complex float [K][ld]    data amplitudes

@@ -401,6 +401,32 @@ pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t n_mc, in
     return PWA_OK;
 }
 
+pwa_status pwa_normint_from_kinematics(pwa_handle* h, const pwa_wave* waves, int K, const float* kin, int64_t n_mc,
+                                       int64_t ld, const float* w, double n_gen, double* Psi, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n_mc, ld);
+    if (st != PWA_OK) return st;
+    if (!waves) return fail(h, PWA_ERR_INVALID_ARG, "waves is NULL");
+    if ((n_mc > 0 && !kin) || !Psi) return fail(h, PWA_ERR_INVALID_ARG, "NULL kin or Psi");
+    if (kin && !aligned16(kin)) return fail(h, PWA_ERR_INVALID_ARG, "kin is not 16-byte aligned");
+    if (!aligned16(Psi)) return fail(h, PWA_ERR_INVALID_ARG, "Psi is not 16-byte aligned");
+    if (w && (reinterpret_cast<uintptr_t>(w) & 3u)) return fail(h, PWA_ERR_INVALID_ARG, "w is not 4-byte aligned");
+    if (!(n_gen > 0.0) || !std::isfinite(n_gen))
+        return fail(h, PWA_ERR_INVALID_ARG, "n_gen must be finite and > 0");
+    pwa::WaveTable wt;
+    st = fill_waves(h, waves, K, &wt);
+    if (st != PWA_OK) return st;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::normint_workspace(K, h->sm_count), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_normint_kin(wt, kin, K, n_mc, ld, w, n_gen, reinterpret_cast<double2*>(Psi), h->ws,
+                                            h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "normint (kinematics) launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
 pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V, int P,
                    const double* Psi, double n_factor, double* nll, void* stream) {
     return nll_common(h, A, K, n, ld, V, P, Psi, n_factor, nll, nullptr, stream);

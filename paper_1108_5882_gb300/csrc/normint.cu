@@ -15,7 +15,7 @@
 // per-thread double-single accumulator held in shared memory (v-major, conflict-free); the
 // phases and then the blocks are combined in a fixed order, and the final division and the
 // Hermitian completion are done in FP64.
-#include "pwa_internal.cuh"
+#include "amp_model.cuh"
 
 namespace pwa {
 
@@ -27,11 +27,58 @@ constexpr int NI_E = 256;  // events per tile
 template <int KMAX>
 __host__ __device__ constexpr int ni_rs() { return KMAX + 2; }
 
+__constant__ float c_ni_inv_int[AMP_JMAX + 1] = {1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9};
+
+// The amplitudes of one event, A_a = BW_a(m) P_J(cos theta) exp(i lambda phi) for a < K, into
+// row[a]: the arithmetic of the amplitude kernel (waves visited group by group, the Legendre
+// recurrence carried across groups), for one event per thread.
+__device__ __forceinline__ void event_amplitudes(const WaveTable& wt, float m, float ct, float ph, bool in,
+                                                 float2* row) {
+    float s1, c1;
+    sincosf(ph, &s1, &c1);
+    float pcur = 1.f, pprev = 0.f;  // P_jc, P_{jc-1}
+    int jc = 0, s = 0;
+    for (int g = 0; g < wt.ng; ++g) {
+        const int end = wt.gend[g];
+        const int a0 = wt.gord[s];
+        const int J = wt.J[a0], lam = wt.lam[a0];
+        const int al = lam < 0 ? -lam : lam;
+        for (; jc < J; ++jc) {
+            const float c2 = 2.f * jc + 1.f, cj = (float)jc, rj = c_ni_inv_int[jc];
+            const float pn = (c2 * ct * pcur - cj * pprev) * rj;
+            pprev = pcur;
+            pcur = pn;
+        }
+        float er = 1.f, ei = 0.f;
+        for (int j = 0; j < al; ++j) {
+            const float tr = er * c1 - ei * s1;
+            ei = er * s1 + ei * c1;
+            er = tr;
+        }
+        if (lam < 0) ei = -ei;
+        const float2 ang = make_float2(pcur * er, pcur * ei);
+        for (; s < end; ++s) {
+            const int a = wt.gord[s];
+            const float Mh = wt.Mhi[a], Ml = wt.Mlo[a], MW = wt.MW[a];
+            const float dr = ((Mh - m) + Ml) * ((Mh + m) + Ml);
+            const float inv = __fdividef(1.f, fmaf(dr, dr, MW * MW));
+            const float2 id = make_float2(dr * inv, MW * inv);
+            const float2 bw = make_float2(MW * id.x, MW * id.y);
+            row[a] = in ? cmul(bw, ang) : make_float2(0.f, 0.f);
+        }
+    }
+}
+
 // block partial layout: part[block][KMAX*KMAX] of complex ff = 4 floats (re.hi, re.lo, im.hi, im.lo)
-template <int KMAX, bool WEIGHTED>
+// FROM_KIN: the tile's amplitudes are computed from the kinematics kin [3][ld] (thread t: event
+// e0 + t, all waves) instead of read from A: Psi straight from the MC events, with no amplitude
+// array written or read.
+template <int KMAX, bool WEIGHTED, bool FROM_KIN = false>
 __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restrict__ A, int K, int64_t n,
                                                          int64_t ld, const float* __restrict__ w,
-                                                         int64_t ev_per_block, float4* __restrict__ part) {
+                                                         int64_t ev_per_block, float4* __restrict__ part,
+                                                         const float* __restrict__ kin = nullptr,
+                                                         WaveTable wt = WaveTable{}) {
     constexpr int KB = KMAX / 4;                 // 4x4 tile rows
     constexpr int NT = KB * (KB + 1) / 2;        // upper-triangle tiles
     constexpr int NPH = PWA_THREADS / NT > 0 ? PWA_THREADS / NT : 1;  // event phases
@@ -57,6 +104,8 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
         tj = row + r;
     }
     for (int v = 0; v < 64; ++v) sacc[v * PWA_THREADS + tid] = 0.f;
+    if (FROM_KIN)  // the padding waves K..KMAX-1 of the computed tiles
+        for (int a = K; a < KMAX; ++a) sA[tid * RS + a] = make_float2(0.f, 0.f);
 
     const int64_t e_begin = (int64_t)blockIdx.x * ev_per_block;
     int64_t e_end = e_begin + ev_per_block;
@@ -65,12 +114,20 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     // register prefetch of the next tile: element idx = tid + 256 j -> row idx / NI_E, event idx % NI_E
     float2 pre[LD2];
     float prew = 0.f;
+    float km = 2.f, kct = 0.f, kph = 0.f;  // FROM_KIN: the kinematics of event e0 + tid
     auto load_tile = [&](int64_t e0) {
+        if (FROM_KIN) {
+            const bool in = e0 + tid < e_end;
+            km = in ? __ldg(kin + e0 + tid) : 2.f;
+            kct = in ? __ldg(kin + ld + e0 + tid) : 0.f;
+            kph = in ? __ldg(kin + 2 * ld + e0 + tid) : 0.f;
+        } else {
 #pragma unroll
-        for (int j = 0; j < LD2; ++j) {
-            const int idx = tid + PWA_THREADS * j;
-            const int a = idx / NI_E, e = idx % NI_E;
-            pre[j] = (a < K && e0 + e < e_end) ? __ldg(A + a * ld + e0 + e) : make_float2(0.f, 0.f);
+            for (int j = 0; j < LD2; ++j) {
+                const int idx = tid + PWA_THREADS * j;
+                const int a = idx / NI_E, e = idx % NI_E;
+                pre[j] = (a < K && e0 + e < e_end) ? __ldg(A + a * ld + e0 + e) : make_float2(0.f, 0.f);
+            }
         }
         if (WEIGHTED) prew = (e0 + tid < e_end) ? __ldg(w + e0 + tid) : 0.f;  // NI_E == PWA_THREADS
     };
@@ -83,10 +140,14 @@ __global__ void __launch_bounds__(PWA_THREADS) k_normint(const float2* __restric
     if (e_begin < e_end) load_tile(e_begin);
     for (int64_t e0 = e_begin; e0 < e_end; e0 += NI_E) {
         __syncthreads();  // previous tile consumed
+        if (FROM_KIN) {
+            event_amplitudes(wt, km, kct, kph, e0 + tid < e_end, sA + tid * RS);  // waves K.. stay zero
+        } else {
 #pragma unroll
-        for (int j = 0; j < LD2; ++j) {
-            const int idx = tid + PWA_THREADS * j;
-            sA[(idx % NI_E) * RS + idx / NI_E] = pre[j];
+            for (int j = 0; j < LD2; ++j) {
+                const int idx = tid + PWA_THREADS * j;
+                sA[(idx % NI_E) * RS + idx / NI_E] = pre[j];
+            }
         }
         if (WEIGHTED) sw[tid] = prew;
         __syncthreads();
@@ -208,12 +269,14 @@ size_t ni_smem() {
 
 template <int KMAX>
 cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float* w, double n_gen,
-                      double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+                      double2* Psi, void* ws, int sm_count, cudaStream_t st, const float* kin = nullptr,
+                      const WaveTable* wt = nullptr) {
     const size_t smem = ni_smem<KMAX>();
-    auto kw = k_normint<KMAX, true>;
-    auto ku = k_normint<KMAX, false>;
+    auto kw = kin ? k_normint<KMAX, true, true> : k_normint<KMAX, true, false>;
+    auto ku = kin ? k_normint<KMAX, false, true> : k_normint<KMAX, false, false>;
     cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const WaveTable wt0 = wt ? *wt : WaveTable{};
     int64_t tiles = (n + NI_E - 1) / NI_E;
     int64_t nb = (int64_t)sm_count * 2;
     if (nb > tiles) nb = tiles;
@@ -224,9 +287,9 @@ cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float
     if (nb < 1) nb = 1;
     float4* part = reinterpret_cast<float4*>(ws);
     if (w)
-        kw<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, w, ev_per_block, part);
+        kw<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, w, ev_per_block, part, kin, wt0);
     else
-        ku<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, nullptr, ev_per_block, part);
+        ku<<<(unsigned)nb, PWA_THREADS, smem, st>>>(A, K, n, ld, nullptr, ev_per_block, part, kin, wt0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int fin_blocks = (K * K * 32 + PWA_THREADS - 1) / PWA_THREADS;  // one warp per entry
@@ -239,6 +302,16 @@ cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float
 size_t normint_workspace(int K, int sm_count) {
     int KMAX = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64;
     return sizeof(float4) * (size_t)KMAX * KMAX * (size_t)sm_count * 2;
+}
+
+cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int64_t n, int64_t ld, const float* w,
+                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+    if (K <= 4) return ni_launch<4>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
+    if (K <= 8) return ni_launch<8>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
+    if (K <= 16) return ni_launch<16>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
+    if (K <= 32) return ni_launch<32>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
+    if (K <= 48) return ni_launch<48>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
+    return ni_launch<64>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
 }
 
 cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const float* w,

@@ -234,6 +234,11 @@ cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const doub
 cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
                             int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
                             uint16_t* Cb, int64_t ldc, int sm_count, cudaStream_t st);
+// Psi straight from MC kinematics kin [3][ld]: the amplitudes of each tile of events are computed
+// in shared memory (with the arithmetic of pwa_amplitudes) and consumed there.
+cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int64_t n, int64_t ld, const float* w,
+                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st);
+
 // The same product on the tensor cores (tcgen05 kind::f16) for a BF16 B; an FP32 A is split into
 // three BF16 parts.  A timeout of its bounded wait sets status bit 1.
 cudaError_t launch_mlp_gemm_tc(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak,

@@ -75,6 +75,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.pwa_amplitudes.restype = S
         lib.pwa_normint.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_double, _vp, _vp]
         lib.pwa_normint.restype = S
+        lib.pwa_normint_from_kinematics.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, _i64, _i64, _vp,
+                                                    ctypes.c_double, _vp, _vp]
+        lib.pwa_normint_from_kinematics.restype = S
         lib.pwa_nll.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int, _vp, ctypes.c_double, _vp,
                                 _vp]
         lib.pwa_nll.restype = S
@@ -248,6 +251,18 @@ class Handle:
         n_gen = float(n_mc if n_gen is None else n_gen)
         self._chk(self.lib.pwa_normint(self.h, _ptr(A_mc), K, int(n_mc), int(ld), _ptr(w), n_gen, _ptr(Psi),
                                        _stream_ptr(stream)))
+
+    def pwa_normint_from_kinematics(self, waves, kin, n_mc, Psi, w=None, n_gen=None, stream=None):
+        """Psi complex128 [K][K] from MC kinematics float32 [3][ld] (amplitudes computed on chip)."""
+        K = len(waves)
+        arr = (pwa_wave * K)(*[pwa_wave(int(j), int(l), float(m), float(wd)) for (j, l, m, wd) in waves])
+        _check_cuda(kin, "kin", torch.float32)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(w, "w", torch.float32)
+        ld = kin.shape[1]
+        n_gen = float(n_mc if n_gen is None else n_gen)
+        self._chk(self.lib.pwa_normint_from_kinematics(self.h, arr, K, _ptr(kin), int(n_mc), int(ld), _ptr(w), n_gen,
+                                                       _ptr(Psi), _stream_ptr(stream)))
 
     def pwa_nll(self, A, n, V, Psi, n_factor, nll, stream=None):
         _check_cuda(A, "A", torch.complex64)

@@ -198,6 +198,35 @@ def test_nll_grad_batched_tensor_core_shape(h, K, P, n, monkeypatch):
     assert h.pwa_batched_shape(K, n, P) == 4
 
 
+@pytest.mark.parametrize("K,n,weighted", [(4, 3001, False), (16, 100_003, True), (13, 257, False), (48, 9_999, True),
+                                        (7, 1, False)])
+def test_normint_from_kinematics(h, K, n, weighted):
+    # Psi straight from the kinematics vs the oracle's Psi of the oracle's amplitudes, and vs
+    # pwa_amplitudes + pwa_normint, within the Psi tolerance widened by the amplitudes' bound
+    from paper_1108_5882_gb300 import pwa
+    ws = inputs.wave_set_plain(SEED + 3) if K == 4 else inputs.wave_set_spread(K, SEED + 1300 + K)
+    ld = n + 1 if n % 2 else n + 2
+    kin = padded(inputs.kinematics(n, SEED + 1400 + K, 5), ld)
+    w = np.random.default_rng(K).uniform(0, 2, size=n).astype(np.float32) if weighted else None
+    Psi_k = torch.zeros((K, K), dtype=torch.complex128, device="cuda")
+    h.pwa_normint_from_kinematics(pwa.waves_from(ws), dev(kin), n, Psi_k, w=None if w is None else dev(w),
+                                  n_gen=1.5 * n)
+    A = torch.zeros((K, ld), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(pwa.waves_from(ws), dev(kin), n, A)
+    Psi_a = torch.zeros((K, K), dtype=torch.complex128, device="cuda")
+    h.pwa_normint(A, n, Psi_a, w=None if w is None else dev(w), n_gen=1.5 * n)
+    A_ref = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin[:, :n]).astype(np.complex64)
+    ref = oracle.normint(A_ref, w=w, n_gen=1.5 * n)
+    d = np.sqrt(np.outer(np.abs(np.diag(ref)), np.abs(np.diag(ref))))
+    # the amplitudes' own bound, |A_gpu - A_ref| <= 4e-6, carried through the sum:
+    # |dPsi_ab| <= 4e-6 (m_a + m_b) with m_a = (1/n_gen) sum_j w_j |A_a(j)|
+    wv = np.ones(n) if w is None else w.astype(np.float64)
+    m = (np.abs(A_ref) * wv).sum(axis=1) / (1.5 * n)
+    tol = 1e-5 * d + 4e-6 * (m[:, None] + m[None, :]) + 1e-30
+    assert np.all(np.abs(Psi_k.cpu().numpy() - ref) <= tol)
+    assert np.all(np.abs(Psi_k.cpu().numpy() - Psi_a.cpu().numpy()) <= tol)  # the unfused path
+
+
 def _incoherent_problem(K, H, n, n_mc, seed):
     # state h: the amplitude model of a wave set of its own (J, lambda, M, Gamma drawn per state),
     # on the same events: A [K][H][n] and the MC normalisation summed over the states
