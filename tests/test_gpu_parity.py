@@ -367,6 +367,11 @@ def test_invalid_arguments_are_rejected(h):
         h.pwa_normint(A, 10, Psi, n_gen=0.0)
     with pytest.raises(pwa.PWAError, match="mass"):
         h.pwa_amplitudes([(0, 0, -1.0, 0.1)] * 4, torch.zeros((3, 10), device="cuda"), 10, A)
+    A5 = torch.zeros((4, 5, 10), dtype=torch.complex64, device="cuda")  # H = 5 states > PWA_MAX_STATES
+    with pytest.raises(pwa.PWAError, match="H = 5"):
+        h.pwa_nll_grad_incoherent(A5, 10, V, Psi, 1.0, nll)
+    with pytest.raises(pwa.PWAError, match="n_gen"):
+        h.pwa_normint_from_kinematics([(0, 0, 1.5, 0.1)] * 4, torch.zeros((3, 10), device="cuda"), 10, Psi, n_gen=0.0)
 
 
 # ------------------------------------------------------------------- full sizes ---------
