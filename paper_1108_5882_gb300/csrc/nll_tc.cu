@@ -23,12 +23,14 @@
 //     D2[p][KMAX + a] = sum_e Im(conj(A_ea) w_ep).
 //
 // Shared memory holds V' (hi, lo), A' and X (hi, lo; both layouts are written from registers,
-// since a transposed TF32 operand is not available); tensor memory holds D1, Y (hi, lo) and D2.
-// D2 accumulates in FP32 over a window of WINDOW tiles (256 events) and is then added to the
-// block's double-single partials (the same [chunk][P][1 + 2K] partials as the other tile
-// shapes, so one finalisation serves all).  Sum ln I: FP32 per tile, double-single across tiles.
-// Every wait on the tensor cores is bounded; a timeout sets status bit 1 and the block's sets'
-// bad flags, waits (bounded) for its last MMA group and frees its tensor memory.
+// since a transposed TF32 operand is not available) and the low words of the G accumulators;
+// tensor memory holds D1 (Y hi overwrites it), Y lo, D2 and the high words of the G
+// accumulators.  D2 accumulates in FP32 over a window of WINDOW tiles (256 events) and is then
+// added to the double-single G accumulators; at the end they are written to the block's
+// [chunk][P][1 + 2K] partials, the layout of the other tile shapes, so one finalisation serves
+// all.  Sum ln I: FP32 per tile and thread, double-single across tiles.  Every wait on the
+// tensor cores is bounded; a timeout sets status bit 1 and the block's sets' bad flags, waits
+// (bounded) for the MMAs in flight and frees the tensor memory.
 #include "nll_common.cuh"
 #include "tc.cuh"
 
