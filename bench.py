@@ -162,6 +162,12 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------- ranks
+def dist_backend():
+    """nccl on GPU ranks; gloo for the host-side tests of the rank logic (or PWA_DIST_BACKEND)."""
+    import torch
+    return os.environ.get("PWA_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+
+
 def dist_init(ngpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -169,8 +175,10 @@ def dist_init(ngpus):
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        backend = dist_backend()
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -185,9 +193,15 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of weak-scaling replicas: each of the `world` ranks processed
+    units_per_rank units, and `seconds` is the slowest rank's time (max over ranks)."""
+    return world * units_per_rank / seconds
 
 
 # ----------------------------------------------------------------------------- workload
@@ -290,7 +304,7 @@ def run_ours(args, world, rank, local):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = tot_ms / args.steps
-    value = world * N * P * args.steps / (tot_ms * 1e-3)
+    value = job_rate(N * P * args.steps, world, tot_ms * 1e-3)
     kernel_ms = sum(step_ms) / len(step_ms)  # one launch of the streaming kernel per step
     ok = h.pwa_sync_status()
 
@@ -402,7 +416,7 @@ def run_ours(args, world, rank, local):
                                "one -lnL+gradient evaluation per step, amplitudes and Psi precomputed",
                    "K": K, "N_data": N, "N_MC": wl["NMC"], "P": P, "l2": "flushed before every step (512 MiB read)",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": world * N * P / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(N * P, world, e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "h2d_ms_per_step": h2d_ms,
                 "what": "pinned H2D of data+MC kinematics and V (copy stream, double-buffered: step t+1's copies "
                         "overlap step t's kernels), amplitudes(data), Psi from the MC kinematics (MC amplitudes computed on chip), "
