@@ -396,7 +396,7 @@ def run_ours(args, world, rank, local):
                 bf16 = float(json.load(fh)["bf16_tflops"])
             peak = bf16 * (1.1 / 2.25) / 3.0
             roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": measured_traffic(f"k_nll_tc_{args.workload}"),
                         "kernel": "k_nll_tc (tcgen05 3xTF32) + k_nll_finalize (one step)",
                         "flops_per_launch": flops, "kernel_us": kernel_ms * 1e3,
                         "peak_kind": "of measured: bf16 burst x 1.1/2.25 (TF32 dense) / 3 (FP32 emulation)",
