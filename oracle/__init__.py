@@ -64,6 +64,8 @@ def _load():
             lib.orc_nll_grad_incoherent.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _fp, _i64, ctypes.c_int, _dp,
                                                     _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
             lib.orc_nll_grad_incoherent.restype = ctypes.c_int
+            lib.orc_hessian.argtypes = [ctypes.c_int, _i64, _fp, _i64, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            lib.orc_hessian.restype = ctypes.c_int
             lib.orc_nll_double_sum.argtypes = [ctypes.c_int, _i64, _fp, _i64, _dp, _dp,
                                                ctypes.c_double]
             lib.orc_nll_double_sum.restype = ctypes.c_double
@@ -191,6 +193,25 @@ def nll_grad_incoherent(A, V, Psi, n_factor=None, with_cond: bool = False):
     if with_cond:
         return nll, grad, cf, cg, bad
     return nll, grad
+
+
+def hessian(A, V, Psi, n_factor=None, exact=False, with_cond: bool = False):
+    """Second derivatives of -lnL in theta = (Re V_0, Im V_0, ...) for one set V [K]: the Fumili
+    outer-product form sum_i r_i r_i^T (exact=False) or the exact Hessian.  [2K][2K] float64."""
+    lib = _load()
+    K, n = A.shape
+    Af = _c64_as_f32(A)
+    V = np.ascontiguousarray(np.asarray(V).reshape(K), dtype=np.complex128)
+    Psi = np.ascontiguousarray(Psi, dtype=np.complex128)
+    if n_factor is None:
+        n_factor = float(n)
+    H = np.zeros((2 * K, 2 * K), dtype=np.float64)
+    cond = np.zeros((2 * K, 2 * K), dtype=np.float64)
+    bad = lib.orc_hessian(K, n, _ptr(Af, _fp), n, _ptr(V, _dp), _ptr(Psi, _dp), float(n_factor), 1 if exact else 0,
+                          _ptr(H, _dp), _ptr(cond, _dp))
+    if with_cond:
+        return H, cond, bad
+    return H
 
 
 def normint_incoherent(A, n_gen=None, w=None):

@@ -16,6 +16,8 @@
  *   - the same with the intensity summed incoherently over unobserved states h,
  *     I = sum_h |sum_a V_a A_{a,h}|^2 (Eq. 1 summed over h; the paper's own example, J/psi ->
  *     gamma X, has such a state: the photon helicity)
+ *   - the Hessian of -lnL in the real coordinates of V: the Fumili outer-product form and the
+ *     exact form (Sec. 4, the fitters)
  *   - the double-sum form of Eq. 3 in long double (used only to pin the O(K) form above)
  *   - the amplitude model A_a = BW_a(m) P_J(cos th) exp(i lambda phi) and its derivatives
  *     in the resonance mass and width (the paper gives no amplitude formula; the reading is
@@ -290,6 +292,87 @@ int orc_nll_grad_incoherent(int K, int H, int64_t n, const float* A, int64_t ld,
     }
     free(Ai); free(u); free(su); free(gre); free(gim); free(gsc);
     return bad_sets;
+}
+
+/* Second derivatives of f = -sum_i ln I_i + n_factor S in the real coordinates
+ * theta = (Re V_0, Im V_0, Re V_1, ...) of one parameter set, for the Fumili / Gauss-Newton
+ * step the paper's fitters take (Sec. 4: Minuit and Fumili):
+ *   r_i = grad_theta ln I_i, r_i[2c] = 2 Re(conj(A_c) u_i) / I_i, r_i[2c+1] = 2 Im(conj(A_c) u_i) / I_i
+ *   mode 0 (Fumili, the outer-product form):  H = sum_i r_i r_i^T
+ *   mode 1 (exact):  H = sum_i (r_i r_i^T - E(A_i A_i^H) / I_i) + n_factor E(Psi)
+ * where E(C) embeds a Hermitian K x K matrix as the 2K x 2K real matrix of the quadratic form
+ * theta -> sum_ab V_a conj(V_b) C_ab: E[2a][2b] = E[2a+1][2b+1] = 2 Re C_ab, E[2a][2b+1] =
+ * 2 Im C_ab, E[2a+1][2b] = -2 Im C_ab (so that d2 I_i = E(A_i A_i^H) and d2 S = E(Psi)).
+ * H is row-major [2K][2K].  cond [2K][2K] (may be NULL): sum_i |r_ix| |r_iy| (+ |E(A A^H)|/I and
+ * n |E(Psi)| for mode 1), the scale the parity tolerance is taken against.  Returns 1 if some
+ * I_i is not positive and finite (H is then left zero), else 0. */
+int orc_hessian(int K, int64_t n, const float* A, int64_t ld, const double* Vd, const double* Psid,
+                double n_factor, int mode, double* H, double* cond) {
+    const cplx* V = (const cplx*)Vd;
+    const cplx* Psi = (const cplx*)Psid;
+    const int D = 2 * K;
+    nsum* acc = (nsum*)calloc((size_t)D * D, sizeof(nsum));
+    double* sc = (double*)calloc((size_t)D * D, sizeof(double));
+    cplx* Ai = (cplx*)malloc(sizeof(cplx) * (size_t)K);
+    double* r = (double*)malloc(sizeof(double) * (size_t)D);
+    int bad = 0;
+    for (int64_t i = 0; i < n && !bad; ++i) {
+        cplx u = 0.0;
+        for (int a = 0; a < K; ++a) {
+            Ai[a] = A[2 * ((int64_t)a * ld + i)] + I * A[2 * ((int64_t)a * ld + i) + 1];
+            u += V[a] * Ai[a];
+        }
+        const double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
+        if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; break; }
+        for (int c = 0; c < K; ++c) {
+            const cplx z = conj(Ai[c]) * u;
+            r[2 * c] = 2.0 * creal(z) / Ii;
+            r[2 * c + 1] = 2.0 * cimag(z) / Ii;
+        }
+        for (int x = 0; x < D; ++x)
+            for (int y = 0; y < D; ++y) {
+                nsum_add(&acc[x * D + y], r[x] * r[y]);
+                sc[x * D + y] += fabs(r[x] * r[y]);
+            }
+        if (mode == 1) {
+            for (int a = 0; a < K; ++a)
+                for (int b = 0; b < K; ++b) {
+                    const cplx cab = Ai[a] * conj(Ai[b]) / Ii;
+                    const double re = 2.0 * creal(cab), im = 2.0 * cimag(cab);
+                    nsum_add(&acc[(2 * a) * D + 2 * b], -re);
+                    nsum_add(&acc[(2 * a + 1) * D + 2 * b + 1], -re);
+                    nsum_add(&acc[(2 * a) * D + 2 * b + 1], -im);
+                    nsum_add(&acc[(2 * a + 1) * D + 2 * b], im);
+                    sc[(2 * a) * D + 2 * b] += fabs(re);
+                    sc[(2 * a + 1) * D + 2 * b + 1] += fabs(re);
+                    sc[(2 * a) * D + 2 * b + 1] += fabs(im);
+                    sc[(2 * a + 1) * D + 2 * b] += fabs(im);
+                }
+        }
+    }
+    for (int x = 0; x < D * D; ++x) H[x] = 0.0;
+    if (!bad) {
+        for (int x = 0; x < D * D; ++x) H[x] = nsum_get(&acc[x]);
+        if (mode == 1) {
+            for (int a = 0; a < K; ++a)
+                for (int b = 0; b < K; ++b) {
+                    const double re = 2.0 * n_factor * creal(Psi[a * K + b]);
+                    const double im = 2.0 * n_factor * cimag(Psi[a * K + b]);
+                    H[(2 * a) * D + 2 * b] += re;
+                    H[(2 * a + 1) * D + 2 * b + 1] += re;
+                    H[(2 * a) * D + 2 * b + 1] += im;
+                    H[(2 * a + 1) * D + 2 * b] -= im;
+                    sc[(2 * a) * D + 2 * b] += fabs(re);
+                    sc[(2 * a + 1) * D + 2 * b + 1] += fabs(re);
+                    sc[(2 * a) * D + 2 * b + 1] += fabs(im);
+                    sc[(2 * a + 1) * D + 2 * b] += fabs(im);
+                }
+        }
+    }
+    if (cond)
+        for (int x = 0; x < D * D; ++x) cond[x] = sc[x];
+    free(acc); free(sc); free(Ai); free(r);
+    return bad;
 }
 
 /* Eq. 3 exactly as printed: ln L = sum_i ln( sum_a sum_a' V_a conj(V_a') A_a conj(A_a') )

@@ -620,3 +620,74 @@ def test_incoherent_brute_force_and_global_phase():
         assert abs(g[0, 2 * c + 1] - gc.imag) <= 1e-12 * max(1.0, abs(gc))
     fr, _ = oracle.nll_grad_incoherent(A, (V * np.exp(0.7j))[None, :], Psi, n_factor=2.5)
     assert abs(fr[0] - f[0]) <= 1e-12 * abs(f[0])
+
+
+# ------------------------------------------------------------------ Hessian (Fumili / exact) ---
+
+def _theta(V):
+    return np.stack([V.real, V.imag], axis=-1).reshape(-1)
+
+
+def test_exact_hessian_matches_finite_differences_of_the_gradient():
+    A = _rand_A(3, 900, 81)
+    Psi = oracle.normint(_rand_A(3, 3000, 82))
+    V = _rand_V(3, 83)
+    H = oracle.hessian(A, V, Psi, exact=True)
+    for x in range(6):
+        c, part = divmod(x, 2)
+        h = 1e-6 * max(1.0, abs(V[c]))
+        Vp, Vm = V.copy(), V.copy()
+        Vp[c] += (1j if part else 1.0) * h
+        Vm[c] -= (1j if part else 1.0) * h
+        col = (oracle.nll_grad(A, Vp[None, :], Psi)[1][0] - oracle.nll_grad(A, Vm[None, :], Psi)[1][0]) / (2 * h)
+        assert np.max(np.abs(col - H[:, x])) <= 2e-5 * max(1.0, np.max(np.abs(H)))
+    assert np.allclose(H, H.T, rtol=1e-12, atol=1e-9 * np.max(np.abs(H)))
+
+
+def test_fumili_hessian_homogeneity_and_phase_direction():
+    # r_i . theta = 2 (I is homogeneous of degree 2 in V) and r_i . (i V) = 0 (global phase), so
+    # H_F theta = 2 sum_i r_i = -2 x (data part of the gradient) and H_F (i V) = 0; H_F is PSD
+    A = _rand_A(4, 700, 84)
+    Psi = oracle.normint(_rand_A(4, 2000, 85))
+    V = _rand_V(4, 86)
+    H = oracle.hessian(A, V, Psi, exact=False)
+    _, g_data = oracle.nll_grad(A, V[None, :], np.zeros_like(Psi))
+    th = _theta(V)
+    assert np.max(np.abs(H @ th + 2 * g_data[0])) <= 1e-10 * np.max(np.abs(H @ th))
+    assert np.max(np.abs(H @ _theta(1j * V))) <= 1e-10 * np.max(np.abs(H)) * np.max(np.abs(th))
+    assert np.min(np.linalg.eigvalsh(0.5 * (H + H.T))) >= -1e-9 * np.max(np.abs(H))
+
+
+def test_hessian_brute_force_tiny():
+    K, n = 2, 4
+    A = _rand_A(K, n, 87)
+    Psi = oracle.normint(_rand_A(K, 9, 88))
+    V = _rand_V(K, 89)
+    Ad = A.astype(np.complex128)
+    HF = np.zeros((4, 4))
+    HX = np.zeros((4, 4))
+    for i in range(n):
+        u = sum(V[a] * Ad[a, i] for a in range(K))
+        Ii = abs(u) ** 2
+        r = []
+        for c in range(K):
+            z = np.conj(Ad[c, i]) * u
+            r += [2 * z.real / Ii, 2 * z.imag / Ii]
+        for x in range(4):
+            for y in range(4):
+                HF[x, y] += r[x] * r[y]
+        for a in range(K):
+            for b in range(K):
+                cab = Ad[a, i] * np.conj(Ad[b, i]) / Ii
+                HX[2 * a, 2 * b] -= 2 * cab.real
+                HX[2 * a + 1, 2 * b + 1] -= 2 * cab.real
+                HX[2 * a, 2 * b + 1] -= 2 * cab.imag
+                HX[2 * a + 1, 2 * b] += 2 * cab.imag
+    for a in range(K):
+        for b in range(K):
+            HX[2 * a, 2 * b] += 2 * 3.0 * Psi[a, b].real
+            HX[2 * a + 1, 2 * b + 1] += 2 * 3.0 * Psi[a, b].real
+            HX[2 * a, 2 * b + 1] += 2 * 3.0 * Psi[a, b].imag
+            HX[2 * a + 1, 2 * b] -= 2 * 3.0 * Psi[a, b].imag
+    assert np.allclose(oracle.hessian(A, V, Psi, n_factor=3.0), HF, rtol=1e-12, atol=1e-12)
+    assert np.allclose(oracle.hessian(A, V, Psi, n_factor=3.0, exact=True), HF + HX, rtol=1e-12, atol=1e-12)
