@@ -303,9 +303,12 @@ int orc_nll_grad_incoherent(int K, int H, int64_t n, const float* A, int64_t ld,
  * where E(C) embeds a Hermitian K x K matrix as the 2K x 2K real matrix of the quadratic form
  * theta -> sum_ab V_a conj(V_b) C_ab: E[2a][2b] = E[2a+1][2b+1] = 2 Re C_ab, E[2a][2b+1] =
  * 2 Im C_ab, E[2a+1][2b] = -2 Im C_ab (so that d2 I_i = E(A_i A_i^H) and d2 S = E(Psi)).
- * H is row-major [2K][2K].  cond [2K][2K] (may be NULL): sum_i |r_ix| |r_iy| (+ |E(A A^H)|/I and
- * n |E(Psi)| for mode 1), the scale the parity tolerance is taken against.  Returns 1 if some
- * I_i is not positive and finite (H is then left zero), else 0. */
+ * H is row-major [2K][2K].  cond [2K][2K] (may be NULL): sum_i (|r_ix| |r_iy| (+ |E(A_i A_i^H)| / I_i
+ * for mode 1)) s_i / |u_i| (+ n |E(Psi)|), with s_i = sum_a |V_a| |A_a(i)|: the scale the parity
+ * tolerance is taken against.  As for the gradient, s_i is the forward-error scale of u_i in
+ * single precision: an FP32 evaluation moves u_i by about eps s_i, so each event's terms move
+ * by about their size times eps s_i / |u_i|.  Returns 1 if some I_i is not positive and finite
+ * (H is then left zero), else 0. */
 int orc_hessian(int K, int64_t n, const float* A, int64_t ld, const double* Vd, const double* Psid,
                 double n_factor, int mode, double* H, double* cond) {
     const cplx* V = (const cplx*)Vd;
@@ -318,12 +321,15 @@ int orc_hessian(int K, int64_t n, const float* A, int64_t ld, const double* Vd, 
     int bad = 0;
     for (int64_t i = 0; i < n && !bad; ++i) {
         cplx u = 0.0;
+        double su = 0.0;
         for (int a = 0; a < K; ++a) {
             Ai[a] = A[2 * ((int64_t)a * ld + i)] + I * A[2 * ((int64_t)a * ld + i) + 1];
             u += V[a] * Ai[a];
+            su += cabs(V[a]) * cabs(Ai[a]);
         }
         const double Ii = creal(u) * creal(u) + cimag(u) * cimag(u);
         if (!(Ii > 0.0) || !isfinite(Ii)) { bad = 1; break; }
+        const double amp = su / sqrt(Ii);  /* s_i / |u_i| >= 1 */
         for (int c = 0; c < K; ++c) {
             const cplx z = conj(Ai[c]) * u;
             r[2 * c] = 2.0 * creal(z) / Ii;
@@ -332,7 +338,7 @@ int orc_hessian(int K, int64_t n, const float* A, int64_t ld, const double* Vd, 
         for (int x = 0; x < D; ++x)
             for (int y = 0; y < D; ++y) {
                 nsum_add(&acc[x * D + y], r[x] * r[y]);
-                sc[x * D + y] += fabs(r[x] * r[y]);
+                sc[x * D + y] += fabs(r[x] * r[y]) * amp;
             }
         if (mode == 1) {
             for (int a = 0; a < K; ++a)
@@ -343,10 +349,10 @@ int orc_hessian(int K, int64_t n, const float* A, int64_t ld, const double* Vd, 
                     nsum_add(&acc[(2 * a + 1) * D + 2 * b + 1], -re);
                     nsum_add(&acc[(2 * a) * D + 2 * b + 1], -im);
                     nsum_add(&acc[(2 * a + 1) * D + 2 * b], im);
-                    sc[(2 * a) * D + 2 * b] += fabs(re);
-                    sc[(2 * a + 1) * D + 2 * b + 1] += fabs(re);
-                    sc[(2 * a) * D + 2 * b + 1] += fabs(im);
-                    sc[(2 * a + 1) * D + 2 * b] += fabs(im);
+                    sc[(2 * a) * D + 2 * b] += fabs(re) * amp;
+                    sc[(2 * a + 1) * D + 2 * b + 1] += fabs(re) * amp;
+                    sc[(2 * a) * D + 2 * b + 1] += fabs(im) * amp;
+                    sc[(2 * a + 1) * D + 2 * b] += fabs(im) * amp;
                 }
         }
     }
