@@ -174,6 +174,20 @@ PWA_API pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n,
                         const float* V, int P, const double* Psi, double n_factor, double* nll,
                         double* grad, void* stream);
 
+/* Second derivatives of nll (pwa_nll) for ONE parameter set in theta = (Re V_0, Im V_0, Re V_1, ...),
+ * the curvature the Fumili / Newton-type fitters use and whose inverse gives the parameter errors
+ * (Sec. 4, "More control over the fitters"):
+ *   r_i = grad_theta ln I_i,  r_i[2c] = 2 Re(conj(A_c) u_i) / I_i,  r_i[2c+1] = 2 Im(conj(A_c) u_i) / I_i
+ *   exact = 0 (Fumili, outer-product form):  H = sum_i r_i r_i^T
+ *   exact = 1:  H = sum_i r_i r_i^T - E(sum_i A_i A_i^H / I_i) + n_factor E(Psi),
+ * E(C)[2a][2b] = E(C)[2a+1][2b+1] = 2 Re C_ab, E(C)[2a][2b+1] = 2 Im C_ab, E(C)[2a+1][2b] = -2 Im C_ab.
+ *   A    complex float [K][ld] (ld even, 16-byte aligned), 1 <= K <= 32
+ *   V    complex float [K]; Psi complex double [K][K]
+ *   H    double [2K][2K] output, row-major; all NaN (and the status word set) if some I_i <= 0 or
+ *        not finite.  The event sums are accumulated in double-single in a fixed order. */
+PWA_API pwa_status pwa_hessian(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V,
+                               const double* Psi, double n_factor, int exact, double* H, void* stream);
+
 /* -lnL (and its gradient) with the intensity summed incoherently over H unobserved states, e.g.
  * the helicity of the radiated photon in J/psi -> gamma X (the paper's example, Sec. 2): Eq. 1
  * summed over h with the production amplitudes shared by all states,

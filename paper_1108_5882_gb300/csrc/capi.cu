@@ -438,6 +438,30 @@ pwa_status pwa_nll_grad(pwa_handle* h, const float* A, int K, int64_t n, int64_t
     return nll_common(h, A, K, n, ld, V, P, Psi, n_factor, nll, grad, stream);
 }
 
+pwa_status pwa_hessian(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V, const double* Psi,
+                       double n_factor, int exact, double* H, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    if (K > PWA_MAX_WAVES / 2) return fail(h, PWA_ERR_INVALID_ARG, "pwa_hessian: K = %d > %d", K, PWA_MAX_WAVES / 2);
+    if ((n > 0 && !A) || !V || !Psi || !H)
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array argument (A, V, Psi and H are required)");
+    if (n > 0 && !aligned16(A)) return fail(h, PWA_ERR_INVALID_ARG, "A is not 16-byte aligned");
+    if (!aligned16(Psi)) return fail(h, PWA_ERR_INVALID_ARG, "Psi is not 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) != 0) return fail(h, PWA_ERR_INVALID_ARG, "V is not 8-byte aligned");
+    if (!std::isfinite(n_factor)) return fail(h, PWA_ERR_INVALID_ARG, "n_factor is not finite");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    st = ensure_workspace(h, pwa::hessian_workspace(K, ld, h->sm_count), 1);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::launch_hessian(reinterpret_cast<const float2*>(A), K, n, ld, reinterpret_cast<const float2*>(V),
+                                        reinterpret_cast<const double2*>(Psi), n_factor, exact ? 1 : 0, H, h->ws,
+                                        h->status, h->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "hessian launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
 pwa_status pwa_nll_grad_incoherent(pwa_handle* h, const float* A, int K, int H, int64_t n, int64_t ld,
                                    const float* V, int P, const double* Psi, double n_factor, double* nll,
                                    double* grad, void* stream) {

@@ -234,6 +234,12 @@ cudaError_t launch_toy_moments(const WaveTable& wt, const double* Md, const doub
 cudaError_t launch_mlp_gemm(int M, int N, int Kc, const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
                             int b_bf16, int64_t sbn, int64_t sbk, const float* bias, int relu, int accumulate, float* C,
                             uint16_t* Cb, int64_t ldc, int sm_count, cudaStream_t st);
+// Hessian of -lnL in the real coordinates of one set V (K <= 32): the Fumili outer-product form,
+// or (exact) the full second derivatives; H double [2K][2K].
+size_t hessian_workspace(int K, int64_t ld, int sm_count);
+cudaError_t launch_hessian(const float2* A, int K, int64_t n, int64_t ld, const float2* V, const double2* Psi,
+                           double nfac, int exact, double* H, void* ws, int* status, int sm_count, cudaStream_t st);
+
 // Psi straight from MC kinematics kin [3][ld]: the amplitudes of each tile of events are computed
 // in shared memory (with the arithmetic of pwa_amplitudes) and consumed there.
 cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int64_t n, int64_t ld, const float* w,

@@ -87,6 +87,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.pwa_nll_grad_incoherent.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _vp, ctypes.c_int,
                                                 _vp, ctypes.c_double, _vp, _vp, _vp]
         lib.pwa_nll_grad_incoherent.restype = S
+        lib.pwa_hessian.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp,
+                                    _vp]
+        lib.pwa_hessian.restype = S
         _register_optional(lib)
         _lib = lib
         return lib
@@ -273,6 +276,16 @@ class Handle:
         P = V.shape[0]
         self._chk(self.lib.pwa_nll(self.h, _ptr(A), K, int(n), int(ld), _ptr(V), P, _ptr(Psi), float(n_factor),
                                    _ptr(nll), _stream_ptr(stream)))
+
+    def pwa_hessian(self, A, n, V, Psi, n_factor, H, exact=False, stream=None):
+        """A complex64 [K][ld], V complex64 [K] (one set), Psi complex128 [K][K]; H float64 [2K][2K]."""
+        _check_cuda(A, "A", torch.complex64)
+        _check_cuda(V, "V", torch.complex64)
+        _check_cuda(Psi, "Psi", torch.complex128)
+        _check_cuda(H, "H", torch.float64)
+        K, ld = A.shape
+        self._chk(self.lib.pwa_hessian(self.h, _ptr(A), K, int(n), int(ld), _ptr(V), _ptr(Psi), float(n_factor),
+                                       1 if exact else 0, _ptr(H), _stream_ptr(stream)))
 
     def pwa_nll_grad_incoherent(self, A, n, V, Psi, n_factor, nll, grad=None, stream=None):
         """A complex64 [K][H][ld] (intensity summed over the H states), V complex64 [P][K], Psi

@@ -89,7 +89,7 @@ def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a8,a9")
+    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a7h,a8,a9")
     ap.add_argument("--json", default=None)
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and one timed launch per kernel, no peak microbenchmark and 64 toys "
@@ -165,6 +165,23 @@ def main():
         sec = T(lambda: h.pwa_nll_grad_incoherent(A, N, V, Psi, float(N), nll, g), R)
         add("a3i", f"incoherent -lnL+grad (H={H} states), K={K}, N={N:.0e}", sec, nbytes=N * K * H * 8,
             flops=N * H * (16 * K + 4.0))
+        del A, kin
+    if "a7h" in rows:
+        # Hessian of -lnL (exact form: two Gram passes) for one set, K = 16, N = 1e6
+        K, N = 16, 1_000_000
+        kin = torch.from_numpy(inputs.kinematics(N, seed, 4)).cuda()
+        A = torch.empty((K, N), dtype=torch.complex64, device="cuda")
+        h.pwa_amplitudes(w16, kin, N, A)
+        V = torch.from_numpy(inputs.production_amplitudes(K, seed)).cuda()
+        Psi = torch.eye(K, dtype=torch.complex128, device="cuda")
+        Hm = torch.empty((2 * K, 2 * K), dtype=torch.float64, device="cuda")
+        for exact in (False, True):
+            sec = T(lambda: h.pwa_hessian(A, N, V, Psi, float(N), Hm, exact=exact), R)
+            D = 2 * K
+            # bytes: A read twice (vectors, exact Gram) + r written and read (2K complex rows)
+            nb = N * K * 8 * (2 if exact else 1) + 2 * N * D * 8
+            fl = N * 8.0 * D * (D + 1) / 2 + (N * 8.0 * K * (K + 1) / 2 if exact else 0.0)
+            add("a7h", f"Hessian of -lnL ({'exact' if exact else 'Fumili'}), K={K}, N={N:.0e}", sec, nbytes=nb, flops=fl)
         del A, kin
     if "a5" in rows:
         # floating shape: data 1e6 + MC 5e6 events, 4 floating parameters (2 masses, 2 widths)

@@ -227,6 +227,32 @@ def test_normint_from_kinematics(h, K, n, weighted):
     assert np.all(np.abs(Psi_k.cpu().numpy() - Psi_a.cpu().numpy()) <= tol)  # the unfused path
 
 
+@pytest.mark.parametrize("K,n", [(4, 3001), (13, 20_001), (16, 100_000), (32, 9_999), (1, 1)])
+def test_hessian_fumili_and_exact(h, K, n):
+    p = make_problem(K, n, max(2 * n, 1000), SEED + 1500 + K, accept_reject=False)
+    ld = n + 1 if n % 2 else n + 2
+    Ad = dev(padded(p.A, ld, fill=np.complex64(np.nan)))
+    V = inputs.starts(1, K, SEED + 1600 + K)[0]
+    for exact in (False, True):
+        H = torch.zeros((2 * K, 2 * K), dtype=torch.float64, device="cuda")
+        h.pwa_hessian(Ad, n, dev(V), dev(p.Psi), float(n), H, exact=exact)
+        ref, cond, bad = oracle.hessian(p.A, V, p.Psi, n_factor=float(n), exact=exact, with_cond=True)
+        assert bad == 0
+        err = np.abs(H.cpu().numpy() - ref) / (cond + 1e-300)
+        assert np.all(err <= 1e-5), (exact, err.max())
+    assert h.pwa_sync_status() == 0
+
+
+def test_hessian_flags_a_vanishing_intensity(h):
+    from paper_1108_5882_gb300 import pwa
+    A = np.zeros((2, 8), dtype=np.complex64)  # u_i = 0 for every event
+    H = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    h.pwa_hessian(dev(A), 8, dev(np.array([1.0 + 0j, 0.5j], dtype=np.complex64)),
+                  dev(np.eye(2, dtype=np.complex128)), 8.0, H)
+    assert np.all(np.isnan(H.cpu().numpy()))
+    assert h.pwa_sync_status() == pwa.PWA_ERR_NONFINITE
+
+
 def _incoherent_problem(K, H, n, n_mc, seed):
     # state h: the amplitude model of a wave set of its own (J, lambda, M, Gamma drawn per state),
     # on the same events: A [K][H][n] and the MC normalisation summed over the states
