@@ -254,6 +254,11 @@ typedef struct pwa_fit_opts {
     int check_every;      /* iterations per graph replay between host checks (default 20) */
     int gauge_fix;        /* 1: rotate each start so that V_0 is real >= 0 and freeze Im V_0 */
     int use_graph;        /* 1: replay iterations as a captured CUDA graph (default 1) */
+    int polar;            /* 1: minimise over (rho_a, phi_a), V_a = rho_a exp(i phi_a), instead of
+                           * (Re V_a, Im V_a) (Sec. 4, "Fits with complex parameters"); the
+                           * magnitude is signed and the phase unwrapped, so neither is bounded;
+                           * with gauge_fix, phi_0 is frozen at 0.  grad_max and gtol then refer
+                           * to these coordinates; V_out and x_out hold V either way (default 0) */
 } pwa_fit_opts;
 
 typedef struct pwa_fit_result {

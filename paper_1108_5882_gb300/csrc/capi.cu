@@ -696,6 +696,12 @@ void pwa_fit_default_opts(pwa_fit_opts* o) {
     o->check_every = 20;
     o->gauge_fix = 1;
     o->use_graph = 1;
+    o->polar = 0;
+}
+
+// the fit kernels' mode bits of a set of options
+static int fit_mode(const pwa_fit_opts& o) {
+    return (o.gauge_fix ? pwa::FIT_GAUGE : 0) | (o.polar ? pwa::FIT_POLAR : 0);
 }
 
 pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, const pwa_fit_opts* opts_in,
@@ -705,8 +711,10 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     pwa_fit_opts o;
     pwa_fit_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1)
-        return fail(h, PWA_ERR_INVALID_ARG, "bad options (max_iter >= 1, 1 <= history <= 20, gtol > 0, check_every >= 1)");
+    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1 ||
+        (o.polar != 0 && o.polar != 1))
+        return fail(h, PWA_ERR_INVALID_ARG,
+                    "bad options (max_iter >= 1, 1 <= history <= 20, gtol > 0, check_every >= 1, polar 0 or 1)");
     int P_tot = 0;
     size_t ws_need = 0;
     for (int f = 0; f < n_fits; ++f) {
@@ -766,7 +774,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     int off = 0;
     for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
         e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(fits[f].V0), fits[f].K, fits[f].P,
-                                 off, o.gauge_fix, eb[f].Vt, s);
+                                 off, fit_mode(o), eb[f].Vt, s);
         off += fits[f].P;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "fit init");
@@ -780,7 +788,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
                                              h->sm_count, s, /*fp32_only=*/true);
             if (ee != cudaSuccess) return ee;
             ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
-                                      o.gtol * std::fabs(d.n_factor), o.gauge_fix, o.max_iter, s);
+                                      o.gtol * std::fabs(d.n_factor), fit_mode(o), o.max_iter, s);
             if (ee != cudaSuccess) return ee;
             p_off += d.P;
         }
@@ -790,7 +798,8 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     if (e != cudaSuccess) return cuda_fail(h, e, "fit loop");
     off = 0;
     for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
-        if (fits[f].V_out) e = pwa::fit_export(h->fitws, P_tot, m, fits[f].K, fits[f].P, off, fits[f].V_out, s);
+        if (fits[f].V_out)
+            e = pwa::fit_export(h->fitws, P_tot, m, fits[f].K, fits[f].P, off, fit_mode(o), fits[f].V_out, s);
         off += fits[f].P;
     }
     std::vector<double> fv, gm;
@@ -815,7 +824,8 @@ pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, in
     pwa_fit_opts o;
     pwa_fit_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1)
+    if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1 ||
+        (o.polar != 0 && o.polar != 1))
         return fail(h, PWA_ERR_INVALID_ARG, "bad options");
     std::vector<pwa::WaveTable> wts(n_fits);
     for (int f = 0; f < n_fits; ++f) {
@@ -915,7 +925,7 @@ pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, in
         for (int q = 0; q < d.F; ++q)
             th0[f][q] = d.float_kind[q] == 0 ? d.waves[d.float_wave[q]].mass : d.waves[d.float_wave[q]].width;
         if (e == cudaSuccess)
-            e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(d.V0), d.K, 1, f, o.gauge_fix,
+            e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(d.V0), d.K, 1, f, fit_mode(o),
                                      ch[f].Vt, s, d.F, th0[f].data(), ch[f].th);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "shape fit init");
@@ -951,7 +961,7 @@ pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, in
                                    h->sm_count, sc);
         if (ee != cudaSuccess) return ee;
         return pwa::fit_launch_step(h->fitws, P_tot, m, ch[f].nll, ch[f].grad, ch[f].Vt, d.K, 1, f,
-                                    o.gtol * std::fabs(d.n_factor), o.gauge_fix, o.max_iter, sc, d.F, ch[f].th,
+                                    o.gtol * std::fabs(d.n_factor), fit_mode(o), o.max_iter, sc, d.F, ch[f].th,
                                     lb[f].data());
     };
     auto iteration = [&]() -> cudaError_t {
@@ -969,7 +979,8 @@ pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, in
     std::vector<int> D_of_p(P_tot);
     for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
         D_of_p[f] = 2 * fits[f].K + fits[f].F;
-        if (fits[f].x_out) e = pwa::fit_export_x(h->fitws, P_tot, m, D_of_p[f], f, fits[f].x_out, s);
+        if (fits[f].x_out)
+            e = pwa::fit_export_x(h->fitws, P_tot, m, fits[f].K, D_of_p[f], f, fit_mode(o), fits[f].x_out, s);
     }
     std::vector<double> fv, gm;
     std::vector<int> it, ev, stv;

@@ -20,6 +20,15 @@
 // Gauge: f is invariant under a global phase of V (Eq. 1), so the Hessian is singular along
 // i V.  With gauge_fix each start is rotated so that V_0 is real and non-negative and the
 // Im V_0 component of the gradient is frozen at zero.
+//
+// Coordinates (Sec. 4, "Fits with complex parameters": the minimiser sees real numbers, and
+// both the Cartesian and the polar representation of a complex parameter have drawbacks).
+// Cartesian: x_2a = Re V_a, x_2a+1 = Im V_a.  Polar: x_2a = rho_a, x_2a+1 = phi_a with
+// V_a = rho_a exp(i phi_a); the gradient of pwa_nll_grad is carried over by the chain rule,
+//   d f / d rho = g_re cos phi + g_im sin phi,   d f / d phi = rho (g_im cos phi - g_re sin phi).
+// The magnitude is signed (rho < 0 is the point (|rho|, phi + pi)), so there is no lower bound
+// to enforce, and the phase is left unwrapped.  With the gauge fixed, phi_0 is the frozen
+// component.  The results are reported as V in both cases.
 #include <cmath>
 #include <vector>
 
@@ -51,6 +60,14 @@ struct FitState {
 };
 
 constexpr int DM = 2 * PWA_MAX_WAVES;
+
+// V_a of its two coordinates: Cartesian (Re, Im) or polar (rho, phi)
+__device__ __forceinline__ double2 coords_to_v(double x0, double x1, bool polar) {
+    if (!polar) return make_double2(x0, x1);
+    double s, c;
+    sincos(x1, &s, &c);
+    return make_double2(x0 * c, x0 * s);
+}
 
 __device__ __forceinline__ double block_dot(const double* a, const double* b, int D, double* red) {
     // fixed-order dot product over D <= 128 components: per-thread products, shared tree
@@ -85,10 +102,10 @@ struct Theta0 {
     double lb[PWA_MAX_FLOAT];
 };
 
-__global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, int p_off, int gauge,
+__global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, int p_off, int mode,
                            float2* __restrict__ Vt, int F, Theta0 th, double* __restrict__ theta_t) {
     const int p = p_off + blockIdx.x, t = threadIdx.x;
-    const int D = 2 * K;
+    const bool gauge = mode & FIT_GAUGE, polar = mode & FIT_POLAR;
     // phase of V_0
     const float2 v0 = V0[(int64_t)blockIdx.x * K];
     double c = 1.0, s = 0.0;
@@ -101,10 +118,13 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
     }
     if (t < K) {
         const float2 v = V0[(int64_t)blockIdx.x * K + t];
-        const double re = c * v.x - s * v.y, im = c * v.y + s * v.x;
-        st.x[(int64_t)p * DM + 2 * t] = re;
-        st.x[(int64_t)p * DM + 2 * t + 1] = (gauge && t == 0) ? 0.0 : im;
-        Vt[(int64_t)blockIdx.x * K + t] = make_float2((float)re, (gauge && t == 0) ? 0.f : (float)im);
+        const double re = c * v.x - s * v.y, im = (gauge && t == 0) ? 0.0 : c * v.y + s * v.x;
+        // polar: rho = |V_a|, phi = arg V_a (phi_0 = 0 exactly when the gauge is fixed)
+        const double x0 = polar ? hypot(re, im) : re, x1 = polar ? atan2(im, re) : im;
+        st.x[(int64_t)p * DM + 2 * t] = x0;
+        st.x[(int64_t)p * DM + 2 * t + 1] = x1;
+        const double2 vt = coords_to_v(x0, x1, polar);
+        Vt[(int64_t)blockIdx.x * K + t] = make_float2((float)vt.x, (float)vt.y);
     }
     if (t < F) {
         st.x[(int64_t)p * DM + 2 * K + t] = th.v[t];
@@ -120,7 +140,6 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
         st.f[p] = INFINITY;
         st.gtd[p] = 0.0;
     }
-    (void)D;
 }
 
 // One L-BFGS step per start.  ft/gt: f and g at the trial point just evaluated (layout of
@@ -128,15 +147,18 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
 // Writes the trial V (and, for F > 0 floating shape parameters, the trial theta) of the next
 // evaluation; x = (Re V_0, Im V_0, ..., Re V_K-1, Im V_K-1, theta_0..theta_F-1).
 __device__ __forceinline__ void write_trial(const double* x, const double* d, double a, int K, int F, int pl,
-                                            float2* Vt, double* theta_t) {
+                                            float2* Vt, double* theta_t, bool polar) {
     const int t = threadIdx.x;
-    if (t < K) Vt[(int64_t)pl * K + t] = make_float2((float)(x[2 * t] + a * d[2 * t]), (float)(x[2 * t + 1] + a * d[2 * t + 1]));
+    if (t < K) {
+        const double2 v = coords_to_v(x[2 * t] + a * d[2 * t], x[2 * t + 1] + a * d[2 * t + 1], polar);
+        Vt[(int64_t)pl * K + t] = make_float2((float)v.x, (float)v.y);
+    }
     if (t < F) theta_t[(int64_t)pl * F + t] = x[2 * K + t] + a * d[2 * K + t];
 }
 
 __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* __restrict__ ft,
                                                     const double* __restrict__ gt, float2* __restrict__ Vt, int K,
-                                                    int p_off, int m, double gtol, int gauge, int max_iter, int F,
+                                                    int p_off, int m, double gtol, int mode, int max_iter, int F,
                                                     double* __restrict__ theta_t, Theta0 th) {
     __shared__ double red[128];
     __shared__ double q[DM], xt[DM];
@@ -144,6 +166,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     __shared__ int s_action;  // 0: keep, 1: accepted, 2: rejected
     const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
     const int D = 2 * K + F;
+    const bool gauge = mode & FIT_GAUGE, polar = mode & FIT_POLAR;
     double* x = st.x + (int64_t)p * DM;
     double* g = st.g + (int64_t)p * DM;
     double* d = st.d + (int64_t)p * DM;
@@ -152,16 +175,24 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     double* rho = st.rho + (int64_t)p * m;
     const int status = st.status[p];
     if (status != FIT_RUNNING) {
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
         return;
     }
     if (t == 0) st.evals[p] += 1;
     const double fnew = ft[pl];
     // trial point that was evaluated = x + alpha d (or x itself for the first evaluation)
     const double alpha = st.alpha[p];
+    if (t < D) xt[t] = (alpha == 0.0) ? x[t] : x[t] + alpha * d[t];
+    __syncthreads();
     if (t < D) {
-        xt[t] = (alpha == 0.0) ? x[t] : x[t] + alpha * d[t];
-        double gv = gt[(int64_t)pl * D + t];
+        const double* gp = gt + (int64_t)pl * D;
+        double gv = gp[t];
+        if (polar && t < 2 * K) {  // chain rule from (Re V_a, Im V_a) to (rho_a, phi_a)
+            const int a = t >> 1;
+            double sn, cs;
+            sincos(xt[2 * a + 1], &sn, &cs);
+            gv = (t & 1) ? xt[2 * a] * (gp[2 * a + 1] * cs - gp[2 * a] * sn) : gp[2 * a] * cs + gp[2 * a + 1] * sn;
+        }
         if (gauge && t == 1) gv = 0.0;
         q[t] = gv;  // gradient at the trial point (frozen gauge component)
     }
@@ -186,7 +217,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const int action = s_action;
     if (action == 3) {  // non-finite at the start point
         if (t == 0) st.status[p] = 3;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
         return;
     }
     if (action == 2) {
@@ -205,7 +236,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
             if (an < 1e-20) st.status[p] = 2;
         }
         __syncthreads();
-        write_trial(x, d, st.alpha[p], K, F, pl, Vt, theta_t);
+        write_trial(x, d, st.alpha[p], K, F, pl, Vt, theta_t, polar);
         return;
     }
     // ---- accepted: history update with s = xt - x, y = gt - g
@@ -242,12 +273,12 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const double gmax = block_max_abs(g, D, red);
     if (gmax < gtol) {
         if (t == 0) st.status[p] = 0;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
         return;
     }
     if (st.iter[p] >= max_iter) {
         if (t == 0) st.status[p] = 1;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t);
+        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
         return;
     }
     // ---- two-loop recursion: q = g; newest to oldest
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
         st.gtd[p] = gtd;
         st.alpha[p] = a0;
     }
-    write_trial(x, d, a0, K, F, pl, Vt, theta_t);
+    write_trial(x, d, a0, K, F, pl, Vt, theta_t, polar);
 }
 
 __global__ void k_count_running(const int* __restrict__ status, int P, int* __restrict__ out) {
@@ -323,15 +354,30 @@ __global__ void k_count_running(const int* __restrict__ status, int P, int* __re
     if (threadIdx.x == 0) *out = s[0];
 }
 
-__global__ void k_fit_export(FitState st, int K, int p_off, int P, double2* __restrict__ Vout) {
-    const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
-    if (t < K && Vout) Vout[(int64_t)pl * K + t] = make_double2(st.x[(int64_t)p * DM + 2 * t], st.x[(int64_t)p * DM + 2 * t + 1]);
-    (void)P;
+// V_a of start p from its coordinates.  With the gauge fixed, a start whose V_0 ended on the
+// negative real axis is reported as -V, the same point of f, so that V_0 >= 0 as documented.
+__device__ __forceinline__ double2 export_v(const FitState& st, int p, int a, int mode) {
+    const double* x = st.x + (int64_t)p * DM;
+    double2 v = coords_to_v(x[2 * a], x[2 * a + 1], mode & FIT_POLAR);
+    if ((mode & FIT_GAUGE) && coords_to_v(x[0], x[1], mode & FIT_POLAR).x < 0.0) v = make_double2(-v.x, -v.y);
+    return v;
 }
 
-__global__ void k_fit_export_x(FitState st, int D, int p, double* __restrict__ xout) {
+__global__ void k_fit_export(FitState st, int K, int p_off, int mode, double2* __restrict__ Vout) {
+    const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
+    if (t < K && Vout) Vout[(int64_t)pl * K + t] = export_v(st, p, t, mode);
+}
+
+// (Re V_0, Im V_0, ..., theta) of start p
+__global__ void k_fit_export_x(FitState st, int K, int D, int p, int mode, double* __restrict__ xout) {
     const int t = threadIdx.x;
-    if (t < D) xout[t] = st.x[(int64_t)p * DM + t];
+    if (t < K) {
+        const double2 v = export_v(st, p, t, mode);
+        xout[2 * t] = v.x;
+        xout[2 * t + 1] = v.y;
+    } else if (t >= 2 * K && t < D) {
+        xout[t] = st.x[(int64_t)p * DM + t];
+    }
 }
 
 }  // namespace
@@ -396,18 +442,18 @@ static Theta0 make_theta0(int F, const double* theta0, const double* lb) {
     return th;
 }
 
-cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
+cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int mode,
                             float2* Vt, cudaStream_t s, int F, const double* theta0, double* theta_t) {
     FitState st = carve(fitws, P_tot, m);
-    k_fit_init<<<P, 128, 0, s>>>(st, V0, K, p_off, gauge, Vt, F, make_theta0(F, theta0, nullptr), theta_t);
+    k_fit_init<<<P, 128, 0, s>>>(st, V0, K, p_off, mode, Vt, F, make_theta0(F, theta0, nullptr), theta_t);
     return cudaGetLastError();
 }
 
 cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
-                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s, int F,
+                            int P, int p_off, double gtol, int mode, int max_iter, cudaStream_t s, int F,
                             double* theta_t, const double* lb) {
     FitState st = carve(fitws, P_tot, m);
-    k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, gauge, max_iter, F, theta_t,
+    k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, mode, max_iter, F, theta_t,
                                    make_theta0(F, nullptr, lb));
     return cudaGetLastError();
 }
@@ -445,15 +491,16 @@ cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>&
     return cudaSuccess;
 }
 
-cudaError_t fit_export_x(void* fitws, int P_tot, int m, int D, int p, double* xout, cudaStream_t s) {
+cudaError_t fit_export_x(void* fitws, int P_tot, int m, int K, int D, int p, int mode, double* xout, cudaStream_t s) {
     FitState st = carve(fitws, P_tot, m);
-    k_fit_export_x<<<1, 128, 0, s>>>(st, D, p, xout);
+    k_fit_export_x<<<1, 128, 0, s>>>(st, K, D, p, mode, xout);
     return cudaGetLastError();
 }
 
-cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s) {
+cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, int mode, double* Vout,
+                       cudaStream_t s) {
     FitState st = carve(fitws, P_tot, m);
-    k_fit_export<<<P, 128, 0, s>>>(st, K, p_off, P, reinterpret_cast<double2*>(Vout));
+    k_fit_export<<<P, 128, 0, s>>>(st, K, p_off, mode, reinterpret_cast<double2*>(Vout));
     return cudaGetLastError();
 }
 

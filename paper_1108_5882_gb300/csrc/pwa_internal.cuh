@@ -198,20 +198,26 @@ cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const floa
 // record a message for pwa_last_error(NULL) (calls without a handle)
 void record_global_error(const char* msg);
 
+// mode bits of the fit kernels: FIT_GAUGE rotates each start so that V_0 is real >= 0 and
+// freezes the phase component of V_0; FIT_POLAR makes the minimiser's coordinates of wave a
+// (rho_a, phi_a) with V_a = rho_a exp(i phi_a) instead of (Re V_a, Im V_a)
+constexpr int FIT_GAUGE = 1, FIT_POLAR = 2;
+
 size_t fit_workspace(int P_tot, int m);
 size_t fit_eval_bytes(int P, int K);
-cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int gauge,
+cudaError_t fit_launch_init(void* fitws, int P_tot, int m, const float2* V0, int K, int P, int p_off, int mode,
                             float2* Vt, cudaStream_t s, int F = 0, const double* theta0 = nullptr,
                             double* theta_t = nullptr);
 cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, const double* gt, float2* Vt, int K,
-                            int P, int p_off, double gtol, int gauge, int max_iter, cudaStream_t s, int F = 0,
+                            int P, int p_off, double gtol, int mode, int max_iter, cudaStream_t s, int F = 0,
                             double* theta_t = nullptr, const double* lb = nullptr);
-cudaError_t fit_export_x(void* fitws, int P_tot, int m, int D, int p, double* xout, cudaStream_t s);
+cudaError_t fit_export_x(void* fitws, int P_tot, int m, int K, int D, int p, int mode, double* xout, cudaStream_t s);
 cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaStream_t s);
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
                              std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int D_of_p[],
                              cudaStream_t s);
-cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, double* Vout, cudaStream_t s);
+cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, int mode, double* Vout,
+                       cudaStream_t s);
 
 size_t shape_workspace(int K, int F, int sm_count);
 cudaError_t launch_nll_shape(const float2* A, const float2* dA, int K, int64_t n, int64_t ld, const float2* Am,

@@ -143,7 +143,8 @@ class pwa_fit_desc(ctypes.Structure):
 
 class pwa_fit_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("history", ctypes.c_int), ("gtol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("polar", ctypes.c_int)]
 
 
 class pwa_fit_result(ctypes.Structure):

@@ -68,3 +68,14 @@ def padded(a, ld, fill=0.0):
     out = np.full((a.shape[0], ld), fill, dtype=a.dtype)
     out[:, :a.shape[1]] = a
     return out
+
+
+def polar_gradient(g, V):
+    """d f / d rho_a, d f / d phi_a at V_a = rho_a exp(i phi_a) from the Cartesian gradient g
+    (Re, Im interleaved).  Their magnitudes do not depend on which of the two polar
+    representations (rho, phi), (-rho, phi + pi) of V_a is taken."""
+    gre, gim = g[0::2], g[1::2]
+    rho, phi = np.abs(V), np.angle(V)
+    gr = gre * np.cos(phi) + gim * np.sin(phi)
+    gp = rho * (gim * np.cos(phi) - gre * np.sin(phi))
+    return gr, gp

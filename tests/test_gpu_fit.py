@@ -3,7 +3,8 @@
 A converged start must be a stationary point of the oracle's -lnL (oracle gradient small,
 and S(V) = V^T Psi V* = 1, which the Euler identity forces at any stationary point); the best
 minimum over the starts must match an independent minimiser (scipy L-BFGS-B on the oracle);
-and a toy fit must recover the seeded production amplitudes within statistical error.
+and a toy fit must recover the seeded production amplitudes within statistical error.  The
+polar coordinates of V (Sec. 4, "Fits with complex parameters") must reach the same minima.
 """
 import math
 
@@ -14,7 +15,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_1108_5882_gb300 import inputs
-from problems import accept_reject_data, make_problem
+from problems import accept_reject_data, make_problem, polar_gradient
 
 pytestmark = pytest.mark.gpu
 SEED = inputs.SEED_BASE
@@ -167,3 +168,41 @@ def test_graph_and_eager_are_identical(h):
     r2, (V2,) = run_fits(h, [(p, V0)], use_graph=0)
     assert [r["nll"] for r in r1] == [r["nll"] for r in r2]
     assert np.array_equal(V1, V2)
+
+
+
+@pytest.mark.parametrize("K,n,n_mc,P", [(4, 10_000, 50_000, 16), (16, 50_000, 100_000, 8)])
+def test_polar_fits_end_at_minima_of_f(h, K, n, n_mc, P):
+    p = make_problem(K, n, n_mc, SEED + 41 + K, plain=(K == 4), accept_reject=(K == 4))
+    V0 = inputs.starts(P, K, SEED + 41 + K)
+    rc, (Vc,) = run_fits(h, [(p, V0)], max_iter=3000)
+    rp, (Vp,) = run_fits(h, [(p, V0)], max_iter=3000, polar=1)
+    conv = [i for i, r in enumerate(rp) if r["status"] == 0]
+    assert len(conv) >= P // 2, [r["status"] for r in rp]
+    for i in conv:
+        r = rp[i]
+        assert r["grad_max"] < 1e-6 * p.n
+        Vf = Vp[i].astype(np.complex64)
+        f, g = oracle.nll_grad(p.A, Vf[None, :], p.Psi)
+        gr, gp = polar_gradient(g[0], Vp[i])
+        gp[0] = 0.0  # phi_0 frozen by the gauge
+        assert max(np.max(np.abs(gr)), np.max(np.abs(gp))) < 1e-5 * p.n
+        # a minimum of f itself, not only of its polar map (which is singular at rho_a = 0):
+        # the Cartesian gradient of wave a is (gr_a, gp_a / rho_a) rotated by phi_a
+        gc = g[0].copy()
+        gc[1] = 0.0  # Im V_0, the same frozen direction at V_0 > 0
+        ga = np.hypot(gc[0::2], gc[1::2])
+        assert np.all(ga < 1e-5 * p.n * np.maximum(1.0, 1.0 / np.abs(Vp[i]))), ga
+        S = float(np.real(Vf.astype(np.complex128) @ p.Psi @ np.conj(Vf.astype(np.complex128))))
+        assert abs(S - 1.0) < 1e-4, S  # stationarity along every rho_a forces S = 1
+        assert abs(f[0] - r["nll"]) <= 1e-5 * max(abs(f[0]), p.n)
+        assert abs(Vp[i][0].imag) == 0.0 and Vp[i][0].real >= 0.0
+    if K == 4:
+        # few waves, data drawn from the model: the best start reaches the global minimum
+        # (Delta lnL < 0.01) in both coordinate systems
+        best_c = min(r["nll"] for r in rc if r["status"] == 0)
+        best_p = min(rp[i]["nll"] for i in conv)
+        assert abs(best_p - best_c) < 0.01, (best_p, best_c)
+    # K = 16 on flat data has many local minima (Sec. 4, "Fits with large numbers of
+    # parameters"): from the same start the two coordinate systems may end in different ones
+    # (so do scipy's L-BFGS-B runs on the oracle in each system), so only minimality is checked.

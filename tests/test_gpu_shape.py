@@ -76,7 +76,8 @@ def _channel(K, n, seed):
     return ws, V, kin, kin_mc
 
 
-def test_shape_fits_of_uneven_channels(h):
+@pytest.mark.parametrize("polar", [0, 1])
+def test_shape_fits_of_uneven_channels(h, polar):
     from paper_1108_5882_gb300 import pwa
     chans = []
     meta = []
@@ -93,7 +94,7 @@ def test_shape_fits_of_uneven_channels(h):
                           n_gen=4 * n, n_factor=n, float_wave=fwave, float_kind=fkind,
                           V0=dev(V * 1.1), x_out=x_out))
         meta.append((ws, V, kin, kin_mc, fwave, fkind, x_out))
-    res = h.pwa_fit_shape_batch(chans, pwa.fit_opts(max_iter=2000))
+    res = h.pwa_fit_shape_batch(chans, pwa.fit_opts(max_iter=2000, polar=polar))
     for r, (ws, V, kin, kin_mc, fwave, fkind, x_out) in zip(res, meta):
         assert r["status"] == 0, r
         x = x_out.cpu().numpy()

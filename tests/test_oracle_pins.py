@@ -691,3 +691,34 @@ def test_hessian_brute_force_tiny():
             HX[2 * a + 1, 2 * b] -= 2 * 3.0 * Psi[a, b].imag
     assert np.allclose(oracle.hessian(A, V, Psi, n_factor=3.0), HF, rtol=1e-12, atol=1e-12)
     assert np.allclose(oracle.hessian(A, V, Psi, n_factor=3.0, exact=True), HF + HX, rtol=1e-12, atol=1e-12)
+
+
+def test_polar_gradient_matches_finite_differences_of_the_oracle():
+    from problems import make_problem, polar_gradient
+    SEED = inputs.SEED_BASE
+    # the fit tests' chain rule against central differences of the oracle -lnL along rho_a
+    # and phi_a at a non-stationary V
+    p = make_problem(4, 2_000, 8_000, SEED + 40, plain=True)
+    V = inputs.starts(1, 4, SEED + 40)[0].astype(np.complex128)
+    f0, g = oracle.nll_grad(p.A, V.astype(np.complex64)[None, :], p.Psi)
+    gr, gp = polar_gradient(g[0], V)
+    rho, phi = np.abs(V), np.angle(V)
+
+    def f_polar(r, ph):
+        # FP64 objective of Eq. 1 at V = r exp(i ph), straight from the definition
+        Vx = r * np.exp(1j * ph)
+        u = Vx @ p.A.astype(np.complex128)
+        return -np.sum(np.log(np.abs(u) ** 2)) + p.n * np.real(Vx @ p.Psi @ Vx.conj())
+
+    for a in range(4):
+        e = 1e-6
+        rp, rm = rho.copy(), rho.copy()
+        rp[a] += e
+        rm[a] -= e
+        fd_r = (f_polar(rp, phi) - f_polar(rm, phi)) / (2 * e)
+        pp, pm = phi.copy(), phi.copy()
+        pp[a] += e
+        pm[a] -= e
+        fd_p = (f_polar(rho, pp) - f_polar(rho, pm)) / (2 * e)
+        assert abs(fd_r - gr[a]) <= 1e-4 * max(1.0, abs(gr[a])), (a, fd_r, gr[a])
+        assert abs(fd_p - gp[a]) <= 1e-4 * max(1.0, abs(gp[a])), (a, fd_p, gp[a])
