@@ -89,7 +89,7 @@ def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a7h,a8,a9")
+    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a7p,a7h,a8,a9")
     ap.add_argument("--json", default=None)
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and one timed launch per kernel, no peak microbenchmark and 64 toys "
@@ -201,7 +201,7 @@ def main():
         del A, dA, dAm, kin
     if rows & {"a1", "a2", "a3", "a5"}:
         del A_mc, kin_mc
-    if rows & {"a4", "a7"}:
+    if rows & {"a4", "a7", "a7p"}:
         K, N, P = 32, 2_000_000, 256
         ws32 = inputs.wave_set_spread(K, seed + 1)
         kin = torch.from_numpy(inputs.kinematics(N, seed + 1, 4)).cuda()
@@ -234,20 +234,25 @@ def main():
             if shape == 4:
                 print(f"      tensor-core shape: {extra['frac_tensor']:.3f} of the 3xTF32 emulated-FP32 peak "
                       f"({tpeak:.1f} TFLOP/s)", flush=True)
-        if "a7" in rows:
+        for tag, polar in (("a7", 0), ("a7p", 1)):
+            if tag not in rows:
+                continue
             Vout = torch.empty((P, K), dtype=torch.complex128, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = h.pwa_fit_batch([dict(A=A, n=N, Psi=Psi, n_factor=N, V0=V, V_out=Vout)])
+            res = h.pwa_fit_batch([dict(A=A, n=N, Psi=Psi, n_factor=N, V0=V, V_out=Vout)], pwa.fit_opts(polar=polar))
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             iters = max(r["iterations"] for r in res)
             evals = sum(r["evaluations"] for r in res) / P
             conv = sum(r["status"] == 0 for r in res)
-            out["rows"].append({"row": "a7", "what": f"batched L-BFGS fit K={K}, N={N:.0e}, P={P}", "wall_s": wall,
-                                "iterations_max": iters, "evaluations_per_start": evals, "converged": conv})
-            print(f"a7  batched L-BFGS fit K={K}, N={N:.0e}, P={P}: {wall:.3f} s, {iters} iterations (max), "
-                  f"{evals:.1f} evaluations/start, {conv}/{P} converged", flush=True)
+            best = min(r["nll"] for r in res)
+            coords = "polar (rho, phi)" if polar else "Cartesian (Re V, Im V)"
+            out["rows"].append({"row": tag, "what": f"batched L-BFGS fit K={K}, N={N:.0e}, P={P}, {coords}",
+                                "wall_s": wall, "iterations_max": iters, "evaluations_per_start": evals,
+                                "converged": conv, "best_nll": best})
+            print(f"{tag:3s} batched L-BFGS fit K={K}, N={N:.0e}, P={P}, {coords}: {wall:.3f} s, {iters} iterations "
+                  f"(max), {evals:.1f} evaluations/start, {conv}/{P} converged, best -lnL {best:.3f}", flush=True)
         del A
     if "a8" in rows:
         sd = inputs.SEED_BASE + 5
