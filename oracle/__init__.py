@@ -7,6 +7,8 @@ module compiles it with gcc on first use and marshals numpy arrays through ctype
 
 Functions and the passages they follow:
   amplitudes   -- A_a(Omega) of Eq. 1 under the fixed-width unit-peak Breit-Wigner reading
+  amplitudes_barrier, breakup_q, barrier2 -- the same with a mass-dependent width and
+                  Blatt-Weisskopf barrier factors (L = J, spinless daughters)
   normint      -- Psi_ab, the inner bracket of Eq. 3 (MC sum over accepted events / N_gen)
   nll_grad     -- -lnL of Eq. 3 (extended form, footnote 2) and its gradient in V
   nll_double_sum -- Eq. 3 in its printed K^2 double-sum form, long double (pin only)
@@ -71,6 +73,13 @@ def _load():
             lib.orc_nll_double_sum.restype = ctypes.c_double
             lib.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_double]
             lib.orc_legendre.restype = ctypes.c_double
+            lib.orc_breakup_q.argtypes = [ctypes.c_double] * 3
+            lib.orc_breakup_q.restype = ctypes.c_double
+            lib.orc_barrier2.argtypes = [ctypes.c_int, ctypes.c_double]
+            lib.orc_barrier2.restype = ctypes.c_double
+            lib.orc_amplitudes_barrier.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_double, _i64, _fp, _i64, _dp]
+            lib.orc_amplitudes_barrier.restype = None
             _register_fit(lib)
             _lib = lib
     return _lib
@@ -129,6 +138,32 @@ def amplitudes(J, lam, M, W, kin, derivs: bool = False):
     lib.orc_amplitudes(K, _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), n,
                        _ptr(kin, _fp), n, _ptr(A, _dp), _ptr(dM, _dp), _ptr(dW, _dp))
     return (A, dM, dW) if derivs else A
+
+
+def breakup_q(m, m1, m2):
+    """Two-body breakup momentum q(m) for m -> m1 + m2 (0 at and below threshold)."""
+    return _load().orc_breakup_q(float(m), float(m1), float(m2))
+
+
+def barrier2(L, z):
+    """Squared Blatt-Weisskopf factor B_L^2 at z = (q R)^2, L <= 4, normalised to 1 at z -> inf."""
+    return _load().orc_barrier2(int(L), float(z))
+
+
+def amplitudes_barrier(J, lam, M, W, m1, m2, R, kin):
+    """A_a(Omega_i), complex128 [K][n], with the mass-dependent width and Blatt-Weisskopf
+    barrier factors of a decay into spinless daughters m1, m2 (L = J, radius R in GeV^-1)."""
+    lib = _load()
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    kin = np.ascontiguousarray(kin, dtype=np.float32)
+    K, n = J.shape[0], kin.shape[1]
+    A = np.zeros((K, n), dtype=np.complex128)
+    lib.orc_amplitudes_barrier(K, _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), float(m1), float(m2),
+                               float(R), n, _ptr(kin, _fp), n, _ptr(A, _dp))
+    return A
 
 
 def normint(A, w=None, n_gen=None):

@@ -22,6 +22,8 @@
  *   - the amplitude model A_a = BW_a(m) P_J(cos th) exp(i lambda phi) and its derivatives
  *     in the resonance mass and width (the paper gives no amplitude formula; the reading is
  *     the fixed-width, unit-peak relativistic Breit-Wigner with ordinary Legendre P_J).
+ *   - the same model with a mass-dependent width and Blatt-Weisskopf barrier factors for a
+ *     two-body decay X -> 1 + 2 into spinless daughters (orbital angular momentum L = J).
  *
  * Everything is the textbook definition evaluated in double precision, in the order the
  * definition states, with Neumaier-compensated accumulation of the long event sums.
@@ -100,6 +102,59 @@ void orc_amplitudes(int K, const int* J, const int* lam, const double* M, const 
             }
         }
     }
+}
+
+/* ---------- mass-dependent width and barrier factors ---------------------------------- */
+
+/* Breakup momentum of a state of mass m decaying into masses m1, m2, in its rest frame:
+ * q^2 = lambda(m^2, m1^2, m2^2) / (4 m^2) with the Kallen function
+ * lambda(x, y, w) = x^2 + y^2 + w^2 - 2xy - 2xw - 2yw.  Zero at and below threshold. */
+double orc_breakup_q(double m, double m1, double m2) {
+    if (!(m > m1 + m2)) return 0.0;
+    double x = m * m, y = m1 * m1, w = m2 * m2;
+    double lam = x * x + y * y + w * w - 2.0 * x * y - 2.0 * x * w - 2.0 * y * w;
+    return lam > 0.0 ? sqrt(lam) / (2.0 * m) : 0.0;
+}
+
+/* Squared Blatt-Weisskopf barrier factor of orbital angular momentum L <= 4 at z = (q R)^2,
+ * normalised to 1 as z -> infinity: B_L^2(z) = z^L / P_L(z) with the textbook polynomials
+ *   P_0 = 1, P_1 = 1 + z, P_2 = 9 + 3z + z^2, P_3 = 225 + 45z + 6z^2 + z^3,
+ *   P_4 = 11025 + 1575z + 135z^2 + 10z^3 + z^4
+ * (P_L(z) = |x^(L+1) h_L(x)|^2, h_L the outgoing spherical Hankel function, x^2 = z). */
+double orc_barrier2(int L, double z) {
+    switch (L) {
+        case 0: return 1.0;
+        case 1: return z / (1.0 + z);
+        case 2: return z * z / (9.0 + 3.0 * z + z * z);
+        case 3: return z * z * z / (225.0 + 45.0 * z + 6.0 * z * z + z * z * z);
+        case 4: return z * z * z * z / (11025.0 + 1575.0 * z + 135.0 * z * z + 10.0 * z * z * z + z * z * z * z);
+        default: return NAN;
+    }
+}
+
+/* Breit-Wigner of a resonance (M, Gamma_0) decaying to m1 + m2 with L = J and radius R:
+ *   Gamma(m) = Gamma_0 (M / m) (q / q0) B_L^2(q^2 R^2) / B_L^2(q0^2 R^2),   q0 = q(M),
+ *   BW(m)    = M Gamma_0 [B_L(q R) / B_L(q0 R)] / (M^2 - m^2 - i M Gamma(m)),
+ * which keeps the unit modulus at the peak, BW(M) = i, of the fixed-width form. */
+cplx orc_bw_barrier(double m, double M, double W, int L, double m1, double m2, double R) {
+    double q = orc_breakup_q(m, m1, m2), q0 = orc_breakup_q(M, m1, m2);
+    double b2 = orc_barrier2(L, q * q * R * R), b20 = orc_barrier2(L, q0 * q0 * R * R);
+    double Gm = W * (M / m) * (q / q0) * (b2 / b20);
+    cplx den = (M * M - m * m) - I * (M * Gm);
+    return (M * W * sqrt(b2 / b20)) / den;
+}
+
+/* A_a(Omega_i) with the barrier Breit-Wigner above, L_a = J_a; layout as orc_amplitudes. */
+void orc_amplitudes_barrier(int K, const int* J, const int* lam, const double* M, const double* W,
+                            double m1, double m2, double R, int64_t n, const float* kin, int64_t ld,
+                            double* A) {
+    cplx* Ac = (cplx*)A;
+    for (int a = 0; a < K; ++a)
+        for (int64_t i = 0; i < n; ++i) {
+            double m = kin[i], ct = kin[ld + i], ph = kin[2 * ld + i];
+            cplx ang = orc_legendre(J[a], ct) * cexp(I * (lam[a] * ph));
+            Ac[(int64_t)a * n + i] = orc_bw_barrier(m, M[a], W[a], J[a], m1, m2, R) * ang;
+        }
 }
 
 /* ---------- MC normalisation integral -------------------------------------------------- */

@@ -722,3 +722,90 @@ def test_polar_gradient_matches_finite_differences_of_the_oracle():
         fd_p = (f_polar(rho, pp) - f_polar(rho, pm)) / (2 * e)
         assert abs(fd_r - gr[a]) <= 1e-4 * max(1.0, abs(gr[a])), (a, fd_r, gr[a])
         assert abs(fd_p - gp[a]) <= 1e-4 * max(1.0, abs(gp[a])), (a, fd_p, gp[a])
+
+
+# ------------------------------------------------------------ barrier factors ------------
+# Mass-dependent width and Blatt-Weisskopf barrier factors (the amplitude model's reading for
+# a decay into two spinless daughters, L = J).
+
+def test_barrier_factor_against_spherical_hankel_functions():
+    # B_L^2(x^2) = 1 / (x^2 |h_L(x)|^2), h_L = j_L + i y_L (scipy), for L = 0..4
+    from scipy.special import spherical_jn, spherical_yn
+    for L in range(5):
+        for x in (0.03, 0.4, 1.0, 2.7, 8.0, 40.0):
+            h = spherical_jn(L, x) + 1j * spherical_yn(L, x)
+            ref = 1.0 / (x * x * abs(h) ** 2)
+            assert abs(oracle.barrier2(L, x * x) - ref) <= 1e-12 * ref, (L, x)
+    # limits: B_L^2 ~ z^L / ((2L-1)!!)^2 at small z, -> 1 at large z
+    for L, df in ((1, 1), (2, 3), (3, 15), (4, 105)):
+        z = 1e-6
+        assert abs(oracle.barrier2(L, z) / (z ** L / df ** 2) - 1.0) < 1e-4
+        assert abs(oracle.barrier2(L, 1e12) - 1.0) < 1e-9
+
+
+def test_breakup_momentum_against_two_body_kinematics():
+    # q from the daughter energy E_1 = (m^2 + m1^2 - m2^2) / (2m), q^2 = E_1^2 - m1^2
+    for m, m1, m2 in ((1.02, 0.4937, 0.4937), (2.5, 0.1396, 0.9383), (3.1, 0.0, 0.0), (1.5, 0.3, 1.1)):
+        E1 = (m * m + m1 * m1 - m2 * m2) / (2 * m)
+        ref = math.sqrt(E1 * E1 - m1 * m1)
+        assert abs(oracle.breakup_q(m, m1, m2) - ref) <= 1e-12 * max(ref, 1.0)
+    assert oracle.breakup_q(3.1, 0.0, 0.0) == 1.55
+    assert oracle.breakup_q(0.9, 0.4937, 0.4937) == 0.0  # below threshold
+    assert oracle.breakup_q(0.9874, 0.4937, 0.4937) == 0.0  # at threshold
+
+
+def _barrier_case(seed, n=400, J=(0, 1, 2, 3, 4), lam=(0, 1, 0, 1, 0)):
+    kin = inputs.kinematics(n, seed, 3)
+    M = np.array([1.3, 1.6, 1.9, 2.2, 2.5][:len(J)])
+    W = np.array([0.08, 0.12, 0.2, 0.1, 0.25][:len(J)])
+    return np.array(J), np.array(lam), M, W, kin
+
+
+def test_barrier_amplitudes_reduce_to_the_fixed_width_model():
+    # L = 0 with massless daughters: q = m/2, Gamma(m) = Gamma_0 (M/m)(m/M) = Gamma_0, B_0 = 1
+    J, lam, M, W, kin = _barrier_case(inputs.SEED_BASE + 50, J=(0, 0, 0), lam=(0, 1, -1))
+    for R in (0.5, 3.0, 20.0):
+        A = oracle.amplitudes_barrier(J, lam, M, W, 0.0, 0.0, R, kin)
+        A0 = oracle.amplitudes(J, lam, M, W, kin)
+        assert np.max(np.abs(A - A0)) <= 1e-13 * np.max(np.abs(A0))
+
+
+def test_barrier_amplitudes_small_and_large_radius_limits():
+    # R -> 0: B_L(q R)/B_L(q0 R) -> (q/q0)^L, so Gamma(m) -> Gamma_0 (M/m)(q/q0)^(2L+1) and the
+    # numerator -> M Gamma_0 (q/q0)^L.  R -> infinity: B_L -> 1, Gamma(m) -> Gamma_0 (M/m)(q/q0).
+    J, lam, M, W, kin = _barrier_case(inputs.SEED_BASE + 51)
+    m1 = m2 = 0.4937
+    m = kin[0].astype(np.float64)
+    q = np.sqrt(np.maximum(m * m / 4 - m1 * m1, 0.0))
+    for R, small in ((1e-4, True), (1e5, False)):
+        A = oracle.amplitudes_barrier(J, lam, M, W, m1, m2, R, kin)
+        for a in range(len(J)):
+            q0 = math.sqrt(M[a] ** 2 / 4 - m1 * m1)
+            r = q / q0
+            L = J[a]
+            G = W[a] * (M[a] / m) * (r ** (2 * L + 1) if small else r)
+            num = M[a] * W[a] * (r ** L if small else 1.0)
+            bw = num / (M[a] ** 2 - m * m - 1j * M[a] * G)
+            ang = eval_legendre(L, kin[1].astype(np.float64)) * np.exp(1j * lam[a] * kin[2].astype(np.float64))
+            assert np.max(np.abs(A[a] - bw * ang)) <= 1e-6 * max(1.0, np.max(np.abs(bw))), (R, a)
+
+
+def test_barrier_amplitudes_unit_peak_and_threshold():
+    m1, m2, R = 0.4937, 0.4937, 3.0
+    J = np.arange(5)
+    lam = np.zeros(5, dtype=int)
+    M = np.array([1.25, 1.5, 1.75, 2.0, 2.5])  # exact in float32
+    W = np.array([0.1, 0.15, 0.2, 0.05, 0.3])
+    for a in range(5):
+        kin = np.array([[M[a]], [1.0], [0.0]], dtype=np.float32)  # m = M, P_J(1) = 1, phi = 0
+        A = oracle.amplitudes_barrier(J, lam, M, W, m1, m2, R, kin)
+        assert abs(A[a, 0] - 1j) <= 1e-14
+    # at threshold q = 0: Gamma = 0 and, for L > 0, the amplitude vanishes like q^L
+    thr = np.float32(m1 + m2) + np.float32(1e-6)
+    kin = np.array([[thr], [1.0], [0.0]], dtype=np.float32)
+    A = oracle.amplitudes_barrier(J, lam, M, W, m1, m2, R, kin)
+    assert abs(A[0, 0]) > 0.01
+    assert np.all(np.abs(A[1:, 0]) < 1e-3)
+    kin = np.array([[0.9], [1.0], [0.0]], dtype=np.float32)  # below threshold: q = 0
+    A = oracle.amplitudes_barrier(J, lam, M, W, m1, m2, R, kin)
+    assert np.all(A[1:, 0] == 0) and A[0, 0] != 0
