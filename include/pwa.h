@@ -124,6 +124,23 @@ PWA_API pwa_status pwa_amplitudes(pwa_handle* h, const pwa_wave* waves, int K, c
                           int64_t n, int64_t ld, float* A, float* dA_dM, float* dA_dW,
                           void* stream);
 
+/* Decay amplitudes as pwa_amplitudes, with a mass-dependent width and Blatt-Weisskopf barrier
+ * factors for a resonance decaying into two spinless daughters of masses m1, m2 (GeV) with
+ * orbital angular momentum L = J of the wave and interaction radius R (GeV^-1).  The paper names
+ * A_a (Sec. 2, Eq. 1) without a formula; this is the usual refinement of the fixed-width form:
+ *   q(m)     = breakup momentum of m -> m1 + m2 (0 at and below threshold), q0 = q(M)
+ *   B_L(z)   = Blatt-Weisskopf factor at z = (q R)^2, normalised to 1 as z -> infinity
+ *   Gamma(m) = Gamma_0 (M / m) (q / q0) B_J^2(q R) / B_J^2(q0 R)
+ *   BW(m)    = M Gamma_0 [B_J(q R) / B_J(q0 R)] / (M^2 - m^2 - i M Gamma(m))   (BW(M) = i)
+ * A_a = BW_a(m) P_J(cos theta) exp(i lambda phi).  Single precision.
+ *   waves  host array [K] with J <= 4 and mass > m1 + m2
+ *   m1, m2 finite, >= 0;  R in (0, 100]
+ *   kin, A, layout and alignment as pwa_amplitudes (columns n..ld-1 of A set to zero)
+ * No intermediate overflows for m up to 100 GeV. */
+PWA_API pwa_status pwa_amplitudes_barrier(pwa_handle* h, const pwa_wave* waves, int K, double m1, double m2,
+                                          double R, const float* kin, int64_t n, int64_t ld, float* A,
+                                          void* stream);
+
 /* Monte-Carlo normalisation integral (Sec. 2, Eq. 3, inner bracket of the second term):
  *   Psi_ab = (1/n_gen) * sum_{j < n_mc} w_j A_a(j) conj(A_b(j))
  * summed in single precision per thread with compensated (double-single) carries, and

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <string>
 
+#include "barrier.cuh"
 #include "pwa_internal.cuh"
 
 namespace {
@@ -375,6 +376,51 @@ pwa_status pwa_amplitudes(pwa_handle* h, const pwa_wave* waves, int K, const flo
                                            reinterpret_cast<float2*>(dA_dM), reinterpret_cast<float2*>(dA_dW),
                                            h->sm_count, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "amplitude launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
+pwa_status pwa_amplitudes_barrier(pwa_handle* h, const pwa_wave* waves, int K, double m1, double m2, double R,
+                                  const float* kin, int64_t n, int64_t ld, float* A, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    pwa_status st = check_amp_layout(h, K, n, ld);
+    if (st != PWA_OK) return st;
+    if (!waves) return fail(h, PWA_ERR_INVALID_ARG, "waves is NULL");
+    if (ld > 0 && (!A || (n > 0 && !kin))) return fail(h, PWA_ERR_INVALID_ARG, "NULL kinematics or amplitude array");
+    if ((A && !aligned16(A)) || (kin && !aligned16(kin)))
+        return fail(h, PWA_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+    if (!(m1 >= 0.0) || !(m2 >= 0.0) || !std::isfinite(m1) || !std::isfinite(m2))
+        return fail(h, PWA_ERR_INVALID_ARG, "daughter masses must be finite and >= 0");
+    if (!(R > 0.0) || !(R <= 100.0)) return fail(h, PWA_ERR_INVALID_ARG, "radius R must be in (0, 100] GeV^-1");
+    pwa::WaveTable wt;
+    st = fill_waves(h, waves, K, &wt);
+    if (st != PWA_OK) return st;
+    pwa::BarrierTable bt;
+    const double msum = m1 + m2, mdif = std::fabs(m1 - m2);
+    bt.msum_hi = (float)msum;
+    bt.msum_lo = (float)(msum - (double)bt.msum_hi);
+    bt.mdif_hi = (float)mdif;
+    bt.mdif_lo = (float)(mdif - (double)bt.mdif_hi);
+    bt.R = (float)R;
+    bt.R2 = (float)(R * R);
+    for (int a = 0; a < K; ++a) {
+        const pwa_wave& w = waves[a];
+        if (w.J > pwa::BARRIER_LMAX)
+            return fail(h, PWA_ERR_INVALID_ARG, "wave %d: J = %d above %d for barrier factors", a, w.J, pwa::BARRIER_LMAX);
+        if (!(w.mass > msum)) return fail(h, PWA_ERR_INVALID_ARG, "wave %d: mass at or below the decay threshold", a);
+        // q0 = q(M) from the factorised Kallen function; B_J^2(q0^2 R^2) > 0 since q0 > 0
+        const double M = w.mass;
+        const double q0 = std::sqrt((M - msum) * (M + msum) * (M - mdif) * (M + mdif)) / (2.0 * M);
+        const double b20 = pwa::barrier2_host(w.J, q0 * q0 * R * R);
+        bt.num[a] = (float)(M * w.width / std::sqrt(b20));
+        bt.cw[a] = (float)(M * M * w.width / (q0 * b20));
+    }
+    for (int a = K; a < PWA_MAX_WAVES; ++a) bt.num[a] = bt.cw[a] = 0.f;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = pwa::launch_amp_barrier(wt, bt, kin, n, ld, reinterpret_cast<float2*>(A), h->sm_count,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "barrier amplitude launch");
     h->err.clear();
     return PWA_OK;
 }

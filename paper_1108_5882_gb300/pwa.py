@@ -73,6 +73,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.pwa_amplitudes.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, _i64, _i64, _vp, _vp,
                                        _vp, _vp]
         lib.pwa_amplitudes.restype = S
+        lib.pwa_amplitudes_barrier.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, _vp, _i64, _i64, _vp, _vp]
+        lib.pwa_amplitudes_barrier.restype = S
         lib.pwa_normint.argtypes = [_vp, _vp, ctypes.c_int, _i64, _i64, _vp, ctypes.c_double, _vp, _vp]
         lib.pwa_normint.restype = S
         lib.pwa_normint_from_kinematics.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, _i64, _i64, _vp,
@@ -245,6 +248,18 @@ class Handle:
             raise ValueError("kin and A must share the leading dimension")
         self._chk(self.lib.pwa_amplitudes(self.h, arr, K, _ptr(kin), int(n), int(ld), _ptr(A), _ptr(dA_dM),
                                           _ptr(dA_dW), _stream_ptr(stream)))
+
+    def pwa_amplitudes_barrier(self, waves, m1, m2, R, kin, n, A, stream=None):
+        """As pwa_amplitudes with a mass-dependent width and Blatt-Weisskopf barrier factors
+        (daughter masses m1, m2, L = J, radius R in GeV^-1)."""
+        _check_cuda(kin, "kin", torch.float32)
+        _check_cuda(A, "A", torch.complex64)
+        ld = A.shape[1]
+        if kin.shape[1] != ld:
+            raise ValueError("kin and A must share the leading dimension")
+        self._chk(self.lib.pwa_amplitudes_barrier(self.h, _wave_array(waves), len(waves), float(m1), float(m2),
+                                                  float(R), _ptr(kin), int(n), int(ld), _ptr(A),
+                                                  _stream_ptr(stream)))
 
     def pwa_normint(self, A_mc, n_mc, Psi, w=None, n_gen=None, stream=None):
         """A_mc complex64 [K][ld]; Psi complex128 [K][K] output; w float32 [n_mc] or None."""

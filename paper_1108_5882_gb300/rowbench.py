@@ -89,7 +89,7 @@ def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--rows", default="a1,a2,a3,a3i,a4,a5,a7,a7p,a7h,a8,a9")
+    ap.add_argument("--rows", default="a1,a1b,a2,a3,a3i,a4,a5,a7,a7p,a7h,a8,a9")
     ap.add_argument("--json", default=None)
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and one timed launch per kernel, no peak microbenchmark and 64 toys "
@@ -114,7 +114,7 @@ def main():
     seed = inputs.SEED_BASE + 2
     ws16 = inputs.wave_set_spread(16, seed)
     w16 = pwa.waves_from(ws16)
-    if rows & {"a1", "a2", "a3", "a5"}:
+    if rows & {"a1", "a1b", "a2", "a3", "a5"}:
         n_mc = 5_000_000
         kin_mc = torch.from_numpy(inputs.kinematics(n_mc, seed, 5)).cuda()
         A_mc = torch.empty((16, n_mc), dtype=torch.complex64, device="cuda")
@@ -128,6 +128,12 @@ def main():
         add("a1", "amplitudes + dA/dM + dA/dG, K=16, 5e6 events", sec, nbytes=n_mc * (12 + 3 * 8 * 16),
             flops=n_mc * 16 * 50.0)
         del dM, dG
+    if "a1b" in rows:
+        # mass-dependent widths and barrier factors (L = J, K+K- daughters, R = 3 GeV^-1)
+        wb = [(min(j, 4), l, m, w) for (j, l, m, w) in w16]
+        sec = T(lambda: h.pwa_amplitudes_barrier(wb, 0.4937, 0.4937, 3.0, kin_mc, n_mc, A_mc), R)
+        add("a1b", "amplitudes with mass-dependent widths and barrier factors, K=16, 5e6 events", sec,
+            nbytes=n_mc * (12 + 8 * 16), flops=n_mc * 16 * 40.0)
     Psi16 = torch.empty((16, 16), dtype=torch.complex128, device="cuda")
     if rows & {"a2", "a3", "a5"}:
         h.pwa_amplitudes(w16, kin_mc, n_mc, A_mc)
@@ -199,7 +205,7 @@ def main():
         add("a5", "streamed-normalisation -lnL + V and (M,G) gradient, K=16, 1e6+5e6", sec,
             nbytes=(N + n_mc) * (K + F) * 8, flops=(N + n_mc) * (16 * K + 4 * F + 12.0))
         del A, dA, dAm, kin
-    if rows & {"a1", "a2", "a3", "a5"}:
+    if rows & {"a1", "a1b", "a2", "a3", "a5"}:
         del A_mc, kin_mc
     if rows & {"a4", "a7", "a7p"}:
         K, N, P = 32, 2_000_000, 256

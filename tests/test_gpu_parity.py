@@ -98,6 +98,46 @@ def test_amplitudes_peak_and_all_spins(h):
     assert np.max(np.abs(A.cpu().numpy() - Ar)) <= 4e-6
 
 
+@pytest.mark.parametrize("K,n,ld,m1,m2,R", [(5, 10_001, 10_002, 0.4937, 0.4937, 3.0),
+                                             (16, 65_537, 65_540, 0.1396, 0.4937, 5.0),
+                                             (64, 3_001, 3_004, 0.0, 0.0, 1.0), (3, 1, 2, 0.4937, 0.4937, 0.2)])
+def test_amplitudes_barrier_parity(h, K, n, ld, m1, m2, R):
+    # mass-dependent widths and Blatt-Weisskopf barrier factors (L = J <= 4) against the oracle,
+    # with events below, at and just above the decay threshold
+    ws = inputs.wave_set_spread(K, SEED + 60 + K)
+    J = np.arange(K) % 5  # every L = J the barrier factors support
+    waves = [(int(j), int(l), float(M), float(W)) for j, l, M, W in zip(J, ws.lam, ws.M, ws.W)]
+    kin = inputs.kinematics(n, SEED + 60 + K, 6)
+    thr = np.float32(m1 + m2)
+    edge = np.array([0.5 * thr, thr, np.nextafter(thr, np.float32(9)), thr + np.float32(1e-3)], dtype=np.float32)
+    kin[0, :min(n, 4)] = edge[:min(n, 4)]
+    A = torch.full((K, ld), complex(7, 7), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes_barrier(waves, m1, m2, R, dev(padded(kin, ld)), n, A)
+    Ag = A.cpu().numpy()
+    Ar = oracle.amplitudes_barrier(J, ws.lam, ws.M, ws.W, m1, m2, R, kin)
+    err = np.abs(Ag[:, :n] - Ar) / np.maximum(1.0, np.abs(Ar))
+    assert np.max(err) <= 5e-6, np.max(err)
+    assert np.all(Ag[:, n:] == 0)  # padding columns zeroed
+    if m1 + m2 > 0 and n >= 4:
+        # below threshold q = 0: only the J = 0 waves survive; at it they vanish like q^J
+        assert np.all(Ag[J > 0, 0] == 0) and np.all(Ag[J == 0, 0] != 0)
+        assert np.all(np.abs(Ag[J > 0, 1:3]) < 1e-3)
+
+
+def test_amplitudes_barrier_reduce_to_the_fixed_width_kernel(h):
+    # L = 0 with massless daughters: Gamma(m) = Gamma_0 and B_0 = 1, so both kernels compute
+    # the fixed-width Breit-Wigner (to FP32 rounding)
+    from paper_1108_5882_gb300 import pwa
+    n = 20_000
+    waves = [(0, lam, 1.2 + 0.2 * a, 0.05 + 0.05 * a) for a, lam in enumerate((0, 1, -1, 2, 0, 1))]
+    kin = dev(inputs.kinematics(n, SEED + 61, 6))
+    A1 = torch.zeros((6, n), dtype=torch.complex64, device="cuda")
+    A2 = torch.zeros((6, n), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(waves, kin, n, A1)
+    h.pwa_amplitudes_barrier(waves, 0.0, 0.0, 2.0, kin, n, A2)
+    assert torch.max(torch.abs(A1 - A2)).item() <= 4e-6
+
+
 # ------------------------------------------------------------------- normalisation ------
 
 @pytest.mark.parametrize("K,n_mc,weighted", [(4, 50_000, False), (16, 30_001, False), (32, 9_999, True),
@@ -398,6 +438,13 @@ def test_invalid_arguments_are_rejected(h):
         h.pwa_nll_grad_incoherent(A5, 10, V, Psi, 1.0, nll)
     with pytest.raises(pwa.PWAError, match="n_gen"):
         h.pwa_normint_from_kinematics([(0, 0, 1.5, 0.1)] * 4, torch.zeros((3, 10), device="cuda"), 10, Psi, n_gen=0.0)
+    kin10 = torch.zeros((3, 10), device="cuda")
+    with pytest.raises(pwa.PWAError, match="J = 5"):
+        h.pwa_amplitudes_barrier([(5, 0, 1.5, 0.1)] * 4, 0.14, 0.14, 3.0, kin10, 10, A)
+    with pytest.raises(pwa.PWAError, match="threshold"):
+        h.pwa_amplitudes_barrier([(2, 0, 0.9, 0.1)] * 4, 0.4937, 0.4937, 3.0, kin10, 10, A)
+    with pytest.raises(pwa.PWAError, match="radius"):
+        h.pwa_amplitudes_barrier([(2, 0, 1.5, 0.1)] * 4, 0.4937, 0.4937, 0.0, kin10, 10, A)
 
 
 # ------------------------------------------------------------------- full sizes ---------
