@@ -110,7 +110,8 @@ def test_amplitudes_barrier_parity(h, K, n, ld, m1, m2, R):
     kin = inputs.kinematics(n, SEED + 60 + K, 6)
     thr = np.float32(m1 + m2)
     edge = np.array([0.5 * thr, thr, np.nextafter(thr, np.float32(9)), thr + np.float32(1e-3)], dtype=np.float32)
-    kin[0, :min(n, 4)] = edge[:min(n, 4)]
+    if m1 + m2 > 0:  # (with massless daughters the threshold is m = 0, outside any phase space)
+        kin[0, :min(n, 4)] = edge[:min(n, 4)]
     A = torch.full((K, ld), complex(7, 7), dtype=torch.complex64, device="cuda")
     h.pwa_amplitudes_barrier(waves, m1, m2, R, dev(padded(kin, ld)), n, A)
     Ag = A.cpu().numpy()
