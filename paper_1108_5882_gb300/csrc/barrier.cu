@@ -14,7 +14,8 @@
 // per thread: the kernel is bound by the HBM write stream of 8K bytes per event.
 //
 // Precision: FP32; the resonance mass and the daughter-mass sums enter as two-float values so
-// that M - m and m - (m1 + m2) are exact to the rounding of m.
+// that M - m and m - (m1 + m2) are exact to the rounding of m.  The per-wave reciprocal is
+// __fdividef's (within 2 ulp for the normal-range denominators M^2 - m^2 and M Gamma(m) give).
 #include "amp_model.cuh"
 #include "barrier.cuh"
 
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_amp_barrier(WaveTable wt, Barri
                     // BW = nu b / (dr - i MG),  dr = M^2 - m^2 from the two-float mass, MG = cw t
                     const float dr = ((Mh - m[k]) + Ml) * ((Mh + m[k]) + Ml);
                     const float mg = cw * t[k];
-                    const float sc = nu * b[k] / fmaf(dr, dr, mg * mg);
+                    const float sc = nu * b[k] * __fdividef(1.f, fmaf(dr, dr, mg * mg));  // <= 2 ulp
                     const float2 bw = make_float2(dr * sc, mg * sc);
                     out[k] = i0 + k < n ? cmul(bw, ang[k]) : make_float2(0.f, 0.f);
                 }
