@@ -1,6 +1,6 @@
 // Decay amplitudes A_a(Omega_i) = BW_a(m_i) * P_J(cos theta_i) * exp(i lambda phi_i).
 //
-// Paper: Sec. 2, Eq. 1 (A_a is the complex decay amplitude at phase-space point Omega) and
+// Paper: Sec. 2, Eq. 1 (A_a: wave a's complex amplitude at the phase-space point Omega) and
 // Sec. 3 ("facilities for amplitude calculation").  The paper prints no amplitude formula;
 // the model is the fixed-width relativistic Breit-Wigner with unit modulus at the peak,
 // BW(m) = M G / (M^2 - m^2 - i M G), times the ordinary Legendre polynomial P_J and the

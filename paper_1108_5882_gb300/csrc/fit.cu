@@ -2,9 +2,9 @@
 // production amplitudes V, many parameter sets at once.
 //
 // The paper's fits run sequentially through Minuit/Fumili (Sec. 4, "More control over the
-// fitters") and are repeated from many random starts to gain confidence in the global minimum
-// (Sec. 2 and Sec. 4, "Fits with large numbers of parameters").  Here every start of every fit
-// is an independent L-BFGS run whose state lives on the device:
+// fitters") and are rerun from many random starts so that the lowest minimum found can be
+// trusted as global (Sec. 2 and Sec. 4, "Fits with large numbers of parameters").  Here every
+// start of every fit is an independent L-BFGS run whose state lives on the device:
 //
 //   one iteration = one batched evaluation of f and g at the trial points of all starts
 //                 + k_lbfgs_step: per start, an Armijo test of the trial point; on acceptance
@@ -22,7 +22,7 @@
 // Im V_0 component of the gradient is frozen at zero.
 //
 // Coordinates (Sec. 4, "Fits with complex parameters": the minimiser sees real numbers, and
-// both the Cartesian and the polar representation of a complex parameter have drawbacks).
+// either real coordinate pair for a complex parameter has drawbacks).
 // Cartesian: x_2a = Re V_a, x_2a+1 = Im V_a.  Polar: x_2a = rho_a, x_2a+1 = phi_a with
 // V_a = rho_a exp(i phi_a); the gradient of pwa_nll_grad is carried over by the chain rule,
 //   d f / d rho = g_re cos phi + g_im sin phi,   d f / d phi = rho (g_im cos phi - g_re sin phi).
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
             s_action = finite ? 1 : 3;
         } else {
             // Armijo, or the approximate Wolfe conditions of Hager and Zhang (2005), which
-            // judge the step by phi' when f differences fall below the rounding of f itself:
+            // test the step by phi' when f differences fall below the rounding of f itself:
             // sigma phi'(0) <= phi'(alpha) <= (2 delta - 1) phi'(0), f(alpha) <= f(0) + eps |f(0)|
             const double f0 = st.f[p], g0 = st.gtd[p];
             const bool armijo = fnew <= f0 + 1e-4 * alpha * g0;

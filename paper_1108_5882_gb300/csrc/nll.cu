@@ -21,8 +21,8 @@
 //    sums of ln I.  k_nll_finalize then sums the chunk partials per start in order and adds
 //    the normalisation term in FP64.
 //
-// Sec. 2 precision remark: amplitudes in single precision, the final sum in double
-// precision with a tree-like summation order.  Here the per-thread sums are FP32 (gradient) or
+// Sec. 2 precision remark: FP32 amplitudes and per-event arithmetic, FP64 for the last sum,
+// added in a tree-like order.  Here the per-thread sums are FP32 (gradient) or
 // double-single (ln I) over a bounded number of events, warp sums a fixed tree; across warps
 // and blocks the single-set kernels sum exactly (integer fixed point) and the batched kernel
 // carries double-single pairs in a fixed order.

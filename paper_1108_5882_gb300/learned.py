@@ -1,10 +1,10 @@
 """Learned start proposer: an MLP maps the angular moments of a data sample to C candidate
 production-amplitude vectors, used as fit starts instead of (or before) random ones.
 
-The paper has no such part; it motivates it.  Fits are repeated from many random starts to gain
-confidence in the global minimum, which is "excessively time consuming" for many parameters
+The paper has no such part; it motivates it.  Fits are rerun from many random starts until
+the lowest minimum is trusted to be global, and that grows costly as the parameter count rises
 (Sec. 2, and Sec. 4 "Fits with large numbers of parameters").  The plain method (random
-multi-start) stays the fallback and the judge.
+multi-start) stays the fallback and decides which minimum is global.
 
 Everything runs in the library's kernels:
   features    pwa_moments (data) / pwa_toy_moments (toys drawn on the fly, never stored)
