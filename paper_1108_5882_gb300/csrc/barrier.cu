@@ -14,8 +14,9 @@
 // per thread: the kernel is bound by the HBM write stream of 8K bytes per event.
 //
 // Precision: FP32; the resonance mass and the daughter-mass sums enter as two-float values so
-// that M - m and m - (m1 + m2) are exact to the rounding of m.  The per-wave reciprocal is
-// __fdividef's (within 2 ulp for the normal-range denominators M^2 - m^2 and M Gamma(m) give).
+// that M - m and m - (m1 + m2) are exact to the rounding of m.  Divisions use __fdividef (within
+// 2 ulp for denominators in the normal range, which m, |g_J|^2 >= 1 and the Breit-Wigner
+// denominator are).
 #include "amp_model.cuh"
 #include "barrier.cuh"
 
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_amp_barrier(WaveTable wt, Barri
             // q^2 = (m - (m1+m2)) (m + (m1+m2)) (m - |m1-m2|) (m + |m1-m2|) / (4 m^2), 0 below threshold
             const float a = (m[k] - bt.msum_hi) - bt.msum_lo, b = (m[k] + bt.msum_hi) + bt.msum_lo;
             const float c = (m[k] - bt.mdif_hi) - bt.mdif_lo, d = (m[k] + bt.mdif_hi) + bt.mdif_lo;
-            rm[k] = 1.f / m[k];
+            rm[k] = __fdividef(1.f, m[k]);
             const float q2 = a > 0.f ? (a * b) * (c * d) * (0.25f * rm[k] * rm[k]) : 0.f;
             q[k] = sqrtf(q2);
             z[k] = q2 * bt.R2;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(PWA_THREADS) k_amp_barrier(WaveTable wt, Barri
                 }
                 if (lam < 0) ei = -ei;
                 ang[k] = make_float2(pcur[k] * er, pcur[k] * ei);
-                const float b2 = zj[k] / fmaf(gcr[k], gcr[k], gci[k] * gci[k]);
+                const float b2 = __fdividef(zj[k], fmaf(gcr[k], gcr[k], gci[k] * gci[k]));  // |g_J|^2 >= 1
                 b[k] = sqrtf(b2);
                 t[k] = q[k] * b2 * rm[k];
             }
