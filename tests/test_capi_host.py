@@ -83,3 +83,48 @@ def test_envelope_host_matches_oracle():
     c_orc = oracle.envelope(ws.M, ws.W, V.astype(np.complex128))
     assert abs(c_lib - c_orc) < 1e-6 * c_orc
     assert c_lib < float(np.sum(np.abs(V).astype(np.float64))) ** 2  # tighter than (sum |V|)^2
+
+
+def test_fit_default_options_and_their_binding_layout():
+    # pwa_fit_default_opts needs no device; the ctypes mirror of pwa_fit_opts must match the C
+    # layout field by field (a missing or misordered field would shift every later one)
+    from paper_1108_5882_gb300 import pwa
+    o = pwa.fit_opts()
+    assert (o.max_iter, o.history, o.gtol, o.check_every, o.gauge_fix, o.use_graph, o.polar) == \
+        (1000, 10, 1e-6, 20, 1, 1, 0)
+    src = open(os.path.join(ROOT, "include", "pwa.h")).read()
+    body = re.search(r"typedef struct pwa_fit_opts \{(.*?)\} pwa_fit_opts;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    c_fields = re.findall(r"\b(\w+)\s*;", body)
+    assert c_fields == [f for f, _ in pwa.pwa_fit_opts._fields_]
+    assert pwa.fit_opts(polar=1).polar == 1
+
+
+def test_barrier_recurrence_of_the_library_header_matches_the_oracle():
+    # the host/device barrier factor of csrc/barrier.cuh (Hankel recurrence), compiled here as
+    # plain C++ with g++, against the oracle's textbook polynomials for L = 0..4
+    import shutil
+    import subprocess
+    import tempfile
+    import oracle
+    if not shutil.which("g++"):
+        pytest.skip("no g++")
+    src = open(os.path.join(ROOT, "paper_1108_5882_gb300", "csrc", "barrier.cuh")).read()
+    fn = re.search(r"(__host__ __device__ inline double barrier2_host\(.*?\n\})", src, flags=re.S).group(1)
+    fn = fn.replace("__host__ __device__ ", "")
+    prog = "#include <cmath>\n#include <cstdio>\nusing std::sqrt;\n" + fn + """
+int main() {
+    const double zs[] = {1e-6, 0.01, 0.3, 1.0, 3.0, 10.0, 80.0, 1e4};
+    for (int L = 0; L <= 4; ++L)
+        for (double z : zs) std::printf("%d %.17g %.17g\\n", L, z, barrier2_host(L, z));
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        cpp, exe = os.path.join(d, "b.cpp"), os.path.join(d, "b")
+        open(cpp, "w").write(prog)
+        subprocess.run(["g++", "-O1", "-o", exe, cpp], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    for line in out.strip().splitlines():
+        L, z, v = line.split()
+        ref = oracle.barrier2(int(L), float(z))
+        assert abs(float(v) - ref) <= 1e-13 * ref + 1e-300, (L, z, v, ref)
