@@ -24,7 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SRC = [os.path.join(_HERE, f) for f in ("pwa_oracle.c", "pwa_oracle_gen.c", "pwa_oracle_fit.c")]
+_SRC = [os.path.join(_HERE, f) for f in ("pwa_oracle.c", "pwa_oracle_gen.c")]
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -37,7 +37,7 @@ _i64 = ctypes.c_int64
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, strict IEEE FP64)."""
-    srcs = [s for s in _SRC if os.path.exists(s)]
+    srcs = list(_SRC)
     newest = max(os.path.getmtime(s) for s in srcs)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
@@ -80,12 +80,13 @@ def _load():
             lib.orc_amplitudes_barrier.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, ctypes.c_double,
                                                    ctypes.c_double, ctypes.c_double, _i64, _fp, _i64, _dp]
             lib.orc_amplitudes_barrier.restype = None
-            _register_fit(lib)
+            _register_gen(lib)
             _lib = lib
     return _lib
 
 
-def _register_fit(lib):
+def _register_gen(lib):
+    # generator, moments and floating-shape functions (pwa_oracle_gen.c, pwa_oracle.c)
     u32p = ctypes.POINTER(ctypes.c_uint32)
     lib.orc_philox4x32.argtypes = [u32p, u32p, u32p]
     lib.orc_philox4x32.restype = None
