@@ -173,7 +173,8 @@ def main():
             flops=N * H * (16 * K + 4.0))
         del A, kin
     if "a7h" in rows:
-        # Hessian of -lnL (exact form: two Gram passes) for one set, K = 16, N = 1e6
+        # Hessian of -lnL for one set, K = 16, N = 1e6 (Fumili: one fused pass; exact: + the
+        # weighted normalisation-integral pass)
         K, N = 16, 1_000_000
         kin = torch.from_numpy(inputs.kinematics(N, seed, 4)).cuda()
         A = torch.empty((K, N), dtype=torch.complex64, device="cuda")
@@ -184,9 +185,11 @@ def main():
         for exact in (False, True):
             sec = T(lambda: h.pwa_hessian(A, N, V, Psi, float(N), Hm, exact=exact), R)
             D = 2 * K
-            # bytes: A read twice (vectors, exact Gram) + r written and read (2K complex rows)
-            nb = N * K * 8 * (2 if exact else 1) + 2 * N * D * 8
-            fl = N * 8.0 * D * (D + 1) / 2 + (N * 8.0 * K * (K + 1) / 2 if exact else 0.0)
+            # algorithmic bytes: A read once (Fumili); exact: A read again by the weighted Gram
+            # pass, and 1/I written and read.  flops: r_i (~14K + 4), the symmetric rank-1
+            # update D(D+1), exact: + the complex Gram 4K(K+1)
+            nb = N * K * 8 * (2 if exact else 1) + (8 * N if exact else 0)
+            fl = N * (14.0 * K + 4 + D * (D + 1)) + (N * 4.0 * K * (K + 1) if exact else 0.0)
             add("a7h", f"Hessian of -lnL ({'exact' if exact else 'Fumili'}), K={K}, N={N:.0e}", sec, nbytes=nb, flops=fl)
         del A, kin
     if "a5" in rows:
