@@ -12,6 +12,9 @@ Functions and the passages they follow:
   normint      -- Psi_ab, the inner bracket of Eq. 3 (MC sum over accepted events / N_gen)
   nll_grad     -- -lnL of Eq. 3 (extended form, footnote 2) and its gradient in V
   nll_double_sum -- Eq. 3 in its printed K^2 double-sum form, long double (pin only)
+  envelope, generate, candidates -- accept-reject toys from I of Eq. 1 (Philox4x32-10 candidates)
+  moments      -- per-mass-bin averages of the real Y_LM (features of the learned proposer)
+  nll_grad_shape, nll_shape_from_kin -- the objective with floating masses and widths (Sec. 2)
 """
 from __future__ import annotations
 
@@ -95,6 +98,9 @@ def _register_gen(lib):
     lib.orc_generate.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                  _i64, ctypes.c_double, _fp, _i64, _i64, _dp]
     lib.orc_generate.restype = ctypes.c_int64
+    lib.orc_candidates.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_uint64, ctypes.c_uint32, _i64,
+                                   _i64, _fp, _fp, _dp, _dp]
+    lib.orc_candidates.restype = None
     lib.orc_ylm_real.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
     lib.orc_ylm_real.restype = ctypes.c_double
     lib.orc_moments.argtypes = [_i64, _fp, _i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
@@ -307,6 +313,26 @@ def generate(J, lam, M, W, V, seed, stream, cand0, n_cand, C, max_out):
                           kin.shape[1], int(max_out), _ptr(mr, _dp))
     n_out = min(int(na), int(max_out))
     return np.ascontiguousarray(kin[:, :n_out]), int(na), float(mr[0])
+
+
+def candidates(J, lam, M, W, V, seed, stream, cand0, n_cand):
+    """Every candidate of an accept-reject range, for decision-by-decision checks: returns
+    (kin float32 [3][n_cand], u float32 [n_cand], I float64 [n_cand], s float64 [n_cand]) with I the
+    FP64 intensity of Eq. 1 at the candidate and s = sum_a |V_a||A_a| (the rounding scale of u)."""
+    lib = _load()
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    n_cand = int(n_cand)
+    kin = np.zeros((3, n_cand), dtype=np.float32)
+    u = np.zeros(n_cand, dtype=np.float32)
+    Iv = np.zeros(n_cand, dtype=np.float64)
+    s = np.zeros(n_cand, dtype=np.float64)
+    lib.orc_candidates(J.shape[0], _ptr(J, _ip), _ptr(lam, _ip), _ptr(M, _dp), _ptr(W, _dp), _ptr(V, _dp), int(seed),
+                       int(stream), int(cand0), n_cand, _ptr(kin, _fp), _ptr(u, _fp), _ptr(Iv, _dp), _ptr(s, _dp))
+    return kin, u, Iv, s
 
 
 # ------------------------------------------------------------------ floating masses/widths -----

@@ -122,6 +122,29 @@ int64_t orc_generate(int K, const int* J, const int* lam, const double* M, const
     return na;
 }
 
+/* Per-candidate view of the same accept-reject step, for judging a single-precision generator
+ * decision by decision: for candidates [cand0, cand0 + n_cand) the phase-space point (float SoA
+ * [3][n_cand]), the accept uniform u, the FP64 intensity I(Omega) of Eq. 1 and the magnitude
+ * sum s = sum_a |V_a| |A_a(Omega)| (>= |u|, the scale of the rounding error of the sum u). */
+void orc_candidates(int K, const int* J, const int* lam, const double* M, const double* W,
+                    const double* Vd, uint64_t seed, uint32_t stream, int64_t cand0, int64_t n_cand,
+                    float* kin, float* u_out, double* I_out, double* s_out) {
+    const cplx* V = (const cplx*)Vd;
+    for (int64_t k = 0; k < n_cand; ++k) {
+        float m, ct, ph, u;
+        orc_candidate(seed, stream, cand0 + k, &m, &ct, &ph, &u);
+        kin[k] = m;
+        kin[n_cand + k] = ct;
+        kin[2 * n_cand + k] = ph;
+        u_out[k] = u;
+        I_out[k] = intensity(K, J, lam, M, W, Vd, m, ct, ph);
+        double s = 0.0;
+        for (int a = 0; a < K; ++a)
+            s += cabs(V[a]) * cabs(orc_bw(m, M[a], W[a])) * fabs(orc_legendre(J[a], ct));
+        s_out[k] = s;
+    }
+}
+
 /* ---------- angular moments (features of the learned start proposer) ------------------ */
 
 /* Real spherical harmonics Y_LM(theta, phi), L <= 4, index k = L^2 + L + M, orthonormal on the

@@ -79,3 +79,16 @@ def polar_gradient(g, V):
     gr = gre * np.cos(phi) + gim * np.sin(phi)
     gp = rho * (gim * np.cos(phi) - gre * np.sin(phi))
     return gr, gp
+
+
+def fp32_decision_band(V, C, unif, I, s, K):
+    """Half-width of the band around the decision boundary unif * C = I inside which a single-
+    precision generator may decide either way, per candidate (unif: the accept uniforms).  The
+    kernel evaluates I from FP32 amplitudes (each within 4e-6 of the FP64 value, |A| <= 1: the
+    amplitude parity bound), sums u = sum_a V_a A_a in FP32 (<= 2K + 2 roundings of terms bounded
+    by s = sum_a |V_a||A_a|), squares it in FP32, and compares with unif * C in FP32 (C rounded to
+    float, one rounding of the product)."""
+    eps = 2.0 ** -24
+    du = np.sum(np.abs(V)) * 4e-6 + (2 * K + 2) * eps * s
+    dI = 2 * s * du + du * du + 2 * eps * s * s
+    return dI + 2 * eps * unif.astype(np.float64) * C

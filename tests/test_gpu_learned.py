@@ -9,6 +9,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_1108_5882_gb300 import inputs
+from problems import fp32_decision_band
 
 pytestmark = pytest.mark.gpu
 SEED = inputs.SEED_BASE + 5
@@ -60,7 +61,11 @@ def test_toy_moments_match_oracle_generator(h):
         n_cand = math.ceil(n_target * C / S)
         kin, na, mr = oracle.generate(ws.J, ws.lam, ws.M, ws.W, Vt, 99, 1000 + t, 0, n_cand, C, 10 * n_target)
         assert mr <= 1.0
-        assert abs(ng[t] - na) <= 2, (ng[t], na)  # accept decisions differ only at the FP32/FP64 boundary
+        # the counts may differ only by decisions inside the FP32 error band of I (the kernel
+        # takes its envelope and candidate count in FP64 on the device, as the oracle does)
+        _, u, I, s = oracle.candidates(ws.J, ws.lam, ws.M, ws.W, Vt, 99, 1000 + t, 0, n_cand)
+        in_band = np.abs(u.astype(np.float64) * C - I) <= fp32_decision_band(Vt, C, u, I, s, K)
+        assert abs(ng[t] - na) <= int(in_band.sum()), (ng[t], na, int(in_band.sum()))
         assert abs(na - n_target) < 6 * math.sqrt(n_target)
         ref = oracle.moments(kin).reshape(-1)
         assert np.max(np.abs(fg[t] - ref)) <= 2e-5, np.max(np.abs(fg[t] - ref))

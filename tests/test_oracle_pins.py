@@ -809,3 +809,164 @@ def test_barrier_amplitudes_unit_peak_and_threshold():
     kin = np.array([[0.9], [1.0], [0.0]], dtype=np.float32)  # below threshold: q = 0
     A = oracle.amplitudes_barrier(J, lam, M, W, m1, m2, R, kin)
     assert np.all(A[1:, 0] == 0) and A[0, 0] != 0
+
+
+# ---------------------------------------------------------------- Adam (learned proposer) ---
+
+def _fr(x):
+    return float(Fraction(x))
+
+
+def test_adam_two_steps_against_hand_derived_values():
+    # Kingma and Ba, Algorithm 1: two bias-corrected steps with b1 = b2 = lr = 1/2, eps = 1,
+    # derived by hand in exact rationals (tests/golden/adam_kingma_ba.json gives the derivation).
+    # Bias correction with b^(t-1), eps inside the square root, a swapped b1/b2 or a missing
+    # square root each change at least one stored value.
+    from oracle import mlp
+    with open(os.path.join(GOLDEN, "adam_kingma_ba.json")) as fh:
+        gold = json.load(fh)
+    p = np.array(gold["p0"], dtype=np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t in range(2):
+        g = np.array(gold["g"][t], dtype=np.float64)
+        p, m, v = mlp.adam(p, g, m, v, gold["lr"], gold["b1"], gold["b2"], gold["eps"], t + 1)
+        assert np.allclose(p, [_fr(x) for x in gold["p"][t]], rtol=0, atol=1e-15)
+        assert np.allclose(m, [_fr(x) for x in gold["m"][t]], rtol=0, atol=1e-15)
+        assert np.allclose(v, [_fr(x) for x in gold["v"][t]], rtol=0, atol=1e-15)
+
+
+def test_adam_limits():
+    # lr -> 0 leaves the parameters unchanged; at step 1 the bias-corrected moments are g and
+    # g^2 exactly, so the step is lr * g / (|g| + eps) whatever b1 and b2 are.
+    from oracle import mlp
+    g = np.random.default_rng(7).normal(size=200) * np.logspace(-3, 3, 200)
+    p0 = np.random.default_rng(8).normal(size=200)
+    z = np.zeros(200)
+    p, _, _ = mlp.adam(p0, g, z, z, 0.0, 0.9, 0.999, 1e-8, 1)
+    assert np.array_equal(p, p0)
+    for b1, b2 in ((0.9, 0.999), (0.5, 0.25)):
+        p, m, v = mlp.adam(p0, g, z, z, 1e-2, b1, b2, 1e-3, 1)
+        step = 1e-2 * g / (np.abs(g) + 1e-3)
+        assert np.all(np.abs((p0 - p) - step) <= 1e-14 * np.abs(step) + 4e-16 * np.abs(p0))
+        assert np.allclose(m, (1 - b1) * g, rtol=1e-15) and np.allclose(v, (1 - b2) * g * g, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- accept-reject generator ---
+
+def _grid_kin(m, ct, ph):
+    mm, cc, pp = np.meshgrid(m, ct, ph, indexing="ij")
+    return np.ascontiguousarray(np.stack([mm.ravel(), cc.ravel(), pp.ravel()]).astype(np.float32))
+
+
+def _grid_intensity(ws, V, kin):
+    A = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin)
+    return np.abs(np.asarray(V, dtype=np.complex128) @ A) ** 2
+
+
+def test_envelope_bounds_the_intensity_on_a_dense_grid():
+    # The accept-reject envelope C must bound I = |sum_a V_a A_a|^2 (Eq. 1) everywhere on the
+    # phase space.  I is evaluated by the amplitude function alone on a dense (m, cos theta, phi)
+    # grid that includes every resonance mass and the cos(theta) = +-1 edges where |P_J| = 1.
+    # An envelope that clamps the mass to the wrong interval end, or drops |V_a|, falls below
+    # the grid maximum somewhere.
+    for K, seed in ((4, 11), (16, 12), (7, 13)):
+        ws = inputs.wave_set_plain(seed) if K == 4 else inputs.wave_set_spread(K, seed)
+        V = inputs.production_amplitudes(K, seed).astype(np.complex128)
+        C = oracle.envelope(ws.M, ws.W, V)
+        m = np.unique(np.concatenate([np.linspace(0.99, 3.0, 1201), ws.M, ws.M + 1e-4, ws.M - 1e-4]))
+        ct = np.linspace(-1.0, 1.0, 41)
+        ph = np.linspace(0.0, 2 * np.pi, 48, endpoint=False)
+        Imax = _grid_intensity(ws, V, _grid_kin(m, ct, ph)).max()
+        assert Imax <= C, (K, Imax, C)
+        assert Imax >= 0.05 * C  # the bound is not vacuous
+
+
+def test_envelope_is_attained_where_the_waves_align():
+    # Two waves of the same (J, lambda), mass and width with V in phase: I = (|V_0| + |V_1|)^2
+    # |BW|^2 |P_J|^2 peaks at m = M, cos(theta) = 1 at exactly the envelope value.  One wave:
+    # C = |V|^2.  The grid maximum must reach C (to the float32 rounding of m = M).
+    ws = inputs.WaveSet(np.array([2, 2], np.int32), np.array([1, 1], np.int32), np.array([1.7, 1.7]),
+                        np.array([0.1, 0.1]))
+    V = np.array([0.7 * np.exp(0.4j), 1.3 * np.exp(0.4j)])
+    C = oracle.envelope(ws.M, ws.W, V)
+    assert abs(C - 4.0) < 1e-12
+    kin = _grid_kin(np.array([1.7]), np.array([1.0]), np.linspace(0, 6, 7))
+    assert np.all(np.abs(_grid_intensity(ws, V, kin) - C) <= 1e-6 * C)
+    one = inputs.WaveSet(ws.J[:1], ws.lam[:1], ws.M[:1], ws.W[:1])
+    assert abs(oracle.envelope(one.M, one.W, V[:1]) - abs(V[0]) ** 2) < 1e-12
+
+
+def _bin_integrals(ws, V, edges, axis, nq=16):
+    """Integral of I over each bin of `axis` (0 = m, 1 = cos theta, 2 = phi) and the whole range
+    of the other two, by composite Gauss-Legendre quadrature in m (nq nodes on every sub-interval
+    of at most 0.01 GeV, a fifth of the narrowest width) and in a cos(theta) or phi bin, Gauss-
+    Legendre at 6 nodes over the full cos(theta) range (exact: I is a polynomial of degree <= 4
+    in cos(theta) for J <= 2) and the trapezoid rule at 8 nodes over the full phi range (exact
+    for the trigonometric degree |lambda_a - lambda_b| <= 1), with I from the amplitude function."""
+    def gauss(lo, hi, q):
+        xq, wq = np.polynomial.legendre.leggauss(q)
+        return 0.5 * (hi - lo) * xq + 0.5 * (hi + lo), 0.5 * (hi - lo) * wq
+
+    def composite(lo, hi, q, h):
+        k = max(1, int(math.ceil((hi - lo) / h - 1e-9)))
+        parts = [gauss(lo + (hi - lo) * i / k, lo + (hi - lo) * (i + 1) / k, q) for i in range(k)]
+        return np.concatenate([x for x, _ in parts]), np.concatenate([w for _, w in parts])
+
+    out = []
+    for b in range(len(edges) - 1):
+        m_rng = (edges[b], edges[b + 1]) if axis == 0 else (inputs.M_LO, inputs.M_HI)
+        nodes = [composite(*m_rng, nq, 0.01)]
+        nodes.append(gauss(edges[b], edges[b + 1], nq) if axis == 1 else gauss(-1.0, 1.0, 6))
+        if axis == 2:
+            nodes.append(gauss(edges[b], edges[b + 1], nq))
+        else:
+            nodes.append((2 * np.pi * np.arange(8) / 8, np.full(8, 2 * np.pi / 8)))
+        Ig = _grid_intensity(ws, V, _grid_kin(*(x for x, _ in nodes)))
+        Ig = Ig.reshape(*(len(x) for x, _ in nodes))
+        out.append(np.einsum("ijk,i,j,k->", Ig, *(w for _, w in nodes)))
+    return np.array(out)
+
+
+def test_generator_sample_follows_the_intensity():
+    # The accepted sample of the oracle's accept-reject must be distributed as I (Eq. 1) on the
+    # flat phase space: chi^2 of the m, cos(theta) and phi histograms of 1.05e6 events against
+    # the bin integrals of I by quadrature, each with p > 1e-4, and the number accepted against
+    # its binomial expectation n_cand <I> / C within 5 sigma.  A reversed comparison, an
+    # envelope below max I, or a wrong scale of u or C fails one of them.
+    from scipy.stats import chi2
+    seed = inputs.SEED_BASE + 1
+    ws = inputs.wave_set_plain(seed)
+    V = inputs.production_amplitudes(4, seed).astype(np.complex128)
+    C = oracle.envelope(ws.M, ws.W, V)
+    n_cand = 20_000_000
+    kin, na, _ = oracle.generate(ws.J, ws.lam, ws.M, ws.W, V, 4242, 1, 0, n_cand, C, n_cand)
+    assert na > 1_000_000
+    vol = (inputs.M_HI - inputs.M_LO) * 2.0 * 2 * np.pi
+    for axis, edges in ((0, np.linspace(inputs.M_LO, inputs.M_HI, 41)), (1, np.linspace(-1, 1, 21)),
+                        (2, np.linspace(0, 2 * np.pi, 17))):
+        integ = _bin_integrals(ws, V, edges, axis)
+        if axis == 0:
+            # quadrature converged: doubling the nodes moves no bin by more than 1e-6 of itself
+            assert np.max(np.abs(_bin_integrals(ws, V, edges, 0, nq=32) / integ - 1)) < 1e-6
+            p_acc = integ.sum() / vol / C
+            sigma = math.sqrt(n_cand * p_acc * (1 - p_acc))
+            assert abs(na - n_cand * p_acc) < 5 * sigma, (na, n_cand * p_acc, sigma)
+        obs, _ = np.histogram(kin[axis].astype(np.float64), bins=edges)
+        exp = na * integ / integ.sum()
+        stat = float(np.sum((obs - exp) ** 2 / exp))
+        assert chi2.sf(stat, len(exp) - 1) > 1e-4, (axis, stat, len(exp) - 1)
+
+
+def test_candidate_view_reproduces_the_generator():
+    # orc_candidates (the per-candidate view the GPU generator tests use) takes the same
+    # decisions as orc_generate: accepted iff u * C < I, in candidate order.
+    seed = inputs.SEED_BASE + 2
+    ws = inputs.wave_set_spread(16, seed)
+    V = inputs.production_amplitudes(16, seed).astype(np.complex128)
+    C = oracle.envelope(ws.M, ws.W, V)
+    kin_c, u, I, s = oracle.candidates(ws.J, ws.lam, ws.M, ws.W, V, 77, 3, 1000, 50_000)
+    kin, na, mr = oracle.generate(ws.J, ws.lam, ws.M, ws.W, V, 77, 3, 1000, 50_000, C, 50_000)
+    acc = u.astype(np.float64) * C < I
+    assert acc.sum() == na and np.array_equal(kin_c[:, acc], kin)
+    assert abs(mr - (I / C).max()) < 1e-15 and np.all(s * s >= I * (1 - 1e-12))
