@@ -1,13 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of the PWA likelihood hot path on GB300 (one JSON line on rank 0).
 
-Workload (default "scale"): K=16 waves (J in {0,2,4} x lambda in {0,1}, masses spread over
-1.3-2.8 GeV), N_data = 1e6 events drawn on the GPU by accept-reject from I under a seeded V,
-N_MC = 5e6 flat phase-space events, complex64 amplitudes.  Amplitudes and Psi are computed once
-(masses and widths fixed: Sec. 2 of the paper, the bracket and per-event terms can be
-pre-calculated), then one step is one fit-iteration evaluation of -lnL and its gradient at a
-new V (the data-event sum, the normalisation term and the deterministic grid reduction: one
-launch of the streaming kernel).
+Workload (default "multistart", the largest single-GPU configuration): K=32 waves (J in
+{0,2,4} x lambda in {0,1}, masses spread over 1.3-2.8 GeV), N_data = 2e6 events drawn on the GPU
+by accept-reject from I under a seeded V, N_MC = 1e7 flat phase-space events, complex64
+amplitudes, P = 256 parameter sets (|V| U[0,2], arg V U[0,2pi)) evaluated together.
+Amplitudes and Psi are computed once (masses and widths fixed: Sec. 2 of the paper, the
+bracket and per-event terms can be pre-calculated); one step is one multistart-iteration
+evaluation of -lnL and its gradient at all P sets (the batched event x wave x set contraction,
+the normalisation term and the fixed-order reduction).  "scale" (K=16, N=1e6, P=1) and
+"plain" (K=4, N=1e4, P=1) give the other configurations' lines.
 
 Metric: event x parameter-set NLL+grad evaluations per second = N_data * P / step time.
   value     device time of the steps (CUDA events on the launching stream), inputs resident in
@@ -15,11 +17,14 @@ Metric: event x parameter-set NLL+grad evaluations per second = N_data * P / ste
   e2e       the same metric through the C ABI from HOST buffers: each step copies the data and MC
             kinematics from pinned host memory, recomputes amplitudes and Psi, evaluates -lnL
             and its gradient, and reads nll and the gradient back.
-  roofline  the dominant kernel (k_nll_stream) against the measured HBM copy bandwidth:
-            algorithmic bytes per launch = N_data * K * 8 (each complex64 amplitude read once).
-  cpu_baseline  the FP64 oracle (single-threaded C) on a bounded sample of the same workload.
+  roofline  the dominant kernel against its roof: P = 1, the streaming kernel against the
+            measured HBM copy bandwidth (N_data * K * 8 bytes per launch); P > 1, the batched
+            contraction's (16K + 12) flop per (event, set) against the FFMA rate measured in the
+            same run (FP32 SIMT shapes) or against the emulated-FP32 tensor peak (tensor-core shape).
+  cpu_baseline  the FP64 oracle (single-threaded C) on all N_data events of the workload and a
+            stated fraction of its parameter sets, extrapolated linearly to a full iteration.
 
---impl reference times the oracle as the reference arm on this workload.
+--impl reference times the oracle as the reference arm on a bounded sample of this workload.
 Under torchrun (N > 1) every rank evaluates its own replica (independent fits, no collective
 on the data path): weak scaling, value = all ranks' units / max time over ranks.
 """
@@ -30,7 +35,9 @@ import ctypes
 import json
 import math
 import os
+import platform
 import statistics
+import subprocess
 import sys
 import threading
 import time
@@ -433,10 +440,10 @@ def run_ours(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(wl_name, n_sample, rank=0):
-    """A bounded sample of the workload for the oracle: first n_sample events (oracle amplitudes
-    of the same flat/accept-reject recipe are not needed for timing; the oracle consumes
-    complex64 amplitudes exactly like the GPU path)."""
+def oracle_sample(wl_name, n_sample, n_sets=4):
+    """The first n_sample events of the workload's wave set for the oracle, with n_sets of its
+    parameter sets.  The events are flat phase-space points (the oracle's cost does not depend on
+    where they lie; it consumes complex64 amplitudes exactly like the GPU path)."""
     import oracle
     from paper_1108_5882_gb300 import inputs
     K, N, NMC, P, seed = WORKLOADS[wl_name]
@@ -449,15 +456,36 @@ def oracle_sample(wl_name, n_sample, rank=0):
     if P == 1:
         V = V_true[None, :]
     else:
-        V = inputs.starts(min(P, 4), K, seed)
+        V = inputs.starts(min(P, n_sets), K, seed)
     return A, V, Psi, N, P
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform module)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(wl, seconds):
+    """The oracle on every data event of the workload and min(P, 4) of its parameter sets, repeated
+    for about `seconds`; a full iteration (all P sets) is extrapolated linearly in the sets."""
     import oracle
     name = [k for k, v in WORKLOADS.items() if v[0] == wl["K"] and v[1] == wl["N"]][0]
-    n_s = 250_000 if wl["P"] == 1 else 50_000
-    A, V, Psi, N, P = oracle_sample(name, n_s)
+    K, N, NMC, P, seed = WORKLOADS[name]
+    A, V, Psi, _, _ = oracle_sample(name, N, n_sets=min(P, 4))
     evals = 0
     t0 = time.perf_counter()
     while True:
@@ -466,9 +494,15 @@ def cpu_baseline(wl, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": A.shape[1] * V.shape[0] * evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{evals} FP64 -lnL+gradient evaluations of the first {A.shape[1]} events x {V.shape[0]} "
-                      f"parameter set(s) of the workload (K={A.shape[0]}), {dt:.1f} s"}
+    ps = V.shape[0]
+    full_s = dt / evals * P / ps
+    sample = (f"{evals} FP64 -lnL+gradient evaluations of all {A.shape[1]} data events x {ps} of the {P} parameter "
+              f"sets (K={K}), {dt:.1f} s")
+    if ps < P:
+        sample += f"; one full iteration ({P} sets) extrapolated linearly from {ps}/{P} of the sets: {full_s:.1f} s"
+    return {"value": A.shape[1] * ps * evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "full_iteration_s": full_s,
+            "full_iteration_extrapolated": ps < P}
 
 
 def run_reference(args, world, rank):
@@ -477,8 +511,8 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     K, N, NMC, P, seed = WORKLOADS[args.workload]
-    n_s = 100_000 if P == 1 else 20_000
-    A, V, Psi, _, _ = oracle_sample(args.workload, n_s)
+    n_s = min(N, 100_000 if P == 1 else 250_000)
+    A, V, Psi, _, _ = oracle_sample(args.workload, n_s, n_sets=4)
     for _ in range(args.warmup):
         oracle.nll_grad(A, V, Psi, n_factor=float(N))
     t0 = time.perf_counter()
@@ -486,8 +520,9 @@ def run_reference(args, world, rank):
         oracle.nll_grad(A, V, Psi, n_factor=float(N))
     dt = time.perf_counter() - t0
     value = A.shape[1] * V.shape[0] * args.steps / dt
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"each step: FP64 -lnL+gradient of the first {A.shape[1]} events x {V.shape[0]} set(s)"}
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"each step: FP64 -lnL+gradient of the first {A.shape[1]} of {N} events x {V.shape[0]} of "
+                     f"{P} set(s)"}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -501,10 +536,10 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="multistart", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -171,8 +171,9 @@ PWA_API pwa_status pwa_normint_from_kinematics(pwa_handle* h, const pwa_wave* wa
  *   n_factor  the factor on the normalisation term (the number of data events for the
  *             extended likelihood; 1.0 gives Eq. 3 exactly as printed)
  *   nll    double [P] output (+inf for a set that met I_i <= 0 or a non-finite intensity)
- * Event sums run in single precision per thread, then double-single across threads and
- * blocks in a fixed order (deterministic: identical inputs give identical bits).
+ * Event sums run in single precision per thread (ln I in double-single); across threads and
+ * blocks they are combined exactly in 64-bit integer fixed point for P = 1, and in double-single
+ * along a fixed-order tree for P > 1.  Either way identical inputs give identical bits.
  * For P > 1 the autotuner may pick the tensor-core shape (pwa_batched_shape() == 4): FP32
  * products emulated by three TF32 products and accumulated in FP32 in tensor memory.  It meets
  * the same tolerances (1e-5 of the -lnL scale, 1e-4 of the gradient scale) but its error at a
@@ -318,13 +319,13 @@ PWA_API pwa_status pwa_nll_grad_shape(pwa_handle* h, const float* A, const float
 
 /* Fits with floating resonance masses and widths, many channels (independent fits of uneven
  * wave and event counts) at once.  Sec. 2: with floating shape parameters the amplitudes are
- * recomputed every iteration and the MC normalisation is summed anew (pwa_nll_grad_shape);
- * Sec. 4: at least three or four free parameters per resonance.  One start per channel:
- * x = (Re V, Im V, theta), theta the floating masses/widths; each iteration recomputes the
- * floating waves' amplitudes and derivatives for data and MC from the device trial point,
- * evaluates the streamed likelihood and takes one L-BFGS step (widths and masses kept above
- * 1e-3 GeV by a fraction-to-the-boundary step limit).  The channels' chains run on parallel
- * streams captured into one CUDA graph per check_every iterations. */
+ * recomputed every iteration and the MC normalisation is summed anew; Sec. 4: at least three or
+ * four free parameters per resonance.  One start per channel: x = (Re V, Im V, theta), theta the
+ * floating masses/widths.  One iteration is two launches for all channels together: the
+ * persistent multi-channel evaluation of pwa_nll_grad_uneven (every amplitude recomputed from the
+ * kinematics at the device trial point) and one L-BFGS step per channel (widths and masses kept
+ * above 1e-3 GeV by a fraction-to-the-boundary step limit); check_every iterations are replayed
+ * as one captured CUDA graph between host convergence checks. */
 typedef struct pwa_shape_fit_desc {
     const pwa_wave* waves;      /* HOST [K]: J, lambda and the starting mass/width of each wave */
     int K;
@@ -340,16 +341,59 @@ typedef struct pwa_shape_fit_desc {
     int F;                      /* floating parameters, 0..PWA_MAX_FLOAT, 2K + F <= 128 */
     const int* float_wave;      /* HOST [F]: wave index of each floating parameter */
     const int* float_kind;      /* HOST [F]: 0 = mass, 1 = width */
-    float* A;                   /* work: complex float [K][ld] (device, overwritten) */
-    float* A_mc;                /* work: complex float [K][ld_mc] */
-    float* dA;                  /* work: complex float [F][ld] */
-    float* dA_mc;               /* work: complex float [F][ld_mc] */
+    float* A;                   /* unused (may be NULL): the amplitudes are recomputed on chip */
+    float* A_mc;                /* unused (may be NULL) */
+    float* dA;                  /* unused (may be NULL) */
+    float* dA_mc;               /* unused (may be NULL) */
     const float* V0;            /* complex float [K] starting V (device) */
     double* x_out;              /* double [2K + F] result (Re V_0, Im V_0, ..., theta) or NULL */
 } pwa_shape_fit_desc;
 
 PWA_API pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, int n_fits,
                                        const pwa_fit_opts* opts, pwa_fit_result* results,
+                                       void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Many independent channels (fits of uneven wave and event counts) with floating resonance
+ * masses and widths, evaluated together in ONE persistent kernel launch (Sec. 2: repeated fits,
+ * and shape parameters that float, so that neither the MC bracket of Eq. 3 nor the per-event
+ * products can be precomputed; Sec. 4: fits with many free parameters).  For each channel the
+ * objective and gradient are those of pwa_nll_grad_shape,
+ *   f = -sum_i ln|u_i|^2 + (n_factor / n_gen) sum_j w_j |u_j|^2,  u = sum_a V_a A_a,
+ * with every amplitude A_a recomputed inside the kernel from the kinematics (the model of
+ * pwa_amplitudes), the floating masses and widths taken from theta.  Nothing is stored per
+ * event besides the caller's kinematics. */
+typedef struct pwa_uneven_channel {
+    const pwa_wave* waves;      /* HOST [K]: J, lambda, mass, width (floating ones: see theta) */
+    int K;                      /* 1..PWA_MAX_WAVES */
+    const float* kin;           /* data kinematics float [3][ld] (device, 16-byte aligned) */
+    int64_t n;
+    int64_t ld;                 /* even, >= n */
+    const float* kin_mc;        /* MC kinematics float [3][ld_mc] (device, 16-byte aligned) */
+    int64_t n_mc;
+    int64_t ld_mc;
+    const float* w_mc;          /* float [n_mc] acceptance flags / weights, or NULL */
+    double n_gen;               /* generated MC events (> 0) */
+    double n_factor;            /* factor on the normalisation term (N_data for the extended form) */
+    int F;                      /* floating shape parameters, 0..PWA_MAX_FLOAT */
+    const int* float_wave;      /* HOST [F]: wave of each floating parameter */
+    const int* float_kind;      /* HOST [F]: 0 = mass, 1 = width (each (wave, kind) at most once) */
+} pwa_uneven_channel;
+
+/* f and the gradient in (V, theta) of n_ch channels in one launch.  Packed device arrays, channel c
+ * at the running offset of the channels before it:
+ *   V      complex float [sum_c K_c]           production amplitudes
+ *   theta  double [sum_c F_c]                  current values of the floating masses / widths
+ *                                              (> 0; may be NULL when no channel has F > 0)
+ *   nll    double [n_ch]                       output (+inf for a channel that met I_i <= 0)
+ *   grad   double [sum_c (2 K_c + F_c)]        output: (Re, Im) pairs of 2 df/dconj(V_a) for the
+ *                                              K_c waves in the caller's order, then df/dtheta_q
+ * The kernel walks a device work list of (channel, event range) items; each item's double-single
+ * sums go to a slot of their own and the block that finishes a channel's last item sums its slots
+ * in a fixed order, so results are deterministic.  The work list is uploaded when the channel
+ * descriptors differ from the previous call's (then the call is not capturable). */
+PWA_API pwa_status pwa_nll_grad_uneven(pwa_handle* h, const pwa_uneven_channel* channels, int n_ch,
+                                       const float* V, const double* theta, double* nll, double* grad,
                                        void* stream);
 
 /* ---------------------------------------------------------------------------------------
@@ -413,15 +457,18 @@ PWA_API pwa_status pwa_mlp_to_bf16(pwa_handle* h, const double* x, uint16_t* y, 
 
 /* -lnL and its gradient for ONE parameter set (P = 1) with no device allocation at all: no
  * handle, no workspace, no cudaMalloc / cudaFree, for callers that cannot allocate device
- * memory (inside a stream capture they do not own, under a memory manager that forbids
- * allocation after start-up, or as a plug-in of a program that owns all device memory).  The
- * paper has no counterpart; this is an interface convenience.
+ * memory (under a memory manager that forbids allocation after start-up, as a plug-in of a
+ * program that owns all device memory, or in a latency-critical loop that must not take the
+ * allocator's locks and implicit synchronisation).  The paper has no counterpart; this is an
+ * interface convenience.
  *   Arguments, layouts and results as pwa_nll_grad with P = 1, on the CURRENT device.
- *   Scratch: a static device array of 1,056,768 + 256 bytes compiled into the library (held
+ *   Scratch: a static device array of 1,056,768 + 8,448 bytes compiled into the library (held
  *   by every GPU that loads it until exit) supports K <= PWA_MAX_WAVES and at most 1024 blocks
  *   per launch; larger K is rejected with PWA_ERR_INVALID_ARG (message via pwa_last_error(NULL)).
- *   The first call on a device looks up the scratch's device address (cudaGetSymbolAddress);
- *   make that first call before any stream capture.
+ *   The first call in each CUDA context looks up the scratch's device address in that context
+ *   (cudaGetSymbolAddress; keyed by the driver's context id, so a context made after
+ *   cudaDeviceReset, or another context current on the device, gets its own lookup); make that
+ *   first call before any stream capture.
  *   Every call shares the scratch: calls ordered on one stream are safe (each call clears the
  *   scratch's counter and flag words on its stream), calls that overlap on the GPU race.
  *   A set that meets I_i <= 0 or a non-finite intensity gets nll = +inf and a zero gradient. */

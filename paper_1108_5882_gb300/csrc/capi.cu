@@ -234,6 +234,68 @@ pwa_status grow_fitws(pwa_handle* h, size_t need) {
     return PWA_OK;
 }
 
+// Arguments of one channel of the multi-channel (uneven) evaluation.
+pwa_status check_uneven_channel(pwa_handle* h, const pwa_uneven_channel& d, int c) {
+    pwa_status st = check_amp_layout(h, d.K, d.n, d.ld);
+    if (st == PWA_OK) st = check_amp_layout(h, d.K, d.n_mc, d.ld_mc);
+    if (st != PWA_OK) return fail(h, st, "channel %d: %s", c, h->err.c_str());
+    if (!d.waves) return fail(h, PWA_ERR_INVALID_ARG, "channel %d: waves NULL", c);
+    pwa::WaveTable wt;
+    st = fill_waves(h, d.waves, d.K, &wt);
+    if (st != PWA_OK) return fail(h, st, "channel %d: %s", c, h->err.c_str());
+    if (d.F < 0 || d.F > PWA_MAX_FLOAT || (d.F > 0 && (!d.float_wave || !d.float_kind)))
+        return fail(h, PWA_ERR_INVALID_ARG, "channel %d: F out of range or NULL float_wave/float_kind", c);
+    for (int q = 0; q < d.F; ++q) {
+        if (d.float_wave[q] < 0 || d.float_wave[q] >= d.K || (d.float_kind[q] != 0 && d.float_kind[q] != 1))
+            return fail(h, PWA_ERR_INVALID_ARG, "channel %d: bad floating parameter %d", c, q);
+        for (int r = 0; r < q; ++r)
+            if (d.float_wave[r] == d.float_wave[q] && d.float_kind[r] == d.float_kind[q])
+                return fail(h, PWA_ERR_INVALID_ARG, "channel %d: floating parameter %d repeated", c, q);
+    }
+    if ((d.n > 0 && !d.kin) || (d.n_mc > 0 && !d.kin_mc))
+        return fail(h, PWA_ERR_INVALID_ARG, "channel %d: NULL kinematics", c);
+    if ((d.kin && !aligned16(d.kin)) || (d.kin_mc && !aligned16(d.kin_mc)) ||
+        (d.w_mc && (reinterpret_cast<uintptr_t>(d.w_mc) & 3u)))
+        return fail(h, PWA_ERR_INVALID_ARG, "channel %d: misaligned array", c);
+    if (!(d.n_gen > 0.0) || !std::isfinite(d.n_gen) || !std::isfinite(d.n_factor))
+        return fail(h, PWA_ERR_INVALID_ARG, "channel %d: bad n_gen or n_factor", c);
+    return PWA_OK;
+}
+
+// Plan of a multi-channel evaluation, and its descriptors and work list on the device (uploaded
+// only when they differ from the last upload; not capturable then).
+pwa_status uneven_prepare(pwa_handle* h, const pwa_uneven_channel* ch, int n_ch, pwa::UnevenPlan* plan,
+                          cudaStream_t s) {
+    char msg[256] = {0};
+    if (pwa::uneven_build_plan(ch, n_ch, plan, msg, sizeof msg) != 0) return fail(h, PWA_ERR_INVALID_ARG, "%s", msg);
+    const size_t need = pwa::uneven_workspace(*plan);
+    std::vector<unsigned char> key(sizeof(pwa::UnevenChannel) * plan->chans.size() + sizeof(int2) * plan->items.size());
+    memcpy(key.data(), plan->chans.data(), sizeof(pwa::UnevenChannel) * plan->chans.size());
+    memcpy(key.data() + sizeof(pwa::UnevenChannel) * plan->chans.size(), plan->items.data(),
+           sizeof(int2) * plan->items.size());
+    if (need > h->uws_bytes) {
+        if (h->uws) {
+            cudaDeviceSynchronize();
+            cudaFree(h->uws);
+            h->uws = nullptr;
+            h->uws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->uws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, PWA_ERR_WORKSPACE, "multi-channel workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        }
+        h->uws_bytes = need;
+        h->uws_key.clear();
+    }
+    if (key != h->uws_key) {
+        cudaError_t e = pwa::uneven_upload(*plan, h->uws, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "multi-channel work list upload");
+        h->uws_key.swap(key);
+    }
+    return PWA_OK;
+}
+
 }  // namespace
 
 namespace pwa {
@@ -303,11 +365,7 @@ void pwa_destroy(pwa_handle* h) {
     if (h->fitws) cudaFree(h->fitws);
     if (h->fit_event) cudaEventDestroy(h->fit_event);
     if (h->fit_stream) cudaStreamDestroy(h->fit_stream);
-    for (int k = 0; k < 8; ++k) {
-        if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
-        if (h->aux_join[k]) cudaEventDestroy(h->aux_join[k]);
-    }
-    if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+    if (h->uws) cudaFree(h->uws);
     delete h;
 }
 
@@ -734,6 +792,34 @@ pwa_status pwa_mlp_to_bf16(pwa_handle* h, const double* x, uint16_t* y, int64_t 
     return e == cudaSuccess ? PWA_OK : cuda_fail(h, e, "to bf16");
 }
 
+pwa_status pwa_nll_grad_uneven(pwa_handle* h, const pwa_uneven_channel* channels, int n_ch, const float* V,
+                               const double* theta, double* nll, double* grad, void* stream) {
+    if (!h) return PWA_ERR_INVALID_ARG;
+    if (!channels || n_ch < 1 || n_ch > (1 << 20)) return fail(h, PWA_ERR_INVALID_ARG, "channels NULL or n_ch < 1");
+    int nF = 0;
+    for (int c = 0; c < n_ch; ++c) {
+        pwa_status st = check_uneven_channel(h, channels[c], c);
+        if (st != PWA_OK) return st;
+        nF += channels[c].F;
+    }
+    if (!V || !nll || !grad || (nF > 0 && !theta))
+        return fail(h, PWA_ERR_INVALID_ARG, "NULL array argument (V, nll, grad, and theta when F > 0)");
+    if ((reinterpret_cast<uintptr_t>(V) & 7u) || (reinterpret_cast<uintptr_t>(nll) & 7u) ||
+        (reinterpret_cast<uintptr_t>(grad) & 7u) || (theta && (reinterpret_cast<uintptr_t>(theta) & 7u)))
+        return fail(h, PWA_ERR_INVALID_ARG, "misaligned V, theta, nll or grad");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pwa::UnevenPlan plan;
+    pwa_status st = uneven_prepare(h, channels, n_ch, &plan, s);
+    if (st != PWA_OK) return st;
+    cudaError_t e = pwa::uneven_launch(plan, h->uws, reinterpret_cast<const float2*>(V), theta, nll, grad, h->status,
+                                       h->sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "multi-channel launch");
+    h->err.clear();
+    return PWA_OK;
+}
+
 void pwa_fit_default_opts(pwa_fit_opts* o) {
     if (!o) return;
     o->max_iter = 1000;
@@ -873,152 +959,86 @@ pwa_status pwa_fit_shape_batch(pwa_handle* h, const pwa_shape_fit_desc* fits, in
     if (o.max_iter < 1 || o.history < 1 || o.history > 20 || !(o.gtol > 0.0) || o.check_every < 1 ||
         (o.polar != 0 && o.polar != 1))
         return fail(h, PWA_ERR_INVALID_ARG, "bad options");
-    std::vector<pwa::WaveTable> wts(n_fits);
+    std::vector<pwa_uneven_channel> chs(n_fits);
     for (int f = 0; f < n_fits; ++f) {
         const pwa_shape_fit_desc& d = fits[f];
-        pwa_status st = check_amp_layout(h, d.K, d.n, d.ld);
-        if (st == PWA_OK) st = check_amp_layout(h, d.K, d.n_mc, d.ld_mc);
+        pwa_uneven_channel& c = chs[f];
+        c.waves = d.waves;
+        c.K = d.K;
+        c.kin = d.kin;
+        c.n = d.n;
+        c.ld = d.ld;
+        c.kin_mc = d.kin_mc;
+        c.n_mc = d.n_mc;
+        c.ld_mc = d.ld_mc;
+        c.w_mc = d.w_mc;
+        c.n_gen = d.n_gen;
+        c.n_factor = d.n_factor;
+        c.F = d.F;
+        c.float_wave = d.float_wave;
+        c.float_kind = d.float_kind;
+        pwa_status st = check_uneven_channel(h, c, f);
         if (st != PWA_OK) return st;
-        if (!d.waves) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: waves NULL", f);
-        st = fill_waves(h, d.waves, d.K, &wts[f]);
-        if (st != PWA_OK) return st;
-        if (d.F < 0 || d.F > PWA_MAX_FLOAT || (d.F > 0 && (!d.float_wave || !d.float_kind)))
-            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: F out of range or NULL float_wave/float_kind", f);
         if (2 * d.K + d.F > 128) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: 2K + F > 128", f);
-        for (int q = 0; q < d.F; ++q) {
-            if (d.float_wave[q] < 0 || d.float_wave[q] >= d.K || (d.float_kind[q] != 0 && d.float_kind[q] != 1))
-                return fail(h, PWA_ERR_INVALID_ARG, "fit %d: bad floating parameter %d", f, q);
-            for (int r = 0; r < q; ++r)
-                if (d.float_wave[r] == d.float_wave[q] && d.float_kind[r] == d.float_kind[q])
-                    return fail(h, PWA_ERR_INVALID_ARG, "fit %d: floating parameter %d repeated", f, q);
-        }
-        if (!d.kin || !d.kin_mc || !d.A || !d.A_mc || !d.V0 || (d.F > 0 && (!d.dA || !d.dA_mc)))
-            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: NULL array", f);
-        if (!aligned16(d.kin) || !aligned16(d.kin_mc) || !aligned16(d.A) || !aligned16(d.A_mc) ||
-            (d.dA && !aligned16(d.dA)) || (d.dA_mc && !aligned16(d.dA_mc)) || (reinterpret_cast<uintptr_t>(d.V0) & 7u) ||
-            (d.x_out && (reinterpret_cast<uintptr_t>(d.x_out) & 7u)))
+        if (!d.V0 || !d.kin || !d.kin_mc) return fail(h, PWA_ERR_INVALID_ARG, "fit %d: NULL array", f);
+        if ((reinterpret_cast<uintptr_t>(d.V0) & 7u) || (d.x_out && (reinterpret_cast<uintptr_t>(d.x_out) & 7u)))
             return fail(h, PWA_ERR_INVALID_ARG, "fit %d: misaligned array", f);
-        if (!(d.n_gen > 0.0) || !std::isfinite(d.n_gen) || !std::isfinite(d.n_factor))
-            return fail(h, PWA_ERR_INVALID_ARG, "fit %d: bad n_gen or n_factor", f);
     }
     DeviceGuard dg(h->device);
     if (!dg.ok) return fail(h, PWA_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t s;
     pwa_status pst = fit_stream_begin(h, stream, &s);
     if (pst != PWA_OK) return pst;
-    const int NS = n_fits < 8 ? n_fits : 8;
-    for (int k = 0; k < NS; ++k) {
-        cudaError_t ce = cudaSuccess;
-        if (!h->aux[k]) ce = cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking);
-        if (ce == cudaSuccess && !h->aux_join[k]) ce = cudaEventCreateWithFlags(&h->aux_join[k], cudaEventDisableTiming);
-        if (ce == cudaSuccess && !h->aux_fork) ce = cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming);
-        if (ce != cudaSuccess) return cuda_fail(h, ce, "fit streams");
-    }
+    pwa::UnevenPlan plan;
+    pst = uneven_prepare(h, chs.data(), n_fits, &plan, s);
+    if (pst != PWA_OK) return pst;
     const int m = o.history;
     const int P_tot = n_fits;
-    // workspace: fit state + per-channel trial point, outputs, partial sums and counters
+    // workspace: fit state, then the packed trial V and theta, f, gradient and per-start step arguments
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t state_b = pwa::fit_workspace(P_tot, m);
-    size_t need = state_b;
+    const size_t vt_b = r256(sizeof(float2) * plan.n_v), th_b = r256(sizeof(double) * (plan.n_theta + 1)),
+                 f_b = r256(sizeof(double) * n_fits), g_b = r256(sizeof(double) * plan.n_grad),
+                 a_b = r256(sizeof(pwa::StepArgs) * n_fits);
+    pst = grow_fitws(h, state_b + vt_b + th_b + f_b + g_b + a_b);
+    if (pst != PWA_OK) return pst;
+    char* c0 = reinterpret_cast<char*>(h->fitws) + state_b;
+    float2* Vt = reinterpret_cast<float2*>(c0);
+    double* tht = reinterpret_cast<double*>(c0 + vt_b);
+    double* fv_d = reinterpret_cast<double*>(c0 + vt_b + th_b);
+    double* gv_d = reinterpret_cast<double*>(c0 + vt_b + th_b + f_b);
+    pwa::StepArgs* args_d = reinterpret_cast<pwa::StepArgs*>(c0 + vt_b + th_b + f_b + g_b);
+    std::vector<pwa::StepArgs> args(n_fits);
+    std::vector<std::vector<double>> th0(n_fits);
     for (int f = 0; f < n_fits; ++f) {
         const pwa_shape_fit_desc& d = fits[f];
-        need += r256(sizeof(float2) * d.K) + r256(sizeof(double) * (d.F + 1)) + r256(sizeof(double)) +
-                r256(sizeof(double) * (2 * d.K + d.F)) + r256(pwa::shape_workspace(d.K, d.F, h->sm_count)) + 256;
-    }
-    pst = grow_fitws(h, need);
-    if (pst != PWA_OK) return pst;
-    struct Ch {
-        float2* Vt;
-        double* th;
-        double* nll;
-        double* grad;
-        void* part;
-        size_t part_b;
-        unsigned* cnt;
-    };
-    std::vector<Ch> ch(n_fits);
-    {
-        char* c = reinterpret_cast<char*>(h->fitws) + state_b;
-        for (int f = 0; f < n_fits; ++f) {
-            const pwa_shape_fit_desc& d = fits[f];
-            ch[f].Vt = reinterpret_cast<float2*>(c);
-            c += r256(sizeof(float2) * d.K);
-            ch[f].th = reinterpret_cast<double*>(c);
-            c += r256(sizeof(double) * (d.F + 1));
-            ch[f].nll = reinterpret_cast<double*>(c);
-            c += r256(sizeof(double));
-            ch[f].grad = reinterpret_cast<double*>(c);
-            c += r256(sizeof(double) * (2 * d.K + d.F));
-            ch[f].part = c;
-            ch[f].part_b = pwa::shape_workspace(d.K, d.F, h->sm_count);
-            c += r256(ch[f].part_b);
-            ch[f].cnt = reinterpret_cast<unsigned*>(c);
-            c += 256;
-        }
-    }
-    cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(h->fitws) + state_b, 0, need - state_b, s);
-    // amplitudes of every wave at the starting masses and widths, then the fit state
-    std::vector<std::vector<double>> th0(n_fits), lb(n_fits);
-    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
-        const pwa_shape_fit_desc& d = fits[f];
-        e = pwa::launch_amplitudes(wts[f], d.kin, d.n, d.ld, reinterpret_cast<float2*>(d.A), nullptr, nullptr,
-                                   h->sm_count, s);
-        if (e == cudaSuccess)
-            e = pwa::launch_amplitudes(wts[f], d.kin_mc, d.n_mc, d.ld_mc, reinterpret_cast<float2*>(d.A_mc), nullptr,
-                                       nullptr, h->sm_count, s);
+        const pwa::UnevenChannel& u = plan.chans[f];
+        pwa::StepArgs& a = args[f];
+        a.K = d.K;
+        a.F = d.F;
+        a.goff = u.goff;
+        a.voff = u.voff;
+        a.toff = u.toff;
+        a.gtol = o.gtol * std::fabs(d.n_factor);
         th0[f].resize(d.F);
-        lb[f].assign(d.F, 1e-3);
+        for (int q = 0; q < PWA_MAX_FLOAT; ++q) a.lb[q] = 1e-3;  // masses and widths stay above 1 MeV
         for (int q = 0; q < d.F; ++q)
             th0[f][q] = d.float_kind[q] == 0 ? d.waves[d.float_wave[q]].mass : d.waves[d.float_wave[q]].width;
-        if (e == cudaSuccess)
-            e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(d.V0), d.K, 1, f, fit_mode(o),
-                                     ch[f].Vt, s, d.F, th0[f].data(), ch[f].th);
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "shape fit init");
-    auto channel = [&](int f, cudaStream_t sc) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(args_d, args.data(), sizeof(pwa::StepArgs) * n_fits, cudaMemcpyHostToDevice, s);
+    for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
         const pwa_shape_fit_desc& d = fits[f];
-        cudaError_t ee = cudaSuccess;
-        for (int q = 0; q < d.F && ee == cudaSuccess; ++q) {
-            const int r = d.float_wave[q];
-            bool first = true;  // one recomputation per floating wave
-            for (int q2 = 0; q2 < q; ++q2) first = first && d.float_wave[q2] != r;
-            if (!first) continue;
-            int qM = -1, qW = -1;
-            for (int q2 = 0; q2 < d.F; ++q2)
-                if (d.float_wave[q2] == r) (d.float_kind[q2] == 0 ? qM : qW) = q2;
-            const pwa_wave& w = d.waves[r];
-            for (int smp = 0; smp < 2 && ee == cudaSuccess; ++smp) {
-                const float* kin = smp == 0 ? d.kin : d.kin_mc;
-                const int64_t nn = smp == 0 ? d.n : d.n_mc, L = smp == 0 ? d.ld : d.ld_mc;
-                float2* AA = reinterpret_cast<float2*>(smp == 0 ? d.A : d.A_mc);
-                float2* DD = reinterpret_cast<float2*>(smp == 0 ? d.dA : d.dA_mc);
-                ee = pwa::launch_amp_floating(w.J, w.lambda, qM >= 0 ? ch[f].th + qM : nullptr, w.mass,
-                                              qW >= 0 ? ch[f].th + qW : nullptr, w.width, kin, nn, L, AA + r * L,
-                                              qM >= 0 ? DD + qM * L : nullptr, qW >= 0 ? DD + qW * L : nullptr,
-                                              h->sm_count, sc);
-            }
-        }
-        if (ee != cudaSuccess) return ee;
-        ee = pwa::launch_nll_shape(reinterpret_cast<const float2*>(d.A), reinterpret_cast<const float2*>(d.dA), d.K,
-                                   d.n, d.ld, reinterpret_cast<const float2*>(d.A_mc),
-                                   reinterpret_cast<const float2*>(d.dA_mc), d.n_mc, d.ld_mc, d.w_mc, d.n_gen,
-                                   d.float_wave, d.F, ch[f].Vt, d.n_factor, ch[f].nll, ch[f].grad, ch[f].part,
-                                   ch[f].part_b, ch[f].cnt, reinterpret_cast<int*>(ch[f].cnt + 1), h->status,
-                                   h->sm_count, sc);
-        if (ee != cudaSuccess) return ee;
-        return pwa::fit_launch_step(h->fitws, P_tot, m, ch[f].nll, ch[f].grad, ch[f].Vt, d.K, 1, f,
-                                    o.gtol * std::fabs(d.n_factor), fit_mode(o), o.max_iter, sc, d.F, ch[f].th,
-                                    lb[f].data());
-    };
+        e = pwa::fit_launch_init(h->fitws, P_tot, m, reinterpret_cast<const float2*>(d.V0), d.K, 1, f, fit_mode(o),
+                                 Vt + args[f].voff, s, d.F, th0[f].data(), tht + args[f].toff);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors above must outlive the copies
+    if (e != cudaSuccess) return cuda_fail(h, e, "shape fit init");
+    // one iteration: every channel's f and gradient in one persistent launch, then one L-BFGS step
+    // launch over all channels
     auto iteration = [&]() -> cudaError_t {
-        cudaError_t ee = cudaEventRecord(h->aux_fork, s);
-        for (int k = 0; k < NS && ee == cudaSuccess; ++k) ee = cudaStreamWaitEvent(h->aux[k], h->aux_fork, 0);
-        for (int f = 0; f < n_fits && ee == cudaSuccess; ++f) ee = channel(f, h->aux[f % NS]);
-        for (int k = 0; k < NS && ee == cudaSuccess; ++k) {
-            ee = cudaEventRecord(h->aux_join[k], h->aux[k]);
-            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(s, h->aux_join[k], 0);
-        }
-        return ee;
+        cudaError_t ee = pwa::uneven_launch(plan, h->uws, Vt, tht, fv_d, gv_d, h->status, h->sm_count, s);
+        if (ee != cudaSuccess) return ee;
+        return pwa::fit_launch_step_multi(h->fitws, P_tot, m, args_d, fv_d, gv_d, Vt, tht, fit_mode(o), o.max_iter, s);
     };
     e = run_fit_loop(h, s, o, P_tot, m, iteration);
     if (e != cudaSuccess) return cuda_fail(h, e, "shape fit loop");

@@ -146,25 +146,27 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
 // pwa_nll_grad).  Writes the next trial point as single-precision V.
 // Writes the trial V (and, for F > 0 floating shape parameters, the trial theta) of the next
 // evaluation; x = (Re V_0, Im V_0, ..., Re V_K-1, Im V_K-1, theta_0..theta_F-1).
-__device__ __forceinline__ void write_trial(const double* x, const double* d, double a, int K, int F, int pl,
-                                            float2* Vt, double* theta_t, bool polar) {
+// Vrow: the start's trial V [K]; th_row: its trial theta [F] (unused when F = 0)
+__device__ __forceinline__ void write_trial(const double* x, const double* d, double a, int K, int F, float2* Vrow,
+                                            double* th_row, bool polar) {
     const int t = threadIdx.x;
     if (t < K) {
         const double2 v = coords_to_v(x[2 * t] + a * d[2 * t], x[2 * t + 1] + a * d[2 * t + 1], polar);
-        Vt[(int64_t)pl * K + t] = make_float2((float)v.x, (float)v.y);
+        Vrow[t] = make_float2((float)v.x, (float)v.y);
     }
-    if (t < F) theta_t[(int64_t)pl * F + t] = x[2 * K + t] + a * d[2 * K + t];
+    if (t < F) th_row[t] = x[2 * K + t] + a * d[2 * K + t];
 }
 
-__global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* __restrict__ ft,
-                                                    const double* __restrict__ gt, float2* __restrict__ Vt, int K,
-                                                    int p_off, int m, double gtol, int mode, int max_iter, int F,
-                                                    double* __restrict__ theta_t, Theta0 th) {
+// The step of start p (one block of 128 threads): fnew and gp = f and g [2K + F] at the trial point
+// just evaluated; lb the lower bounds of the F shape parameters.
+__device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew, const double* __restrict__ gp,
+                                                float2* Vrow, double* th_row, int K, int F, int m, double gtol,
+                                                int mode, int max_iter, const double* lb) {
     __shared__ double red[128];
     __shared__ double q[DM], xt[DM];
     __shared__ double a_hist[32];
     __shared__ int s_action;  // 0: keep, 1: accepted, 2: rejected
-    const int pl = blockIdx.x, p = p_off + pl, t = threadIdx.x;
+    const int t = threadIdx.x;
     const int D = 2 * K + F;
     const bool gauge = mode & FIT_GAUGE, polar = mode & FIT_POLAR;
     double* x = st.x + (int64_t)p * DM;
@@ -175,17 +177,15 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     double* rho = st.rho + (int64_t)p * m;
     const int status = st.status[p];
     if (status != FIT_RUNNING) {
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
+        write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
         return;
     }
     if (t == 0) st.evals[p] += 1;
-    const double fnew = ft[pl];
     // trial point that was evaluated = x + alpha d (or x itself for the first evaluation)
     const double alpha = st.alpha[p];
     if (t < D) xt[t] = (alpha == 0.0) ? x[t] : x[t] + alpha * d[t];
     __syncthreads();
     if (t < D) {
-        const double* gp = gt + (int64_t)pl * D;
         double gv = gp[t];
         if (polar && t < 2 * K) {  // chain rule from (Re V_a, Im V_a) to (rho_a, phi_a)
             const int a = t >> 1;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const int action = s_action;
     if (action == 3) {  // non-finite at the start point
         if (t == 0) st.status[p] = 3;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
+        write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
         return;
     }
     if (action == 2) {
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
             if (an < 1e-20) st.status[p] = 2;
         }
         __syncthreads();
-        write_trial(x, d, st.alpha[p], K, F, pl, Vt, theta_t, polar);
+        write_trial(x, d, st.alpha[p], K, F, Vrow, th_row, polar);
         return;
     }
     // ---- accepted: history update with s = xt - x, y = gt - g
@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
     const double gmax = block_max_abs(g, D, red);
     if (gmax < gtol) {
         if (t == 0) st.status[p] = 0;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
+        write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
         return;
     }
     if (st.iter[p] >= max_iter) {
         if (t == 0) st.status[p] = 1;
-        write_trial(x, x, 0.0, K, F, pl, Vt, theta_t, polar);
+        write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
         return;
     }
     // ---- two-loop recursion: q = g; newest to oldest
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
             double amax = a0;
             for (int q = 0; q < F; ++q) {
                 const double dq = d[2 * K + q];
-                if (dq < 0.0) amax = fmin(amax, 0.9 * (x[2 * K + q] - th.lb[q]) / (-dq));
+                if (dq < 0.0) amax = fmin(amax, 0.9 * (x[2 * K + q] - lb[q]) / (-dq));
             }
             red[0] = amax;
         }
@@ -338,7 +338,28 @@ __global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* _
         st.gtd[p] = gtd;
         st.alpha[p] = a0;
     }
-    write_trial(x, d, a0, K, F, pl, Vt, theta_t, polar);
+    write_trial(x, d, a0, K, F, Vrow, th_row, polar);
+}
+
+__global__ void __launch_bounds__(128) k_lbfgs_step(FitState st, const double* __restrict__ ft,
+                                                    const double* __restrict__ gt, float2* __restrict__ Vt, int K,
+                                                    int p_off, int m, double gtol, int mode, int max_iter, int F,
+                                                    double* __restrict__ theta_t, Theta0 th) {
+    const int pl = blockIdx.x;
+    lbfgs_step_body(st, p_off + pl, ft[pl], gt + (int64_t)pl * (2 * K + F), Vt + (int64_t)pl * K,
+                    theta_t + (int64_t)pl * F, K, F, m, gtol, mode, max_iter, th.lb);
+}
+
+// One step for every start p of fits of different sizes: start p's K, F, gradient row, trial V
+// and theta offsets, tolerance and bounds from args[p]; f of start p is ft[p].
+__global__ void __launch_bounds__(128) k_lbfgs_step_multi(FitState st, const StepArgs* __restrict__ args,
+                                                          const double* __restrict__ ft, const double* __restrict__ gt,
+                                                          float2* __restrict__ Vt, double* __restrict__ theta_t, int m,
+                                                          int mode, int max_iter) {
+    const int p = blockIdx.x;
+    const StepArgs a = args[p];
+    lbfgs_step_body(st, p, ft[p], gt + a.goff, Vt + a.voff, theta_t + a.toff, a.K, a.F, m, a.gtol, mode, max_iter,
+                    a.lb);
 }
 
 __global__ void k_count_running(const int* __restrict__ status, int P, int* __restrict__ out) {
@@ -455,6 +476,14 @@ cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, con
     FitState st = carve(fitws, P_tot, m);
     k_lbfgs_step<<<P, 128, 0, s>>>(st, ft, gt, Vt, K, p_off, m, gtol, mode, max_iter, F, theta_t,
                                    make_theta0(F, nullptr, lb));
+    return cudaGetLastError();
+}
+
+cudaError_t fit_launch_step_multi(void* fitws, int P_tot, int m, const StepArgs* args, const double* ft,
+                                  const double* gt, float2* Vt, double* theta_t, int mode, int max_iter,
+                                  cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_lbfgs_step_multi<<<P_tot, 128, 0, s>>>(st, args, ft, gt, Vt, theta_t, m, mode, max_iter);
     return cudaGetLastError();
 }
 

@@ -1,17 +1,25 @@
 // -lnL and its gradient for one parameter set without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA stream capture it does not
-// own, host code under a memory manager that forbids allocations after start-up, or plug-ins
-// of a larger program that owns all device memory.  pwa_nll_grad needs a handle, and both the
-// handle and its workspace are allocated with cudaMalloc.  pwa_nll_grad_noalloc needs neither:
-// its scratch (block partial sums, the completion counter, flags and fixed-point sums) lives in the
-// file-scope device array below, which every GPU that loads the library holds until exit.
+// Some callers cannot call cudaMalloc: host code under a memory manager that forbids
+// allocations after start-up, plug-ins of a larger program that owns all device memory, and
+// latency-critical loops that must not take the allocator's locks or its implicit
+// synchronisation.  pwa_nll_grad needs a handle, and both the handle and its workspace are
+// allocated with cudaMalloc.  pwa_nll_grad_noalloc needs neither: its scratch (block partial
+// sums, the completion counter, flags and fixed-point sums) lives in the file-scope device array
+// below, which every GPU that loads the library holds until exit.
 //
 // Limits: K <= PWA_MAX_WAVES and at most NOALLOC_MAX_BLOCKS blocks per launch (the launch is
 // capped there; any n is accepted).  The scratch is shared by every call on a device and keeps
 // the last call's contents: each call clears the control words on its stream before
 // its kernel runs, so calls ordered on one stream are safe, while calls that overlap on the
 // GPU (different streams, different host threads) race on the scratch and give wrong results.
+//
+// The scratch's device address belongs to the CUDA context in which it was looked up.  It is
+// looked up on the first call in each context (keyed by the driver's unique context id, so a
+// context created after cudaDeviceReset, or another context made current on the same device,
+// gets a fresh lookup instead of a stale address).
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -30,26 +38,64 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_PART_BYTES;  // 1,056,
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+struct NoallocSlot {
+    unsigned long long ctx_id;  // unique id of the context the address was looked up in
+    void* ptr;
+    int sms;
+    bool valid;
+};
+NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES] = {};
+
+// The driver's cuCtxGetCurrent and cuCtxGetId, reached through the runtime (no link-time
+// dependency on libcuda).
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+bool current_context_id(int dev, unsigned long long* id) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return false;
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(f0);
+        get_id = reinterpret_cast<PfnCtxGetId>(f1);
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return false;
+    if (!c) {
+        // no context is current yet: cudaSetDevice makes the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess || get_current(&c) != CUDA_SUCCESS || !c) return false;
+    }
+    return get_id(c, id) == CUDA_SUCCESS;
+}
 
 // Device address of the scratch array and the SM count of the current device, looked up once
-// per device (with that device current).  In host code the symbol g_noalloc_scratch is only a
+// per context (with that device current).  In host code the symbol g_noalloc_scratch is only a
 // host-side stand-in: its device address has to come from cudaGetSymbolAddress.
 cudaError_t noalloc_setup(int dev, void** ptr, int* sms) {
+    unsigned long long id = 0;
+    if (!current_context_id(dev, &id)) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot& s = g_noalloc_slot[dev];
+    if (!s.valid || s.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        g_noalloc_sms[dev] = n > 0 ? n : 1;
-        g_noalloc_ptr[dev] = p;
+        s.ptr = p;
+        s.sms = n > 0 ? n : 1;
+        s.ctx_id = id;
+        s.valid = true;
     }
-    *ptr = g_noalloc_ptr[dev];
-    *sms = g_noalloc_sms[dev];
+    *ptr = s.ptr;
+    *sms = s.sms;
     return cudaSuccess;
 }
 
@@ -83,7 +129,8 @@ extern "C" PWA_API pwa_status pwa_nll_grad_noalloc(const float* A, int K, int64_
     cudaError_t e = noalloc_setup(dev, &base, &sms);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return noalloc_fail(PWA_ERR_CUDA, "pwa_nll_grad_noalloc: cudaGetSymbolAddress of the scratch failed");
+        return noalloc_fail(PWA_ERR_CUDA, "pwa_nll_grad_noalloc: no current context, or cudaGetSymbolAddress of the "
+                                          "scratch failed");
     }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* b = reinterpret_cast<unsigned char*>(base);

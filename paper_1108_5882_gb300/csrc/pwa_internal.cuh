@@ -31,9 +31,9 @@ struct pwa_handle {
     size_t fitws_bytes = 0;
     cudaStream_t fit_stream = nullptr;  // capturable stream the fitter runs on
     cudaEvent_t fit_event = nullptr;
-    cudaStream_t aux[8] = {};            // fork/join streams of the multi-channel fits
-    cudaEvent_t aux_join[8] = {};
-    cudaEvent_t aux_fork = nullptr;
+    void* uws = nullptr;                 // multi-channel evaluation: descriptors, work list, item sums
+    size_t uws_bytes = 0;
+    std::vector<unsigned char> uws_key;  // host image of the descriptors and work list last uploaded
 };
 
 namespace pwa {
@@ -218,6 +218,51 @@ cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>&
                              cudaStream_t s);
 cudaError_t fit_export(void* fitws, int P_tot, int m, int K, int P, int p_off, int mode, double* Vout,
                        cudaStream_t s);
+
+// Per-start arguments of the L-BFGS step over fits of different sizes: wave count, shape
+// parameters, offsets of the start's gradient row, trial V and trial theta in their packed
+// arrays, convergence threshold and the shape parameters' lower bounds.
+struct StepArgs {
+    int K, F, goff, voff, toff;
+    double gtol;
+    double lb[PWA_MAX_FLOAT];
+};
+cudaError_t fit_launch_step_multi(void* fitws, int P_tot, int m, const StepArgs* args, const double* ft,
+                                  const double* gt, float2* Vt, double* theta_t, int mode, int max_iter,
+                                  cudaStream_t s);
+
+// Many channels of floating-shape likelihoods in one persistent launch (uneven.cu).  Device
+// descriptor of one channel; waves in (J, lambda)-sorted order s, ord[s] the caller's index.
+struct UnevenChannel {
+    const float* kin;
+    const float* kin_mc;
+    const float* w_mc;
+    int64_t n, ld, n_mc, ld_mc;
+    double scale;  // n_factor / n_gen
+    int K, F, ng, nchunk;
+    int epi;       // events per work item
+    int items_d, items_m;
+    int voff, toff, goff;
+    int64_t poff;  // first item-sum slot (float2 units)
+    int ord[PWA_MAX_WAVES];
+    double Md[PWA_MAX_WAVES], Wd[PWA_MAX_WAVES];
+    signed char qM[PWA_MAX_WAVES], qW[PWA_MAX_WAVES];  // floating parameter of the mass / width, -1 fixed
+    int gend[PWA_MAX_WAVES], gJ[PWA_MAX_WAVES], glam[PWA_MAX_WAVES];
+    int cgrp[PWA_MAX_WAVES / 16];  // group of the first wave of each 16-wave chunk
+};
+struct UnevenPlan {
+    int n_ch = 0;
+    std::vector<UnevenChannel> chans;
+    std::vector<int2> items;  // (channel, item within the channel: data items, then MC items)
+    int64_t part_f2 = 0;      // item-sum slots (float2)
+    int n_v = 0, n_theta = 0, n_grad = 0;  // lengths of the packed V, theta and gradient arrays
+};
+// builds the plan from validated descriptors; returns 0, or -1 with a message in err
+int uneven_build_plan(const pwa_uneven_channel* ch, int n_ch, UnevenPlan* plan, char* err, size_t err_len);
+size_t uneven_workspace(const UnevenPlan& p);
+cudaError_t uneven_upload(const UnevenPlan& p, void* ws, cudaStream_t st);
+cudaError_t uneven_launch(const UnevenPlan& p, void* ws, const float2* V, const double* theta, double* nll,
+                          double* grad, int* status, int sm_count, cudaStream_t st);
 
 size_t shape_workspace(int K, int F, int sm_count);
 cudaError_t launch_nll_shape(const float2* A, const float2* dA, int K, int64_t n, int64_t ld, const float2* Am,

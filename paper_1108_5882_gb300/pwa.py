@@ -111,6 +111,8 @@ def _register_optional(lib):
     lib.pwa_fit_shape_batch.argtypes = [_vp, ctypes.POINTER(pwa_shape_fit_desc), ctypes.c_int,
                                         ctypes.POINTER(pwa_fit_opts), ctypes.POINTER(pwa_fit_result), _vp]
     lib.pwa_fit_shape_batch.restype = S
+    lib.pwa_nll_grad_uneven.argtypes = [_vp, ctypes.POINTER(pwa_uneven_channel), ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+    lib.pwa_nll_grad_uneven.restype = S
     lib.pwa_moments.argtypes = [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]
     lib.pwa_moments.restype = S
     lib.pwa_toy_moments.argtypes = [_vp, ctypes.POINTER(pwa_wave), ctypes.c_int, _vp, ctypes.c_int, _vp,
@@ -161,6 +163,13 @@ class pwa_shape_fit_desc(ctypes.Structure):
                 ("n_factor", ctypes.c_double), ("F", ctypes.c_int), ("float_wave", ctypes.POINTER(ctypes.c_int)),
                 ("float_kind", ctypes.POINTER(ctypes.c_int)), ("A", _vp), ("A_mc", _vp), ("dA", _vp), ("dA_mc", _vp),
                 ("V0", _vp), ("x_out", _vp)]
+
+
+class pwa_uneven_channel(ctypes.Structure):
+    _fields_ = [("waves", ctypes.POINTER(pwa_wave)), ("K", ctypes.c_int), ("kin", _vp), ("n", _i64), ("ld", _i64),
+                ("kin_mc", _vp), ("n_mc", _i64), ("ld_mc", _i64), ("w_mc", _vp), ("n_gen", ctypes.c_double),
+                ("n_factor", ctypes.c_double), ("F", ctypes.c_int), ("float_wave", ctypes.POINTER(ctypes.c_int)),
+                ("float_kind", ctypes.POINTER(ctypes.c_int))]
 
 
 def status_string(s: int) -> str:
@@ -419,31 +428,66 @@ def _nll_grad_shape(self, A, dA, n, A_mc, dA_mc, n_mc, float_wave, V, n_factor, 
 Handle.pwa_nll_grad_shape = _nll_grad_shape
 
 
+def _uneven_array(channels):
+    """pwa_uneven_channel[] from dicts with waves [(J, lambda, M, W)], kin / kin_mc (float32 [3][ld]
+    CUDA), n, n_mc, optional n_gen, n_factor, w_mc, float_wave, float_kind.  Returns the array and
+    the host buffers it points into (keep them alive for the call)."""
+    arr = (pwa_uneven_channel * len(channels))()
+    keep = []
+    for i, c in enumerate(channels):
+        K = len(c["waves"])
+        fwv = c.get("float_wave", [])
+        F = len(fwv)
+        _check_cuda(c["kin"], "kin", torch.float32)
+        _check_cuda(c["kin_mc"], "kin_mc", torch.float32)
+        _check_cuda(c.get("w_mc"), "w_mc", torch.float32)
+        wv = _wave_array(c["waves"])
+        fw = (ctypes.c_int * max(F, 1))(*[int(x) for x in fwv])
+        fk = (ctypes.c_int * max(F, 1))(*[int(x) for x in c.get("float_kind", [])])
+        keep += [wv, fw, fk]
+        arr[i] = pwa_uneven_channel(wv, K, c["kin"].data_ptr(), int(c["n"]), c["kin"].shape[1], c["kin_mc"].data_ptr(),
+                                    int(c["n_mc"]), c["kin_mc"].shape[1],
+                                    c["w_mc"].data_ptr() if c.get("w_mc") is not None else None,
+                                    float(c.get("n_gen", c["n_mc"])), float(c.get("n_factor", c["n"])), F, fw, fk)
+    return arr, keep
+
+
+def _nll_grad_uneven(self, channels, V, theta, nll, grad, stream=None):
+    """f and gradient of many channels in one launch.  V complex64 [sum K] (CUDA), theta float64
+    [sum F] or None, nll float64 [n_ch], grad float64 [sum (2K + F)] (outputs)."""
+    _check_cuda(V, "V", torch.complex64)
+    _check_cuda(theta, "theta", torch.float64)
+    _check_cuda(nll, "nll", torch.float64)
+    _check_cuda(grad, "grad", torch.float64)
+    arr, keep = _uneven_array(channels)
+    self._chk(self.lib.pwa_nll_grad_uneven(self.h, arr, len(channels), _ptr(V), _ptr(theta), _ptr(nll), _ptr(grad),
+                                           _stream_ptr(stream)))
+    del keep
+
+
+Handle.pwa_nll_grad_uneven = _nll_grad_uneven
+
+
 def _fit_shape_batch(self, channels, opts=None, stream=None):
     """channels: list of dicts with waves [(J, lambda, M, W)], kin / kin_mc (float32 [3][ld] CUDA),
     n, n_mc, n_gen, n_factor, float_wave, float_kind, V0 (complex64 [K] CUDA), optional w_mc and
-    x_out (float64 [2K+F] CUDA).  Work buffers are allocated here.  Returns per-channel results."""
+    x_out (float64 [2K+F] CUDA).  Returns per-channel results."""
     arr = (pwa_shape_fit_desc * len(channels))()
     keep = []
     for i, c in enumerate(channels):
         K = len(c["waves"])
         F = len(c["float_wave"])
         ld, ld_mc = c["kin"].shape[1], c["kin_mc"].shape[1]
-        dev = c["kin"].device
-        A = torch.empty((K, ld), dtype=torch.complex64, device=dev)
-        Am = torch.empty((K, ld_mc), dtype=torch.complex64, device=dev)
-        dA = torch.empty((max(F, 1), ld), dtype=torch.complex64, device=dev)
-        dAm = torch.empty((max(F, 1), ld_mc), dtype=torch.complex64, device=dev)
         wv = _wave_array(c["waves"])
         fw = (ctypes.c_int * max(F, 1))(*[int(x) for x in c["float_wave"]])
         fk = (ctypes.c_int * max(F, 1))(*[int(x) for x in c["float_kind"]])
         _check_cuda(c["V0"], "V0", torch.complex64)
         _check_cuda(c.get("x_out"), "x_out", torch.float64)
-        keep += [A, Am, dA, dAm, wv, fw, fk]
+        keep += [wv, fw, fk]
         arr[i] = pwa_shape_fit_desc(wv, K, c["kin"].data_ptr(), int(c["n"]), ld, c["kin_mc"].data_ptr(), int(c["n_mc"]),
                                     ld_mc, c["w_mc"].data_ptr() if c.get("w_mc") is not None else None,
                                     float(c.get("n_gen", c["n_mc"])), float(c.get("n_factor", c["n"])), F, fw, fk,
-                                    A.data_ptr(), Am.data_ptr(), dA.data_ptr(), dAm.data_ptr(), c["V0"].data_ptr(),
+                                    None, None, None, None, c["V0"].data_ptr(),
                                     c["x_out"].data_ptr() if c.get("x_out") is not None else None)
     res = (pwa_fit_result * len(channels))()
     o = opts if opts is not None else fit_opts()

@@ -12,6 +12,8 @@ denominators):
   Psi:         |Psi_gpu - Psi_ref|_ab <= 1e-5 * sqrt(Psi_aa Psi_bb)
   Hessian:     |H_gpu - H_ref| <= 1e-5 * (the same sums of term magnitudes, per entry)
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -62,6 +64,28 @@ def check_nll(f_gpu, g_gpu, A, V, Psi, n_factor=None, check_grad=True):
         err_g = np.abs(g_gpu - g_ref) / scale
         assert np.all(err_g <= 1e-4), err_g.max()
     return f_ref, g_ref
+
+
+def check_plain_gradient(g_gpu, A, V, Psi, n_factor=None):
+    """At a random (non-stationary) V the gradient is O(N) and needs no condition-aware scale:
+    every component with |g_ref| >= 1e-3 max|g_ref| within 1e-4 of itself, and max|g_gpu - g_ref|
+    <= 1e-4 max|g_ref|.  Returns the ratio of the parity scale built from s_i = sum_a |V_a||A_ia|
+    to the one built from |u_i| (the gradient tolerance's reading of the precision remark), per
+    component, for the record."""
+    n = A.shape[1]
+    n_factor = float(n if n_factor is None else n_factor)
+    f_ref, g_ref, cf, cg, bad = oracle.nll_grad(A, V, Psi, n_factor=n_factor, with_cond=True)
+    err = np.abs(g_gpu - g_ref)
+    big = np.abs(g_ref) >= 1e-3 * np.max(np.abs(g_ref), axis=1, keepdims=True)
+    assert np.all(err[big] <= 1e-4 * np.abs(g_ref[big])), (err[big] / np.abs(g_ref[big])).max()
+    assert np.all(np.max(err, axis=1) <= 1e-4 * np.max(np.abs(g_ref), axis=1))
+    A64 = A.astype(np.complex128)
+    ratios = []
+    for p in range(V.shape[0]):
+        u = V[p].astype(np.complex128) @ A64
+        scale_u = 2 * (np.abs(A64) @ (1.0 / np.abs(u))) + 2 * n_factor * (np.abs(V[p]) @ np.abs(Psi))
+        ratios.append(cg[p] / scale_u)
+    return np.array(ratios)
 
 
 # ------------------------------------------------------------------- amplitudes ---------
@@ -187,12 +211,37 @@ def test_nll_grad_single_set(h, K):
     assert f2[0] == f[0] or abs(f2[0] - f[0]) <= 1e-12 * abs(f[0])
 
 
+@pytest.mark.parametrize("variant", ["PWA_STREAM_HOLD=0", "PWA_STREAM_FUSED=0", "PWA_STREAM_TMA=1",
+                                     "PWA_STREAM_HOLD=0,PWA_STREAM_FUSED=0"])
+@pytest.mark.parametrize("K", [4, 16, 32, 64])
+def test_nll_grad_single_set_variants(h, K, variant, monkeypatch):
+    # the non-default single-set kernels, forced: the amplitudes reloaded for the gradient pass
+    # instead of held in registers (HOLD=0), the grid reduction finalised by a second launch
+    # instead of the last block (FUSED=0), and the bulk-copy staged kernel (TMA=1); ragged tail,
+    # NaN padding never read, several blocks
+    for kv in variant.split(","):
+        k, v = kv.split("=")
+        monkeypatch.setenv(k, v)
+    n = 20_001
+    p = make_problem(K, n, 2 * n, SEED + 200 + K, accept_reject=False)
+    ld = n + 3
+    for V in (p.V_true[None, :], inputs.starts(1, K, SEED + 201)):
+        f, g = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), n, V, p.Psi)
+        check_nll(f, g, p.A, V, p.Psi)
+        f2, _ = gpu_nll_grad(h, padded(p.A, ld, fill=np.complex64(np.nan)), n, V, p.Psi, grad=False)
+        assert abs(f2[0] - f[0]) <= 1e-12 * abs(f[0])
+
+
 def test_plain_workload_at_random_starts(h):
     # plain workload: K=4, N_data=1e4, N_MC=5e4, data by accept-reject, one set per launch
     p = make_problem(4, 10_000, 50_000, SEED + 1, plain=True)
+    ratios = []
     for V in inputs.starts(8, 4, SEED + 1):
         f, g = gpu_nll_grad(h, p.A, p.n, V[None, :], p.Psi)
         check_nll(f, g, p.A, V[None, :], p.Psi)
+        ratios.append(check_plain_gradient(g, p.A, V[None, :], p.Psi))
+    r = np.concatenate(ratios).ravel()
+    print(f"plain workload: s_i / |u_i| gradient scale ratio median {np.median(r):.2f}, max {r.max():.2f}")
 
 
 @pytest.mark.parametrize("K,P", [(4, 2), (8, 33), (16, 64), (16, 100), (32, 7), (32, 256), (48, 40), (64, 65)])
@@ -465,6 +514,12 @@ def test_scale_workload_full_size(h):
     V = inputs.production_amplitudes(K, SEED + 2)[None, :]
     f, g = gpu_nll_grad(h, A, n, V, Psi)
     check_nll(f, g, A, V, Psi)
+    # a random start: plain relative gradient error, and the two gradient scales compared
+    V = inputs.starts(1, K, SEED + 2)
+    f, g = gpu_nll_grad(h, A, n, V, Psi)
+    check_nll(f, g, A, V, Psi)
+    r = check_plain_gradient(g, A, V, Psi).ravel()
+    print(f"scale workload: s_i / |u_i| gradient scale ratio median {np.median(r):.2f}, max {r.max():.2f}")
 
 
 def test_multistart_workload_full_size_sampled(h):
@@ -477,8 +532,19 @@ def test_multistart_workload_full_size_sampled(h):
     Psi = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
     V = inputs.starts(P, K, SEED + 3)
     f, g = gpu_nll_grad(h, A, n, V, Psi)
+    # the autotuner's choice at this size is the tensor-core shape (FP32 products as three TF32
+    # products), the shape the benchmark times; the samples below check that shape
+    assert h.pwa_batched_shape(K, n, P) == 4
     for q in (0, 101, 255):
         check_nll(f[q:q + 1], g[q:q + 1], A, V[q:q + 1], Psi)
+    # the FP32 SIMT shape the fitter evaluates with, forced, at the same size
+    os.environ["PWA_BATCHED_SHAPE"] = "3"
+    try:
+        f3, g3 = gpu_nll_grad(h, A, n, V, Psi)
+    finally:
+        del os.environ["PWA_BATCHED_SHAPE"]
+    for q in (7, 128, 254):
+        check_nll(f3[q:q + 1], g3[q:q + 1], A, V[q:q + 1], Psi)
 
 
 # ------------------------------------------------------------------- generator ----------
