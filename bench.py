@@ -56,6 +56,9 @@ WORKLOADS = {
     "scale": (16, 1_000_000, 5_000_000, 1, 11085884),
     "multistart": (32, 2_000_000, 10_000_000, 256, 11085885),
 }
+# uneven: 64 channels, K ~ U{4..48}, N_data log-U[1e4, 4e6], N_MC = 5 N_data, 2 floating masses and
+# 2 floating widths per channel
+UNEVEN = (64, 11085886)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -439,6 +442,202 @@ def run_ours(args, world, rank, local):
     return res
 
 
+# ----------------------------------------------------------------------------- uneven channels
+def setup_uneven(h, rank):
+    """64 channels on the device: data drawn by the library's accept-reject from I under a seeded V
+    per channel, flat MC drawn by torch's seeded device generator, floating masses and widths of
+    waves 0 and K/2 set slightly off the values the data were drawn with."""
+    import torch
+
+    from paper_1108_5882_gb300 import inputs, pwa
+    n_ch, seed = UNEVEN
+    seed = seed + 1000 * rank
+    chans = []
+    for c, (K, N, NMC) in enumerate(inputs.uneven_channels(n_ch, seed)):
+        ws = inputs.wave_set_spread(K, seed, stream=100 + c)
+        waves = pwa.waves_from(ws)
+        V = inputs.production_amplitudes(K, seed, stream=200 + c)
+        C = pwa.pwa_envelope(waves, V)
+        ld, ld_mc = N + (N & 1), NMC + (NMC & 1)
+        kin = torch.zeros((3, ld), dtype=torch.float32, device="cuda")
+        na = torch.zeros(1, dtype=torch.int64, device="cuda")
+        Vd = torch.from_numpy(V).cuda()
+        got, cand0, chunk = 0, 0, 1 << 26
+        while got < N:
+            tmp = torch.zeros((3, N - got), dtype=torch.float32, device="cuda")
+            h.pwa_generate(waves, Vd, seed, c, cand0, chunk, C, tmp, N - got, na)
+            k = min(int(na.item()), N - got)
+            kin[:, got:got + k] = tmp[:, :k]
+            got += k
+            cand0 += chunk
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed * 64 + c)
+        kin_mc = torch.zeros((3, ld_mc), dtype=torch.float32, device="cuda")
+        u = torch.rand((3, NMC), generator=g, device="cuda")
+        kin_mc[0, :NMC] = inputs.M_LO + (inputs.M_HI - inputs.M_LO) * u[0]
+        kin_mc[1, :NMC] = 2.0 * u[1] - 1.0
+        kin_mc[2, :NMC] = torch.clamp(2.0 * math.pi * u[2], max=math.nextafter(2.0 * math.pi, 0.0))
+        del u
+        fl = [0, K // 2]
+        theta = [ws.M[fl[0]] * 1.002, ws.M[fl[1]] * 0.998, ws.W[fl[0]] * 1.01, ws.W[fl[1]] * 0.99]
+        chans.append(dict(waves=waves, K=K, kin=kin, n=N, kin_mc=kin_mc, n_mc=NMC, n_gen=float(NMC), n_factor=float(N),
+                          float_wave=[fl[0], fl[1], fl[0], fl[1]], float_kind=[0, 0, 1, 1], V=V, theta=theta, ws=ws))
+    torch.cuda.synchronize()
+    return chans
+
+
+def uneven_flops(chans):
+    """Algorithmic FP32 work of one evaluation of every channel: per (event, wave) one Breit-Wigner
+    (11 flop), the complex multiply-add into u (8) and into the gradient (8); per event and
+    floating parameter its derivative term (10); per event |u|^2, ln I and w (12)."""
+    return float(sum((c["n"] + c["n_mc"]) * (27 * c["K"] + 10 * len(c["float_wave"]) + 12) for c in chans))
+
+
+def cpu_baseline_uneven(chans, seconds):
+    """The oracle on whole channels (FP64 amplitudes with their mass and width derivatives, then
+    f and the gradient in V and theta), smallest channels first for about `seconds`; a full
+    evaluation of all channels is extrapolated linearly in (events x waves)."""
+    import oracle
+    order = sorted(range(len(chans)), key=lambda c: (chans[c]["n"] + chans[c]["n_mc"]) * chans[c]["K"])
+    done, work_done, t_tot = 0, 0.0, 0.0
+    for c in order:
+        ch = chans[c]
+        ws = ch["ws"]
+        kin = np.ascontiguousarray(ch["kin"][:, :ch["n"]].cpu().numpy())
+        kin_mc = np.ascontiguousarray(ch["kin_mc"][:, :ch["n_mc"]].cpu().numpy())
+        M, W = ws.M.copy(), ws.W.copy()
+        for q, (r, k) in enumerate(zip(ch["float_wave"], ch["float_kind"])):
+            (M if k == 0 else W)[r] = ch["theta"][q]
+        t0 = time.perf_counter()
+        A, dM, dW = oracle.amplitudes(ws.J, ws.lam, M, W, kin, derivs=True)
+        Am, dMm, dWm = oracle.amplitudes(ws.J, ws.lam, M, W, kin_mc, derivs=True)
+        dA = np.stack([(dM if k == 0 else dW)[r] for r, k in zip(ch["float_wave"], ch["float_kind"])])
+        dAm = np.stack([(dMm if k == 0 else dWm)[r] for r, k in zip(ch["float_wave"], ch["float_kind"])])
+        oracle.nll_grad_shape(A.astype(np.complex64), dA.astype(np.complex64), Am.astype(np.complex64),
+                              dAm.astype(np.complex64), ch["float_wave"], ch["V"], n_factor=ch["n_factor"],
+                              n_gen=ch["n_gen"])
+        t_tot += time.perf_counter() - t0
+        done += 1
+        work_done += (ch["n"] + ch["n_mc"]) * ch["K"]
+        if t_tot >= seconds:
+            break
+    work_all = float(sum((c["n"] + c["n_mc"]) * c["K"] for c in chans))
+    full_s = t_tot * work_all / work_done
+    n_all = sum(c["n"] for c in chans)
+    return {"value": n_all / full_s, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+            "nproc": os.cpu_count(), "full_iteration_s": full_s, "full_iteration_extrapolated": done < len(chans),
+            "sample": f"FP64 amplitudes (with mass and width derivatives) and -lnL+gradient of the {done} smallest of "
+                      f"{len(chans)} channels, {t_tot:.1f} s; one evaluation of all channels extrapolated linearly in "
+                      f"events x waves ({work_done / work_all:.4f} of the work): {full_s:.1f} s"}
+
+
+def run_uneven(args, world, rank, local):
+    import torch
+
+    from paper_1108_5882_gb300 import build, pwa
+    if rank == 0 or world > 1:
+        build.build()
+    torch.cuda.set_device(local)
+    h = pwa.Handle(local)
+    chans = setup_uneven(h, rank)
+    descs = [dict(waves=c["waves"], kin=c["kin"], n=c["n"], kin_mc=c["kin_mc"], n_mc=c["n_mc"], n_gen=c["n_gen"],
+                  n_factor=c["n_factor"], float_wave=c["float_wave"], float_kind=c["float_kind"]) for c in chans]
+    V = torch.from_numpy(np.concatenate([c["V"] for c in chans])).cuda()
+    theta = torch.tensor(np.concatenate([c["theta"] for c in chans]), dtype=torch.float64, device="cuda")
+    nll = torch.zeros(len(chans), dtype=torch.float64, device="cuda")
+    grad = torch.zeros(sum(2 * c["K"] + len(c["float_wave"]) for c in chans), dtype=torch.float64, device="cuda")
+    n_data = sum(c["n"] for c in chans)
+    n_events = sum(c["n"] + c["n_mc"] for c in chans)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.pwa_nll_grad_uneven(descs, V, theta, nll, grad)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    with sampler:
+        torch.cuda._sleep(int(min(2.0, 3e-3 * args.steps + 0.02) * 2.0e9))
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = tot_ms / args.steps
+    value = job_rate(n_data * args.steps, world, tot_ms * 1e-3)
+    ok = h.pwa_sync_status()
+    # ---- end to end: every step copies all kinematics from pinned host memory, evaluates, reads back
+    kin_h = [c["kin"].cpu().pin_memory() for c in chans]
+    kin_mc_h = [c["kin_mc"].cpu().pin_memory() for c in chans]
+    V_h, theta_h = V.cpu().pin_memory(), theta.cpu().pin_memory()
+    nll_h = torch.empty_like(nll, device="cpu").pin_memory()
+    grad_h = torch.empty_like(grad, device="cpu").pin_memory()
+    n_e2e = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        for c, a, b in zip(chans, kin_h, kin_mc_h):
+            c["kin"].copy_(a, non_blocking=True)
+            c["kin_mc"].copy_(b, non_blocking=True)
+        V.copy_(V_h, non_blocking=True)
+        theta.copy_(theta_h, non_blocking=True)
+        step()
+        nll_h.copy_(nll, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e, world)
+    h2d = sum(t.numel() * 4 for t in kin_h + kin_mc_h) + V_h.numel() * 8 + theta_h.numel() * 8
+    d2h = nll_h.numel() * 8 + grad_h.numel() * 8
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    ffma = fma_peak_tflops(sms)
+    flops = uneven_flops(chans)
+    kernel_ms = sum(step_ms) / len(step_ms)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    peak_hbm, _ = measured_peaks()
+    kin_bytes = 12.0 * n_events
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (accept-reject from I per channel on the GPU; flat MC from a seeded device generator)",
+        "config": {"workload": f"uneven: {len(chans)} channels, K ~ U{{4..48}}, N_data log-U[1e4, 4e6] (sum {n_data}), "
+                               f"N_MC = 5 N_data (sum {n_events - n_data}), 2 floating masses + 2 floating widths per "
+                               "channel; one step = f and the gradient in (V, M, Gamma) of every channel in one "
+                               "persistent launch, every amplitude recomputed from the kinematics",
+                   "channels": len(chans), "N_data_total": n_data, "N_MC_total": n_events - n_data,
+                   "units": "data events (the MC events are streamed in the same step and not counted)",
+                   "l2": f"inputs ({kin_bytes / 1e9:.1f} GB of kinematics) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": job_rate(n_data, world, e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "what": "pinned H2D of every channel's data and MC kinematics, V and theta; the persistent "
+                        "evaluation; D2H of f and the gradient"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ffma, "unit": "TFLOP/s", "frac": achieved / ffma,
+                     "traffic": None, "kernel": "k_uneven (persistent, all channels)", "flops_per_launch": flops,
+                     "kernel_us": kernel_ms * 1e3,
+                     "peak_kind": "measured now: FFMA microbenchmark (libpwa_peaks.so), FP32 SIMT",
+                     "hbm_frac": kin_bytes / (kernel_ms * 1e-3) / 1e9 / peak_hbm,
+                     "design": "recompute from kinematics (12 bytes per event); FP32-bound"},
+        "clocks": sampler.summary(), "status": pwa.status_string(ok), "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline_uneven(chans, args.cpu_seconds)
+    h.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_sample(wl_name, n_sample, n_sets=4):
     """The first n_sample events of the workload's wave set for the oracle, with n_sets of its
@@ -505,11 +704,50 @@ def cpu_baseline(wl, seconds):
             "full_iteration_extrapolated": ps < P}
 
 
+def run_reference_uneven(args, world):
+    """The oracle arm of the uneven workload: each step evaluates the smallest channel in full
+    (FP64 amplitudes with derivatives, then f and the gradient in V, M and Gamma) on flat events."""
+    import oracle
+    from paper_1108_5882_gb300 import inputs
+    n_ch, seed = UNEVEN
+    specs = inputs.uneven_channels(n_ch, seed)
+    c = min(range(n_ch), key=lambda i: (specs[i][1] + specs[i][2]) * specs[i][0])
+    K, N, NMC = specs[c]
+    ws = inputs.wave_set_spread(K, seed, stream=100 + c)
+    V = inputs.production_amplitudes(K, seed, stream=200 + c)
+    kin, kin_mc = inputs.kinematics(N, seed, 300 + c), inputs.kinematics(NMC, seed, 400 + c)
+    fwave, fkind = [0, K // 2, 0, K // 2], [0, 0, 1, 1]
+
+    def one():
+        A, dM, dW = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin, derivs=True)
+        Am, dMm, dWm = oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc, derivs=True)
+        dA = np.stack([(dM if k == 0 else dW)[r] for r, k in zip(fwave, fkind)]).astype(np.complex64)
+        dAm = np.stack([(dMm if k == 0 else dWm)[r] for r, k in zip(fwave, fkind)]).astype(np.complex64)
+        oracle.nll_grad_shape(A.astype(np.complex64), dA, Am.astype(np.complex64), dAm, fwave, V, n_factor=float(N))
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = N * args.steps / dt
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"each step: the smallest of {n_ch} channels (K={K}, N_data={N}, N_MC={NMC}) in full"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uneven: {n_ch} channels (oracle on its smallest channel per step)"},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
     import oracle
     oracle.build()
+    if args.workload == "uneven":
+        return run_reference_uneven(args, world)
     K, N, NMC, P, seed = WORKLOADS[args.workload]
     n_s = min(N, 100_000 if P == 1 else 250_000)
     A, V, Psi, _, _ = oracle_sample(args.workload, n_s, n_sets=4)
@@ -539,7 +777,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="multistart", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="multistart", choices=sorted(WORKLOADS) + ["uneven"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -553,7 +791,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
     world, rank, local = dist_init(args.gpus)
-    res = run_ours(args, world, rank, local)
+    res = (run_uneven if args.workload == "uneven" else run_ours)(args, world, rank, local)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

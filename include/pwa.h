@@ -323,9 +323,12 @@ PWA_API pwa_status pwa_nll_grad_shape(pwa_handle* h, const float* A, const float
  * four free parameters per resonance.  One start per channel: x = (Re V, Im V, theta), theta the
  * floating masses/widths.  One iteration is two launches for all channels together: the
  * persistent multi-channel evaluation of pwa_nll_grad_uneven (every amplitude recomputed from the
- * kinematics at the device trial point) and one L-BFGS step per channel (widths and masses kept
- * above 1e-3 GeV by a fraction-to-the-boundary step limit); check_every iterations are replayed
- * as one captured CUDA graph between host convergence checks. */
+ * kinematics at the device trial point) and one L-BFGS step per channel; the minimiser works in
+ * log(mass) and log(width) (widths and masses also kept above 1e-3 GeV by a fraction-to-the-
+ * boundary step limit), so result.grad_max and gtol refer to d f / d log(theta) for those;
+ * check_every iterations are replayed as one captured CUDA graph between host convergence
+ * checks.  A start whose shape parameter sits on its bound with the gradient pushing below it
+ * stops with status 2. */
 typedef struct pwa_shape_fit_desc {
     const pwa_wave* waves;      /* HOST [K]: J, lambda and the starting mass/width of each wave */
     int K;

@@ -29,6 +29,11 @@
 // The magnitude is signed (rho < 0 is the point (|rho|, phi + pi)), so there is no lower bound
 // to enforce, and the phase is left unwrapped.  With the gauge fixed, phi_0 is the frozen
 // component.  The results are reported as V in both cases.
+//
+// Floating shape parameters (resonance masses and widths, all positive) enter the minimiser as
+// log(theta): the gradient becomes theta d f / d theta, on the scale of the V components
+// instead of ~ n / Gamma, and no step can take a parameter to or below zero; a lower bound
+// (1e-3 GeV) is still kept by a fraction-to-the-boundary step limit in these coordinates.
 #include <cmath>
 #include <vector>
 
@@ -127,7 +132,7 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
         Vt[(int64_t)blockIdx.x * K + t] = make_float2((float)vt.x, (float)vt.y);
     }
     if (t < F) {
-        st.x[(int64_t)p * DM + 2 * K + t] = th.v[t];
+        st.x[(int64_t)p * DM + 2 * K + t] = log(th.v[t]);  // shape parameters: log coordinates
         theta_t[(int64_t)blockIdx.x * F + t] = th.v[t];
     }
     if (t == 0) {
@@ -154,7 +159,7 @@ __device__ __forceinline__ void write_trial(const double* x, const double* d, do
         const double2 v = coords_to_v(x[2 * t] + a * d[2 * t], x[2 * t + 1] + a * d[2 * t + 1], polar);
         Vrow[t] = make_float2((float)v.x, (float)v.y);
     }
-    if (t < F) th_row[t] = x[2 * K + t] + a * d[2 * K + t];
+    if (t < F) th_row[t] = exp(x[2 * K + t] + a * d[2 * K + t]);
 }
 
 // The step of start p (one block of 128 threads): fnew and gp = f and g [2K + F] at the trial point
@@ -193,6 +198,7 @@ __device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew
             sincos(xt[2 * a + 1], &sn, &cs);
             gv = (t & 1) ? xt[2 * a] * (gp[2 * a + 1] * cs - gp[2 * a] * sn) : gp[2 * a] * cs + gp[2 * a + 1] * sn;
         }
+        if (t >= 2 * K) gv *= exp(xt[t]);  // d f / d log(theta) = theta d f / d theta
         if (gauge && t == 1) gv = 0.0;
         q[t] = gv;  // gradient at the trial point (frozen gauge component)
     }
@@ -326,13 +332,21 @@ __device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew
             double amax = a0;
             for (int q = 0; q < F; ++q) {
                 const double dq = d[2 * K + q];
-                if (dq < 0.0) amax = fmin(amax, 0.9 * (x[2 * K + q] - lb[q]) / (-dq));
+                if (dq < 0.0) amax = fmin(amax, 0.9 * (x[2 * K + q] - log(lb[q])) / (-dq));
             }
             red[0] = amax;
         }
         __syncthreads();
         a0 = red[0];
         __syncthreads();
+        if (!(a0 > 0.0)) {
+            // a shape parameter sits on its lower bound and the direction points below it: no
+            // feasible step is left, so the start stops (line search failed) instead of
+            // evaluating zero-length steps until the iteration bound
+            if (t == 0) st.status[p] = 2;
+            write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
+            return;
+        }
     }
     if (t == 0) {
         st.gtd[p] = gtd;
@@ -397,7 +411,7 @@ __global__ void k_fit_export_x(FitState st, int K, int D, int p, int mode, doubl
         xout[2 * t] = v.x;
         xout[2 * t + 1] = v.y;
     } else if (t >= 2 * K && t < D) {
-        xout[t] = st.x[(int64_t)p * DM + t];
+        xout[t] = exp(st.x[(int64_t)p * DM + t]);
     }
 }
 

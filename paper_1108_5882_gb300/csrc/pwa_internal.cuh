@@ -239,7 +239,7 @@ struct UnevenChannel {
     const float* w_mc;
     int64_t n, ld, n_mc, ld_mc;
     double scale;  // n_factor / n_gen
-    int K, F, ng, nchunk;
+    int K, F, ng;
     int epi;       // events per work item
     int items_d, items_m;
     int voff, toff, goff;
@@ -248,7 +248,6 @@ struct UnevenChannel {
     double Md[PWA_MAX_WAVES], Wd[PWA_MAX_WAVES];
     signed char qM[PWA_MAX_WAVES], qW[PWA_MAX_WAVES];  // floating parameter of the mass / width, -1 fixed
     int gend[PWA_MAX_WAVES], gJ[PWA_MAX_WAVES], glam[PWA_MAX_WAVES];
-    int cgrp[PWA_MAX_WAVES / 16];  // group of the first wave of each 16-wave chunk
 };
 struct UnevenPlan {
     int n_ch = 0;
@@ -270,9 +269,6 @@ cudaError_t launch_nll_shape(const float2* A, const float2* dA, int K, int64_t n
                              const int* fwave, int F, const float2* V, double nfac, double* nll, double* grad,
                              void* ws, size_t ws_bytes, unsigned* counter, int* badw, int* status, int sm_count,
                              cudaStream_t st);
-cudaError_t launch_amp_floating(int J, int lam, const double* Mdev, double Mc, const double* Gdev, double Gc,
-                                const float* kin, int64_t n, int64_t ld, float2* A, float2* dM, float2* dG,
-                                int sm_count, cudaStream_t st);
 
 size_t moments_workspace(int n_bins, int T);
 size_t toy_moments_workspace(int n_bins, int T);

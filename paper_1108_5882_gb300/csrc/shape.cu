@@ -14,9 +14,8 @@
 // of (scalar, 2K gradient sums, F shape sums), and the last block sums the data partials and the
 // MC partials separately, in block order, and combines them in FP64.
 //
-// k_amp_floating recomputes one floating wave's amplitudes and derivatives with its mass and
-// width read from device memory (the fitter's trial point), so a fit iteration needs no host
-// round trip.
+// (The multi-channel fitter does not use this kernel: its evaluation, in uneven.cu, recomputes
+// the amplitudes from the kinematics at the device trial point.)
 #include "amp_model.cuh"
 #include "pwa_internal.cuh"
 
@@ -184,57 +183,6 @@ __global__ void __launch_bounds__(PWA_THREADS) k_nll_shape(ShapeArgs s, const fl
         grad[v - 1] = isbad ? 0.0 : (-2.0 * sval[0][v] + 2.0 * scale * sval[1][v]);
 }
 
-// Amplitudes (and their mass/width derivatives) of one wave with M and Gamma read from device
-// memory: M = Mdev ? *Mdev : Mc, G = Gdev ? *Gdev : Gc.  Same model and FP32 arithmetic as
-// k_amplitudes; the two-float mass split is formed on the device.
-__global__ void __launch_bounds__(PWA_THREADS) k_amp_floating(int J, int lam, const double* __restrict__ Mdev, double Mc,
-                                                              const double* __restrict__ Gdev, double Gc,
-                                                              const float* __restrict__ kin, int64_t n, int64_t ld,
-                                                              float2* __restrict__ A, float2* __restrict__ dM,
-                                                              float2* __restrict__ dG) {
-    const double M = Mdev ? *Mdev : Mc;
-    const double G = Gdev ? *Gdev : Gc;
-    WaveTable wt;
-    wt.K = 1;
-    wt.J[0] = J;
-    wt.lam[0] = lam;
-    wt.Mhi[0] = (float)M;
-    wt.Mlo[0] = (float)(M - (double)wt.Mhi[0]);
-    wt.W[0] = (float)G;
-    wt.MW[0] = (float)(M * G);
-    wt.ng = 1;
-    wt.gend[0] = 1;
-    wt.gord[0] = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += stride) {
-        if (i >= n) {
-            A[i] = make_float2(0.f, 0.f);
-            if (dM) dM[i] = make_float2(0.f, 0.f);
-            if (dG) dG[i] = make_float2(0.f, 0.f);
-            continue;
-        }
-        const float m = __ldg(kin + i), ct = __ldg(kin + ld + i), ph = __ldg(kin + 2 * ld + i);
-        EventAngles t;
-        event_angles(ct, ph, t);
-        const float2 ang = wave_angle(wt, 0, t);
-        float dr;
-        const float2 id = bw_inv_den(wt, 0, m, &dr);
-        const float MW = wt.MW[0];
-        A[i] = cmul(make_float2(MW * id.x, MW * id.y), ang);
-        if (dM || dG) {
-            const float2 id2 = cmul(id, id);
-            if (dM) {
-                const float cm = -wt.W[0] * (wt.Mhi[0] * wt.Mhi[0] + m * m);
-                dM[i] = cmul(make_float2(cm * id2.x, cm * id2.y), ang);
-            }
-            if (dG) {
-                const float cw = (wt.Mhi[0] + wt.Mlo[0]) * dr;
-                dG[i] = cmul(make_float2(cw * id2.x, cw * id2.y), ang);
-            }
-        }
-    }
-}
-
 int kmax_shape(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64; }
 
 template <int KMAX>
@@ -300,16 +248,6 @@ cudaError_t launch_nll_shape(const float2* A, const float2* dA, int K, int64_t n
         case 48: return shape_launch<48>(a, V, scale, ws, ws_bytes, counter, badw, status, nll, grad, sm_count, st);
         default: return shape_launch<64>(a, V, scale, ws, ws_bytes, counter, badw, status, nll, grad, sm_count, st);
     }
-}
-
-cudaError_t launch_amp_floating(int J, int lam, const double* Mdev, double Mc, const double* Gdev, double Gc,
-                                const float* kin, int64_t n, int64_t ld, float2* A, float2* dM, float2* dG,
-                                int sm_count, cudaStream_t st) {
-    if (ld == 0) return cudaSuccess;
-    int64_t blocks = (ld + PWA_THREADS - 1) / PWA_THREADS;
-    if (blocks > (int64_t)sm_count * 8) blocks = (int64_t)sm_count * 8;
-    k_amp_floating<<<(unsigned)blocks, PWA_THREADS, 0, st>>>(J, lam, Mdev, Mc, Gdev, Gc, kin, n, ld, A, dM, dG);
-    return cudaGetLastError();
 }
 
 }  // namespace pwa

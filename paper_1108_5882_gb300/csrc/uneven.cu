@@ -20,12 +20,15 @@
 // gradient.  The last block to leave resets the item counter, so consecutive launches (and
 // graph replays) need no memset.
 //
-// Per 4096-event sub-tile, phase A walks the waves group by group (groups of equal (J, lambda)
-// share P_J(cos theta) exp(i lambda phi)) to form u, then I, ln I and w = u / I (data) or
-// w = w_j u (MC), kept in shared memory with cos(phi), sin(phi).  Phase B runs over chunks of 16
-// waves: per event y = conj(Y_g) w for the current group and, per wave, g_a += conj(BW_a) y with
-// BW_a recomputed, plus the mass and width derivative terms of floating waves.  Each thread
-// accumulates in FP32 over its 16 events of the sub-tile; the block combines in double-single.
+// An item is processed in tiles of 256 events.  Phase A, one thread per event: the waves are
+// walked group by group (groups of equal (J, lambda) share P_J(cos theta) exp(i lambda phi)) to
+// form u, then I, ln I (data) or w_j I (MC), and w = u / I or w_j u; the per-group products
+// y_g = conj(Y_g) w go to shared memory.  Phase B, one thread per (wave a, subset r of the tile's
+// events): g_a += conj(BW_a(m_e)) y_{g(a),e} over the subset, with the wave's parameters held in
+// registers, plus the mass and width derivative terms on the threads of floating waves.  Each
+// thread's FP32 tile sums enter double-single accumulators; the item's sums combine the subsets
+// of each wave in a fixed order.  Small loops and no per-wave register arrays keep the code
+// compact (its instruction fetch, not the arithmetic, limited earlier designs).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -36,12 +39,13 @@ namespace pwa {
 
 namespace {
 
-constexpr int UN_KPT = 16;                      // waves per phase-B chunk (32 accumulators)
-constexpr int UN_NCH_MAX = PWA_MAX_WAVES / UN_KPT;
-constexpr int UN_SUB = 4096;                    // events per sub-tile (cached in shared memory)
-constexpr int UN_EPT = UN_SUB / PWA_THREADS;    // events per thread per sub-tile
+constexpr int UN_EPT = 2;                       // phase A: events per thread
+constexpr int UN_TILE = UN_EPT * PWA_THREADS;   // events per tile
+constexpr int UN_NG = 12;                       // groups of equal (J, lambda) per channel, at most
+constexpr int UN_NFW = PWA_MAX_FLOAT;           // floating waves per channel, at most
 constexpr int UN_NW = PWA_THREADS / 32;
 constexpr int64_t UN_ITEM_WORK = 1 << 19;       // target wave-events per item
+constexpr int64_t UN_ITEM_MIN_EV = 4096;
 constexpr int64_t UN_ITEM_MAX_EV = 65536;
 
 __constant__ float c_un_inv_int[9] = {1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9};
@@ -52,12 +56,6 @@ struct Leg {
     float pcur, pprev;
     int jc;
 };
-
-__device__ __forceinline__ void leg_reset(Leg& L) {
-    L.pcur = 1.f;
-    L.pprev = 0.f;
-    L.jc = 0;
-}
 
 // Angular factor P_J(cos theta) exp(i lambda phi) of a group; J must not decrease between calls.
 __device__ __forceinline__ float2 group_angle(Leg& L, int J, int lam, float ct, float c1, float s1) {
@@ -78,51 +76,6 @@ __device__ __forceinline__ float2 group_angle(Leg& L, int J, int lam, float ct, 
     return make_float2(L.pcur * er, L.pcur * ei);
 }
 
-struct UnevenItemSmem {
-    float4 prm[PWA_MAX_WAVES];  // per sorted wave: M_hi, M_lo, M G, (M G)^2
-    float2 V[PWA_MAX_WAVES];    // production amplitude of sorted wave s
-    float W[PWA_MAX_WAVES];     // width (floating waves' derivative terms)
-    int ord[PWA_MAX_WAVES];     // original index of sorted wave s
-    int gend[PWA_MAX_WAVES];
-    int gJ[PWA_MAX_WAVES], glam[PWA_MAX_WAVES];
-    signed char qM[PWA_MAX_WAVES], qW[PWA_MAX_WAVES];
-    int cgrp[UN_NCH_MAX];
-    ff acc[1 + 2 * PWA_MAX_WAVES + PWA_MAX_FLOAT];  // item sums (original wave order)
-    float red[UN_NW][32];
-    ff lred[UN_NW];
-    float sred[UN_NW][PWA_MAX_FLOAT];
-    int item, last, bad;
-};
-
-__device__ __forceinline__ void item_setup(UnevenItemSmem& sm, const UnevenChannel& C, const float2* __restrict__ V,
-                                           const double* __restrict__ theta) {
-    const int t = threadIdx.x;
-    const int K = C.K;
-    if (t < K) {
-        const int a = C.ord[t];
-        double M = C.Md[t], G = C.Wd[t];
-        if (C.qM[t] >= 0) M = theta[C.toff + C.qM[t]];
-        if (C.qW[t] >= 0) G = theta[C.toff + C.qW[t]];
-        const float Mh = (float)M;
-        const float Ml = (float)(M - (double)Mh);
-        const float MW = (float)(M * G);
-        sm.prm[t] = make_float4(Mh, Ml, MW, MW * MW);
-        sm.W[t] = (float)G;
-        sm.V[t] = V[C.voff + a];
-        sm.ord[t] = a;
-        sm.qM[t] = C.qM[t];
-        sm.qW[t] = C.qW[t];
-    }
-    if (t < C.ng) {
-        sm.gend[t] = C.gend[t];
-        sm.gJ[t] = C.gJ[t];
-        sm.glam[t] = C.glam[t];
-    }
-    if (t < UN_NCH_MAX) sm.cgrp[t] = C.cgrp[t];
-    for (int v = t; v < 1 + 2 * K + C.F; v += PWA_THREADS) sm.acc[v] = ff_zero();
-    if (t == 0) sm.bad = 0;
-}
-
 // Breit-Wigner BW = M G / (M^2 - m^2 - i M G) of one wave at m, and M^2 - m^2, from its
 // parameters (M_hi, M_lo, M G, (M G)^2); the reciprocal of |D|^2 by __fdividef (2 ulp).
 __device__ __forceinline__ float2 bw_of(float4 p, float m, float* dr_out) {
@@ -133,23 +86,20 @@ __device__ __forceinline__ float2 bw_of(float4 p, float m, float* dr_out) {
     return make_float2(dr * t1, p.z * t1);
 }
 
-// Block sum of one value per lane l < 32 (value l of every thread) into sm.acc[dst(l)].
-template <class Dst>
-__device__ __forceinline__ void block_add_32(UnevenItemSmem& sm, float (&x)[32], Dst dst) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    warp_transpose_reduce32(x);
-    sm.red[warp][lane] = x[0];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int d = dst(lane);
-        if (d >= 0) {
-            ff s = sm.acc[d];
-            for (int w = 0; w < UN_NW; ++w) s = ff_add_f(s, sm.red[w][lane]);
-            sm.acc[d] = s;
-        }
-    }
-    __syncthreads();
-}
+struct UnevenSmem {
+    float4 prm[PWA_MAX_WAVES];  // per sorted wave: M_hi, M_lo, M G, (M G)^2
+    float2 V[PWA_MAX_WAVES];    // production amplitude of sorted wave s
+    int gend[UN_NG], gJ[UN_NG], glam[UN_NG];
+    // floating waves: sorted index, group, width, 1 / (M G), and their mass / width parameter
+    int fs[UN_NFW], fg[UN_NFW], fqM[UN_NFW], fqW[UN_NFW];
+    float fW[UN_NFW], frMW[UN_NFW];
+    float2 y[UN_NG][UN_TILE + 1];  // per group and event of the tile: conj(Y_g) w (Y_g during phase A)
+    float m[UN_TILE];
+    ff gre[PWA_THREADS], gim[PWA_THREADS];  // item sums per (wave, subset) thread
+    float2 sh[UN_NW][2 * UN_NFW];           // per warp: the floating waves' mass and width sums
+    ff lred[UN_NW];
+    int nfw, item, last, bad;
+};
 
 __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* __restrict__ chans, int n_ch,
                                                            const int2* __restrict__ items, int n_items,
@@ -157,8 +107,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
                                                            const double* __restrict__ theta, double* __restrict__ nll,
                                                            double* __restrict__ grad, float2* __restrict__ part,
                                                            unsigned* __restrict__ ctrl, int* __restrict__ status) {
-    extern __shared__ float4 s_ev[];  // [UN_SUB]: (Re w, Im w, cos phi, sin phi) of the sub-tile
-    __shared__ UnevenItemSmem sm;
+    __shared__ UnevenSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned* tickets = ctrl + 1;
     unsigned* bad_ch = ctrl + 1 + n_ch;
@@ -171,7 +120,42 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
         if (it >= n_items) break;
         const int2 wi = items[it];
         const UnevenChannel& C = chans[wi.x];
-        item_setup(sm, C, V, theta);
+        const int K = C.K, F = C.F, ng = C.ng;
+        // ---- per item: the channel's wave table at the trial point
+        if (tid < K) {
+            double M = C.Md[tid], G = C.Wd[tid];
+            if (C.qM[tid] >= 0) M = theta[C.toff + C.qM[tid]];
+            if (C.qW[tid] >= 0) G = theta[C.toff + C.qW[tid]];
+            const float Mh = (float)M;
+            const float MW = (float)(M * G);
+            sm.prm[tid] = make_float4(Mh, (float)(M - (double)Mh), MW, MW * MW);
+            sm.V[tid] = V[C.voff + C.ord[tid]];
+        }
+        if (tid < ng) {
+            sm.gend[tid] = C.gend[tid];
+            sm.gJ[tid] = C.gJ[tid];
+            sm.glam[tid] = C.glam[tid];
+        }
+        if (tid == 0) {
+            // the floating waves in sorted order, with their parameters' indices
+            int nf = 0, g = 0;
+            for (int s = 0; s < K; ++s) {
+                while (C.gend[g] <= s) ++g;
+                if (C.qM[s] >= 0 || C.qW[s] >= 0) {
+                    sm.fs[nf] = s;
+                    sm.fg[nf] = g;
+                    sm.fqM[nf] = C.qM[s];
+                    sm.fqW[nf] = C.qW[s];
+                    const double Mf = C.qM[s] >= 0 ? theta[C.toff + C.qM[s]] : C.Md[s];
+                    const double Gf = C.qW[s] >= 0 ? theta[C.toff + C.qW[s]] : C.Wd[s];
+                    sm.fW[nf] = (float)Gf;
+                    sm.frMW[nf] = 1.f / (float)(Mf * Gf);
+                    ++nf;
+                }
+            }
+            sm.nfw = nf;
+            sm.bad = 0;
+        }
         const bool is_mc = wi.y >= C.items_d;
         const int li = is_mc ? wi.y - C.items_d : wi.y;
         const float* kin = is_mc ? C.kin_mc : C.kin;
@@ -180,149 +164,175 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
         const float* wm = is_mc ? C.w_mc : nullptr;
         const int64_t begin = (int64_t)li * C.epi;
         const int64_t end = min(begin + (int64_t)C.epi, ns);
-        const int K = C.K, F = C.F, ng = C.ng, nchunk = C.nchunk;
+        // phase-B role of this thread: wave a (sorted), event subset r of R
+        const int R = PWA_THREADS / K;
+        const int a = tid % K, r = tid / K;
+        const bool active = r < R;
         __syncthreads();
-
-        ff lacc = ff_zero();
+        float4 pa = make_float4(0.f, 0.f, 1.f, 1.f);
+        int ga = 0;
+        if (active) {
+            pa = sm.prm[a];
+            while (sm.gend[ga] <= a) ++ga;
+        }
+        const int nfw = sm.nfw;
+        ff gre = ff_zero(), gim = ff_zero(), lacc = ff_zero();
+        float shM[UN_NFW], shW[UN_NFW];  // floating waves' d/dM and d/dG sums of the item (phase A)
+#pragma unroll
+        for (int j = 0; j < UN_NFW; ++j) shM[j] = shW[j] = 0.f;
         bool bad = false;
-        float gsh[PWA_MAX_FLOAT];
-#pragma unroll
-        for (int q = 0; q < PWA_MAX_FLOAT; ++q) gsh[q] = 0.f;
 
-        for (int64_t s0 = begin; s0 < end; s0 += UN_SUB) {
-            // ---- phase A: u, I, ln I (or w_j I), w per event; cache w and (cos, sin) phi
-            for (int k = 0; k < UN_EPT; ++k) {
-                const int e = k * PWA_THREADS + tid;
-                const int64_t i = s0 + e;
-                const bool valid = i < end;
-                const float m = valid ? __ldg(kin + i) : 2.f;
-                const float ct = valid ? __ldg(kin + ld + i) : 0.f;
-                const float ph = valid ? __ldg(kin + 2 * ld + i) : 0.f;
-                float s1, c1;
-                sincosf(ph, &s1, &c1);
-                Leg L;
-                leg_reset(L);
-                float ur = 0.f, ui = 0.f;
-                int s = 0;
-                for (int g = 0; g < ng; ++g) {
-                    const float2 Y = group_angle(L, sm.gJ[g], sm.glam[g], ct, c1, s1);
-                    float zr = 0.f, zi = 0.f;
-                    const int ge = sm.gend[g];
-                    for (; s < ge; ++s) {
-                        float dr;
-                        const float2 bw = bw_of(sm.prm[s], m, &dr);
-                        const float2 v = sm.V[s];
-                        cmac(zr, zi, v.x, v.y, bw.x, bw.y);
-                    }
-                    cmac(ur, ui, Y.x, Y.y, zr, zi);
-                }
-                const float I0 = fmaf(ur, ur, ui * ui);
-                float wr = 0.f, wi = 0.f;
-                if (valid) {
-                    if (!is_mc) {
-                        if (intensity_ok(I0)) {
-                            lacc = ff_add_f(lacc, __logf(I0));
-                            const float r = __frcp_rn(I0);
-                            wr = ur * r;
-                            wi = ui * r;
-                        } else {
-                            bad = true;
-                        }
-                    } else {
-                        const float wt = wm ? __ldg(wm + i) : 1.f;
-                        lacc = ff_add_f(lacc, wt * I0);
-                        wr = wt * ur;
-                        wi = wt * ui;
-                    }
-                }
-                s_ev[e] = make_float4(wr, wi, c1, s1);
-            }
-            __syncthreads();
-            // ---- phase B: gradient sums over chunks of UN_KPT waves
-            for (int c = 0; c < nchunk; ++c) {
-                float acc[32];
+        for (int64_t t0 = begin; t0 < end; t0 += UN_TILE) {
+            const int ntile = (int)min((int64_t)UN_TILE, end - t0);
+            // ---- phase A: UN_EPT events per thread; u, I, w; conj(Y_g) w per group into shared
+            // memory; the floating waves' mass and width derivative terms
+            {
+                float m[UN_EPT], ct[UN_EPT], c1[UN_EPT], s1[UN_EPT], ur[UN_EPT], ui[UN_EPT];
+                Leg L[UN_EPT];
 #pragma unroll
-                for (int v = 0; v < 32; ++v) acc[v] = 0.f;
-                const int sb = c * UN_KPT;
                 for (int k = 0; k < UN_EPT; ++k) {
                     const int e = k * PWA_THREADS + tid;
-                    const int64_t i = s0 + e;
-                    const bool valid = i < end;
-                    const float m = valid ? __ldg(kin + i) : 2.f;
-                    const float ct = valid ? __ldg(kin + ld + i) : 0.f;
-                    const float4 ev = s_ev[e];
-                    Leg L;
-                    leg_reset(L);
-                    int g = sm.cgrp[c];
-                    float2 Y = group_angle(L, sm.gJ[g], sm.glam[g], ct, ev.z, ev.w);
-                    // y = conj(Y) w
-                    float yr = Y.x * ev.x + Y.y * ev.y, yi = Y.x * ev.y - Y.y * ev.x;
-                    int gnext = sm.gend[g];
+                    const int64_t i = t0 + e;
+                    const bool valid = e < ntile;
+                    m[k] = valid ? __ldg(kin + i) : 2.f;
+                    ct[k] = valid ? __ldg(kin + ld + i) : 0.f;
+                    const float ph = valid ? __ldg(kin + 2 * ld + i) : 0.f;
+                    sincosf(ph, &s1[k], &c1[k]);
+                    L[k] = Leg{1.f, 0.f, 0};
+                    ur[k] = ui[k] = 0.f;
+                }
+                int s = 0;
+                for (int g = 0; g < ng; ++g) {
+                    float2 Y[UN_EPT];
+                    float zr[UN_EPT], zi[UN_EPT];
 #pragma unroll
-                    for (int j = 0; j < UN_KPT; ++j) {
-                        const int s = sb + j;
-                        if (s < K) {
-                            if (s == gnext) {
-                                ++g;
-                                Y = group_angle(L, sm.gJ[g], sm.glam[g], ct, ev.z, ev.w);
-                                yr = Y.x * ev.x + Y.y * ev.y;
-                                yi = Y.x * ev.y - Y.y * ev.x;
-                                gnext = sm.gend[g];
-                            }
-                            const float4 p = sm.prm[s];
+                    for (int k = 0; k < UN_EPT; ++k) {
+                        Y[k] = group_angle(L[k], sm.gJ[g], sm.glam[g], ct[k], c1[k], s1[k]);
+                        sm.y[g][k * PWA_THREADS + tid] = Y[k];
+                        zr[k] = zi[k] = 0.f;
+                    }
+                    const int ge = sm.gend[g];
+                    for (; s < ge; ++s) {
+                        const float4 p = sm.prm[s];
+                        const float2 v = sm.V[s];
+#pragma unroll
+                        for (int k = 0; k < UN_EPT; ++k) {
                             float dr;
-                            const float2 bw = bw_of(p, m, &dr);
-                            cmac_conj(acc[2 * j], acc[2 * j + 1], bw.x, bw.y, yr, yi);
-                            const int qm = sm.qM[s], qw = sm.qW[s];
-                            if (qm >= 0 || qw >= 0) {
-                                // dA/dM = -G (M^2 + m^2) Y / D^2, dA/dG = M (M^2 - m^2) Y / D^2; with
-                                // 1/D = BW / (M G): R = Re(V (1/D)^2 conj(y))
-                                const float rinv = __fdividef(1.f, p.z);
-                                const float idr = bw.x * rinv, idi = bw.y * rinv;
-                                const float i2r = idr * idr - idi * idi, i2i = 2.f * idr * idi;
-                                const float2 v = sm.V[s];
-                                const float qr = v.x * i2r - v.y * i2i, qi = v.x * i2i + v.y * i2r;
-                                const float R = qr * yr + qi * yi;
-                                const float cm = -sm.W[s] * (p.x * p.x + m * m);
-                                const float cw = (p.x + p.y) * dr;
+                            const float2 bw = bw_of(p, m[k], &dr);
+                            cmac(zr[k], zi[k], v.x, v.y, bw.x, bw.y);
+                        }
+                    }
 #pragma unroll
-                                for (int q = 0; q < PWA_MAX_FLOAT; ++q) {
-                                    if (q == qm) gsh[q] = fmaf(cm, R, gsh[q]);
-                                    if (q == qw) gsh[q] = fmaf(cw, R, gsh[q]);
-                                }
+                    for (int k = 0; k < UN_EPT; ++k) cmac(ur[k], ui[k], Y[k].x, Y[k].y, zr[k], zi[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < UN_EPT; ++k) {
+                    const int e = k * PWA_THREADS + tid;
+                    const float I0 = fmaf(ur[k], ur[k], ui[k] * ui[k]);
+                    float wr = 0.f, wi = 0.f;
+                    if (e < ntile) {
+                        if (!is_mc) {
+                            if (intensity_ok(I0)) {
+                                lacc = ff_add_f(lacc, __logf(I0));
+                                const float rI = __frcp_rn(I0);
+                                wr = ur[k] * rI;
+                                wi = ui[k] * rI;
+                            } else {
+                                bad = true;
                             }
+                        } else {
+                            const float wt = wm ? __ldg(wm + t0 + e) : 1.f;
+                            lacc = ff_add_f(lacc, wt * I0);
+                            wr = wt * ur[k];
+                            wi = wt * ui[k];
+                        }
+                    }
+                    for (int g = 0; g < ng; ++g) {
+                        const float2 Y = sm.y[g][e];
+                        sm.y[g][e] = make_float2(Y.x * wr + Y.y * wi, Y.x * wi - Y.y * wr);  // conj(Y) w
+                    }
+                    sm.m[e] = m[k];
+                    // floating wave j (sorted index fs, group fg): d/dM and d/dG of Re(conj(w) V A):
+                    // dA/dM = -G (M^2 + m^2) Y / D^2, dA/dG = M (M^2 - m^2) Y / D^2, 1/D = BW / (M G),
+                    // so each is its coefficient times Re(V (1/D)^2 conj(y)), y = conj(Y) w
+#pragma unroll
+                    for (int j = 0; j < UN_NFW; ++j) {
+                        if (j < nfw) {
+                            const int sj = sm.fs[j];
+                            const float4 p = sm.prm[sj];
+                            const float2 v = sm.V[sj];
+                            const float2 y = sm.y[sm.fg[j]][e];
+                            float dr;
+                            const float2 bw = bw_of(p, m[k], &dr);
+                            const float rMW = sm.frMW[j];
+                            const float idr = bw.x * rMW, idi = bw.y * rMW;
+                            const float i2r = idr * idr - idi * idi, i2i = 2.f * idr * idi;
+                            const float qr = v.x * i2r - v.y * i2i, qi = v.x * i2i + v.y * i2r;
+                            const float Rr = qr * y.x + qi * y.y;
+                            shM[j] = fmaf(-sm.fW[j] * (p.x * p.x + m[k] * m[k]), Rr, shM[j]);
+                            shW[j] = fmaf((p.x + p.y) * dr, Rr, shW[j]);
                         }
                     }
                 }
-                const int Kc = K - sb;
-                block_add_32(sm, acc, [&](int l) { return (l >> 1) < Kc ? 1 + 2 * sm.ord[sb + (l >> 1)] + (l & 1) : -1; });
             }
+            __syncthreads();
+            // ---- phase B: thread = (wave a, subset r); g_a += conj(BW_a(m_e)) y_e over the tile
+            if (active) {
+                float ar = 0.f, ai = 0.f;
+                const float2* yg = sm.y[ga];
+#pragma unroll 4
+                for (int e = r; e < ntile; e += R) {
+                    float dr;
+                    const float2 bw = bw_of(pa, sm.m[e], &dr);
+                    const float2 y = yg[e];
+                    cmac_conj(ar, ai, bw.x, bw.y, y.x, y.y);
+                }
+                gre = ff_add_f(gre, ar);
+                gim = ff_add_f(gim, ai);
+            }
+            __syncthreads();
         }
-        // ---- item sums of the scalar and the shape terms
+        // ---- item sums: per wave over the subsets r in order; ln I (or w I) and the floating
+        // waves' sums over the warps in order
+        sm.gre[tid] = gre;
+        sm.gim[tid] = gim;
 #pragma unroll
         for (int mm = 16; mm > 0; mm >>= 1) lacc = ff_add(lacc, ff_shfl_xor(lacc, mm));
 #pragma unroll
-        for (int q = 0; q < PWA_MAX_FLOAT; ++q) gsh[q] = warp_sum(gsh[q]);
+        for (int j = 0; j < UN_NFW; ++j) {
+            shM[j] = warp_sum(shM[j]);
+            shW[j] = warp_sum(shW[j]);
+        }
         if (lane == 0) {
             sm.lred[warp] = lacc;
 #pragma unroll
-            for (int q = 0; q < PWA_MAX_FLOAT; ++q) sm.sred[warp][q] = gsh[q];
+            for (int j = 0; j < UN_NFW; ++j) sm.sh[warp][2 * j] = make_float2(shM[j], shW[j]);
         }
         const int any_bad = __syncthreads_or(bad ? 1 : 0);
         const int NV = 1 + 2 * K + F;
         float2* slot = part + C.poff + (int64_t)wi.y * NV;
-        for (int v = tid; v < NV; v += PWA_THREADS) {
-            ff t;
-            if (v == 0) {
-                t = ff_zero();
-                for (int w = 0; w < UN_NW; ++w) t = ff_add(t, sm.lred[w]);
-            } else if (v <= 2 * K) {
-                t = sm.acc[v];
-            } else {
-                t = ff_zero();
-                for (int w = 0; w < UN_NW; ++w) t = ff_add_f(t, sm.sred[w][v - 1 - 2 * K]);
+        if (tid < K) {
+            ff tr = ff_zero(), ti = ff_zero();
+            for (int rr = 0; rr < R; ++rr) {
+                const int t = rr * K + tid;
+                tr = ff_add(tr, sm.gre[t]);
+                ti = ff_add(ti, sm.gim[t]);
             }
-            slot[v] = make_float2(t.hi, t.lo);
+            const int o = C.ord[tid];
+            slot[1 + 2 * o] = make_float2(tr.hi, tr.lo);
+            slot[2 + 2 * o] = make_float2(ti.hi, ti.lo);
+        } else if (tid >= PWA_THREADS - 2 * UN_NFW) {
+            const int jj = tid - (PWA_THREADS - 2 * UN_NFW), j = jj >> 1, kind = jj & 1;
+            if (j < nfw) {
+                ff t = ff_zero();
+                for (int w = 0; w < UN_NW; ++w) t = ff_add_f(t, kind ? sm.sh[w][2 * j].y : sm.sh[w][2 * j].x);
+                const int q = kind ? sm.fqW[j] : sm.fqM[j];
+                if (q >= 0) slot[1 + 2 * K + q] = make_float2(t.hi, t.lo);
+            }
+        } else if (tid == PWA_THREADS - 2 * UN_NFW - 1) {
+            ff t = ff_zero();
+            for (int w = 0; w < UN_NW; ++w) t = ff_add(t, sm.lred[w]);
+            slot[0] = make_float2(t.hi, t.lo);
         }
         if (any_bad && tid == 0) atomicOr(bad_ch + wi.x, 1u);
         __threadfence();
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
             const float2* cp = part + C.poff;
             const int nd = C.items_d, nm = C.items_m;
             const int nch = PWA_THREADS / NV > 0 ? PWA_THREADS / NV : 1;
-            // sm.red / sm.acc are free now: combine chunk sums in registers via shared ff
+            float2* sfin = reinterpret_cast<float2*>(&sm.y[0][0]);  // the tile buffers are free now
             for (int set = 0; set < 2; ++set) {
                 const int first = set == 0 ? 0 : nd;
                 const int count = set == 0 ? nd : nm;
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
                     const int v = vv % NV, chn = vv / NV;
                     const int cnt = count > chn ? (count - chn + nch - 1) / nch : 0;
                     const ff t = ff_sum_strided(cp, (int64_t)(first + chn) * NV + v, (int64_t)nch * NV, cnt);
-                    s_ev[set * nch * NV + vv] = make_float4(t.hi, t.lo, 0.f, 0.f);
+                    sfin[set * nch * NV + vv] = make_float2(t.hi, t.lo);
                 }
             }
             __syncthreads();
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
                 for (int set = 0; set < 2; ++set) {
                     ff t = ff_zero();
                     for (int chn = 0; chn < nch; ++chn) {
-                        const float4 x = s_ev[set * nch * NV + chn * NV + v];
+                        const float2 x = sfin[set * nch * NV + chn * NV + v];
                         t = ff_add(t, ff{x.x, x.y});
                     }
                     val[set] = ff_to_double(t);
@@ -388,8 +398,6 @@ __global__ void __launch_bounds__(PWA_THREADS, 3) k_uneven(const UnevenChannel* 
 int g_uneven_occ = -1;
 
 }  // namespace
-
-size_t uneven_smem_bytes() { return sizeof(float4) * (size_t)UN_SUB; }
 
 int uneven_build_plan(const pwa_uneven_channel* ch, int n_ch, UnevenPlan* plan, char* err, size_t err_len) {
     plan->chans.assign(n_ch, UnevenChannel{});
@@ -440,15 +448,12 @@ int uneven_build_plan(const pwa_uneven_channel* ch, int n_ch, UnevenPlan* plan, 
             while (u.ord[s] != d.float_wave[q]) ++s;
             (d.float_kind[q] == 0 ? u.qM[s] : u.qW[s]) = (signed char)q;
         }
-        u.nchunk = (d.K + UN_KPT - 1) / UN_KPT;
-        for (int cc = 0; cc < UN_NCH_MAX; ++cc) {
-            int g = 0;
-            const int s0 = cc * UN_KPT;
-            while (g < u.ng && u.gend[g] <= s0) ++g;
-            u.cgrp[cc] = g < u.ng ? g : u.ng - 1;
+        if (u.ng > UN_NG) {
+            snprintf(err, err_len, "channel %d: %d groups of equal (J, lambda), at most %d", c, u.ng, UN_NG);
+            return -1;
         }
-        int64_t epi = (UN_ITEM_WORK / d.K + UN_SUB - 1) / UN_SUB * UN_SUB;
-        epi = std::min<int64_t>(std::max<int64_t>(epi, UN_SUB), UN_ITEM_MAX_EV);
+        int64_t epi = (UN_ITEM_WORK / d.K + 1023) / 1024 * 1024;
+        epi = std::min<int64_t>(std::max<int64_t>(epi, UN_ITEM_MIN_EV), UN_ITEM_MAX_EV);
         u.epi = (int)epi;
         u.items_d = (int)std::max<int64_t>(1, (d.n + epi - 1) / epi);
         u.items_m = (int)((d.n_mc + epi - 1) / epi);
@@ -521,12 +526,10 @@ cudaError_t uneven_upload(const UnevenPlan& p, void* ws, cudaStream_t st) {
 cudaError_t uneven_launch(const UnevenPlan& p, void* ws, const float2* V, const double* theta, double* nll,
                           double* grad, int* status, int sm_count, cudaStream_t st) {
     UnevenLayout L = uneven_layout(p, ws);
-    const size_t smem = uneven_smem_bytes();
+    const size_t smem = 0;
     if (g_uneven_occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_uneven, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_uneven, PWA_THREADS, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_uneven, PWA_THREADS, smem);
         if (e != cudaSuccess) return e;
         g_uneven_occ = o > 0 ? o : 1;
     }
