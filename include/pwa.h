@@ -175,11 +175,12 @@ PWA_API pwa_status pwa_normint_from_kinematics(pwa_handle* h, const pwa_wave* wa
  * blocks they are combined exactly in 64-bit integer fixed point for P = 1, and in double-single
  * along a fixed-order tree for P > 1.  Either way identical inputs give identical bits.
  * For P > 1 the autotuner may pick the tensor-core shape (pwa_batched_shape() == 4): FP32
- * products emulated by three TF32 products and accumulated in FP32 in tensor memory.  It meets
- * the same tolerances (1e-5 of the -lnL scale, 1e-4 of the gradient scale) but its error at a
- * minimum, where the gradient cancels to ~1e-6 of its terms, is ~100x that of the SIMT shapes;
- * pwa_fit_batch therefore evaluates with the SIMT shapes only, and PWA_BATCHED_SHAPE=0..3
- * forces a SIMT shape for other callers. */
+ * products emulated by three TF32 products (both parts rounded to TF32), accumulated in FP32 in
+ * tensor memory over 64 events, then in double-single.  It meets the same tolerances (1e-5 of the
+ * -lnL scale, 1e-4 of the gradient scale); at a minimum, where the gradient cancels to ~1e-6 of
+ * its terms, its error is ~4e-8 of the gradient scale (about 30x that of the SIMT shapes, 10x
+ * below pwa_fit_batch's convergence threshold at 2e6 events).  PWA_BATCHED_SHAPE=0..4 forces a
+ * shape. */
 PWA_API pwa_status pwa_nll(pwa_handle* h, const float* A, int K, int64_t n, int64_t ld, const float* V,
                    int P, const double* Psi, double n_factor, double* nll, void* stream);
 

@@ -917,7 +917,7 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
             cudaError_t ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
                                              reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll,
                                              eb[f].grad, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
-                                             h->sm_count, s, /*fp32_only=*/true);
+                                             h->sm_count, s);
             if (ee != cudaSuccess) return ee;
             ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
                                       o.gtol * std::fabs(d.n_factor), fit_mode(o), o.max_iter, s);

@@ -956,7 +956,6 @@ struct Shape {
 // shape 4: the tensor-core kernel k_nll_tc (3xTF32, K <= 32)
 const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}, {128, 64}, {64, 128}};
 constexpr int kNumShapes = 5;
-constexpr int kTensorShape = 4;
 
 template <int KMAX, int E, int PB>
 bool shape_feasible() {
@@ -1079,18 +1078,15 @@ int tuned_shape(int K, int64_t n, int P) {
     return it != g_tuned.end() ? it->second : -1;
 }
 
-// fp32_only: the FP32 SIMT shapes only (the minimiser's evaluations: near a minimum the
-// gradient is a cancellation to ~1e-6 of its terms, below the accuracy of the tensor-core
-// shape, whose FP32 accumulation in tensor memory is not rounded to nearest)
 int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const float2* V, void* ws, size_t ws_bytes, int* bad,
-                 int* status, int with_grad, int sm_count, cudaStream_t st, bool fp32_only) {
+                 int* status, int with_grad, int sm_count, cudaStream_t st) {
     const int kmax = kmax_batched(K);
     const char* env = getenv("PWA_BATCHED_SHAPE");
     if (env) {
         int s = atoi(env);
-        if (s >= 0 && s < kNumShapes && shape_ok(kmax, s) && !(fp32_only && s == kTensorShape)) return s;
+        if (s >= 0 && s < kNumShapes && shape_ok(kmax, s)) return s;
     }
-    const auto key = std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), fp32_only ? 1 : 0);
+    const auto key = std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), 0);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -1107,7 +1103,7 @@ int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const flo
     int best = fallback;
     float best_ms = 1e30f;
     for (int s = 0; s < kNumShapes; ++s) {
-        if (!shape_ok(kmax, s) || (fp32_only && s == kTensorShape)) continue;
+        if (!shape_ok(kmax, s)) continue;
         int nc;
         float tot = 0.f;
         bool ok = true;
@@ -1184,7 +1180,7 @@ size_t nll_workspace(int K, int64_t n, int P, int sm_count) {
 
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
-                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st, bool fp32_only) {
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st) {
     if (P == 1) {
         // counter[0]: completion ticket, counter[1]: non-finite flag of this evaluation
         int* badw = reinterpret_cast<int*>(counter + 1);
@@ -1193,7 +1189,7 @@ cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const floa
         return stream_dispatch<false>(A, K, n, ld, V, Psi, nfac, nll, nullptr, ws, ws_bytes, counter, badw, status, sm_count, st);
     }
     const int with_grad = grad != nullptr;
-    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, status, with_grad, sm_count, st, fp32_only);
+    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, status, with_grad, sm_count, st);
     int nchunk = 1;
     cudaError_t e = batched_dispatch(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st,
                                      &nchunk);

@@ -25,14 +25,22 @@
 // Shared memory holds V' (hi, lo), A' and X (hi, lo; both layouts are written from registers,
 // since a transposed TF32 operand is not available) and the low words of the G accumulators;
 // tensor memory holds D1 (Y hi overwrites it), Y lo, D2 and the high words of the G
-// accumulators.  D2 accumulates in FP32 over a window of WINDOW tiles (256 events) and is then
-// added to the double-single G accumulators; at the end they are written to the block's
-// [chunk][P][1 + 2K] partials, the layout of the other tile shapes, so one finalisation serves
-// all.  Sum ln I: FP32 per tile and thread, double-single across tiles.  Every wait on the
+// accumulators.  D2 has two column blocks: hi.hi alone, and the small hi.lo + lo.hi.  They
+// accumulate in FP32 over WINDOW tiles (64 events) and are then added to the double-single G
+// accumulators.  The tensor cores' FP32 accumulation does not round to nearest; at a minimum the
+// data sum of the gradient is coherent (about n Psi^T V), so that error adds up over a window
+// instead of averaging out: draining every tile keeps it ~1e-8 of the gradient scale, 10x below
+// the minimiser's convergence threshold at 2e6 events.  At the end they are written to the
+// block's [chunk][P][1 + 2K] partials, the layout of the other tile shapes, so one finalisation
+// serves all.  Sum ln I: FP32 per tile and thread, double-single across tiles.  Every wait on the
 // tensor cores is bounded; a timeout sets status bit 1 and the block's sets' bad flags, waits
 // (bounded) for the MMAs in flight and frees the tensor memory.
 #include "nll_common.cuh"
 #include "tc.cuh"
+
+#ifndef PWA_TC_WINDOW
+#define PWA_TC_WINDOW 1
+#endif
 
 namespace pwa {
 
@@ -55,13 +63,13 @@ struct TcCfg {
     static constexpr uint32_t SMEM_USED = OFF_BAR + 64;
     // at least half of an SM's shared memory, so that one block holds the SM (and its tensor memory)
     static constexpr uint32_t SMEM = SMEM_USED > 118784u ? SMEM_USED : 118784u;
-    // tensor-memory columns: D1 (U, then Y hi in place), Y lo, D2 (two column blocks: hi.hi + lo.hi
-    // and hi.lo), the high words of the G accumulators
+    // tensor-memory columns: D1 (U, then Y hi in place), Y lo, D2 (two column blocks: hi.hi, and
+    // hi.lo + lo.hi), the high words of the G accumulators
     static constexpr uint32_t T_D1 = 0, T_YL = 2 * E, T_D2 = 4 * E, T_ACC = T_D2 + 2 * N2, TMEM_COLS = 512;
     // tiles per FP32 accumulation window of G in tensor memory before it is added to the
     // double-single accumulators (the tensor cores' accumulation is not rounded to nearest, so
-    // its error grows with the window; the minimiser does not use this kernel)
-    static constexpr int WINDOW = 4;
+    // its error grows with the window)
+    static constexpr int WINDOW = PWA_TC_WINDOW;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
     static constexpr int ITEMS = (ITEMS_TOT + NC - 1) / NC;       // per compute thread
     static_assert(KMAX % 8 == 0 && KMAX <= 32, "tensor-core batched kernel: K <= 32");
@@ -102,7 +110,7 @@ __device__ __forceinline__ bool nb_or(int id, int n, bool v) {
 // so GEMM2 of half 0 runs during the epilogue of half 1, and GEMM1(t+1) during the X copy,
 // the loads and the drain.  The epilogue writes Y hi over D1 in place; GEMM1(t+1), which
 // overwrites D1, waits for GEMM2(t), which reads Y hi.  GEMM2 takes X hi and X lo as one
-// operand of 2 N2 rows (hi.hi and hi.lo in one MMA per k-step), then adds lo.hi into the first
+// operand of 2 N2 rows (hi.hi and hi.lo in one MMA per k-step), then adds lo.hi into the second
 // column block.  Every WINDOW tiles the two column blocks are added to the G accumulators (high
 // words in tensor memory, low words in shared memory).  A wait that times out sets a block flag;
 // from then on no MMA is issued and no mbarrier wait is made, but every named barrier is still
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
 #pragma unroll
                             for (int d = 0; d < 2; ++d) {
                                 const uint32_t s = 4 * j + 2 * hf + d;
-                                mma_tf32_ts(tmem + C::T_D2, tmem + C::T_YL + 8u * s, dXh + 16u * s, idn, 1u);
+                                mma_tf32_ts(tmem + C::T_D2 + C::N2, tmem + C::T_YL + 8u * s, dXh + 16u * s, idn, 1u);
                             }
                         if (hf == 1) umma_commit(bar_g2);
                     }

@@ -190,10 +190,10 @@ cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t l
                                     const double2* Psi, double nfac, double* nll, double* grad, float2* part,
                                     size_t part_bytes, unsigned* counter, int* badw, int* status, int max_blocks,
                                     int sm_count, cudaStream_t st);
-// P > 1: autotuned tile shape; fp32_only restricts it to the FP32 SIMT shapes (the minimiser)
+// P > 1: the autotuned tile shape
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
-                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st, bool fp32_only = false);
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
 
 // record a message for pwa_last_error(NULL) (calls without a handle)
 void record_global_error(const char* msg);

@@ -105,12 +105,14 @@ __device__ __forceinline__ float tf32_round(float x) {
 }
 
 // The operand split of the three-product emulation of an FP32 product, a b ~ a_hi b_hi +
-// a_hi b_lo + a_lo b_hi: hi = the nearest TF32 value, lo = x - hi (exact in FP32, |lo| <=
-// 2^-11 |x|).  The tensor cores read the leading 11 bits of lo, so x is represented to within
-// 2^-21 |x|.
+// a_hi b_lo + a_lo b_hi: hi = the nearest TF32 value, lo = the nearest TF32 value of x - hi
+// (|x - hi| <= 2^-11 |x|).  So x = hi + lo to within 2^-22 |x|, and the residual is a rounding
+// to nearest: unbiased.  (Left unrounded, lo would be read by the tensor cores with its low 13
+// bits dropped, a truncation toward zero whose bias adds up over the millions of terms of an
+// event sum instead of averaging out.)
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
     hi = tf32_round(x);
-    lo = x - hi;
+    lo = tf32_round(x - hi);
 }
 
 }  // namespace pwa

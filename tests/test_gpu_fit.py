@@ -86,6 +86,29 @@ def test_fit_plain_workload_starts(h):
     assert best_gpu <= best_scipy + 1e-6 * abs(best_scipy)
 
 
+@pytest.mark.parametrize("shape", ["3", "4"])
+def test_multistart_fit_with_each_batched_shape(h, shape, monkeypatch):
+    # K = 32, 2e5 events, 64 starts per launch, with the pipelined FP32 SIMT shape and with the
+    # tensor-core shape (FP32 products as three TF32 products, the sums drained from tensor memory
+    # every 64 events) forced: the starts converge to oracle-stationary points with S = 1
+    monkeypatch.setenv("PWA_BATCHED_SHAPE", shape)
+    p = make_problem(32, 200_000, 400_000, SEED + 31, accept_reject=False)
+    V0 = inputs.starts(64, 32, SEED + 31)
+    res, (V,) = run_fits(h, [(p, V0)], max_iter=3000)
+    bad = [(i, r) for i, r in enumerate(res) if r["status"] != 0]
+    # the tensor-core shape's gradient error at a minimum (~4e-8 of the gradient scale) lets an
+    # occasional start in a flat valley stall above the threshold (1 of these 64 at 2e5 events);
+    # at the multistart size (2e6 events, 256 starts) every start converges with it
+    assert len(bad) <= (0 if shape == "3" else 2), (len(bad), bad[:4])
+    for i, r in enumerate(res):
+        if r["status"] != 0:
+            continue
+        f, gmax, S = stationary(p, V[i])
+        assert gmax < 1e-5, (i, gmax)
+        assert abs(S - 1.0) < 1e-4, S
+        assert abs(f - r["nll"]) <= 1e-5 * max(abs(f), p.n)
+
+
 def test_toy_fit_recovers_seeded_amplitudes(h):
     # N = 1e5 events drawn from I under V_true; the fit from V_true's neighbourhood must land
     # within statistical error of V_true rescaled to S = 1 (the extended-likelihood scale) and
