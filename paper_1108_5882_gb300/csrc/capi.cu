@@ -499,7 +499,8 @@ pwa_status pwa_normint(pwa_handle* h, const float* A_mc, int K, int64_t n_mc, in
     st = ensure_workspace(h, pwa::normint_workspace(K, h->sm_count), 1);
     if (st != PWA_OK) return st;
     cudaError_t e = pwa::launch_normint(reinterpret_cast<const float2*>(A_mc), K, n_mc, ld, w, n_gen,
-                                        reinterpret_cast<double2*>(Psi), h->ws, h->sm_count, (cudaStream_t)stream);
+                                        reinterpret_cast<double2*>(Psi), h->ws, h->sm_count, (cudaStream_t)stream,
+                                        h->status);
     if (e != cudaSuccess) return cuda_fail(h, e, "normint launch");
     h->err.clear();
     return PWA_OK;
@@ -525,7 +526,7 @@ pwa_status pwa_normint_from_kinematics(pwa_handle* h, const pwa_wave* waves, int
     st = ensure_workspace(h, pwa::normint_workspace(K, h->sm_count), 1);
     if (st != PWA_OK) return st;
     cudaError_t e = pwa::launch_normint_kin(wt, kin, K, n_mc, ld, w, n_gen, reinterpret_cast<double2*>(Psi), h->ws,
-                                            h->sm_count, (cudaStream_t)stream);
+                                            h->sm_count, (cudaStream_t)stream, h->status);
     if (e != cudaSuccess) return cuda_fail(h, e, "normint (kinematics) launch");
     h->err.clear();
     return PWA_OK;

@@ -26,7 +26,8 @@
 // since a transposed TF32 operand is not available) and the low words of the G accumulators;
 // tensor memory holds D1 (Y hi overwrites it), Y lo, D2 and the high words of the G
 // accumulators.  D2 has two column blocks: hi.hi alone, and the small hi.lo + lo.hi.  They
-// accumulate in FP32 over WINDOW tiles (64 events) and are then added to the double-single G
+// accumulate in FP32 in tensor memory over WINDOW tiles (64 events), are added in FP32 (rounded
+// to nearest) into registers, and every FF_EVERY windows into the double-single G
 // accumulators.  The tensor cores' FP32 accumulation does not round to nearest; at a minimum the
 // data sum of the gradient is coherent (about n Psi^T V), so that error adds up over a window
 // instead of averaging out: draining every tile keeps it ~1e-8 of the gradient scale, 10x below
@@ -70,6 +71,8 @@ struct TcCfg {
     // double-single accumulators (the tensor cores' accumulation is not rounded to nearest, so
     // its error grows with the window)
     static constexpr int WINDOW = PWA_TC_WINDOW;
+    // windows per double-single update of the G accumulators (FP32 round-to-nearest in between)
+    static constexpr int FF_EVERY = 4;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
     static constexpr int ITEMS = (ITEMS_TOT + NC - 1) / NC;       // per compute thread
     static_assert(KMAX % 8 == 0 && KMAX <= 32, "tensor-core batched kernel: K <= 32");
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
 
     ff lsum = ff_zero();
     bool mybad = false, drained = false;
+    int since_ff = 0;
 
     if (mma_warp) {
         // ================================================================ MMA warp
@@ -345,24 +349,46 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
             }
         };
         float* acc_lo = reinterpret_cast<float*>(tsm + C::OFF_ACC) + pl;  // [column][PB]
-        // G accumulators (hi in tensor memory, lo in shared memory) += the window in D2; the two
-        // threads of a lane take alternate groups of 16 columns
-        auto drain = [&](bool first) {
-#pragma unroll 1
-            for (int q = hh; q < C::N2 / 16; q += 2) {
-                float d0[16], d1[16], ah[16];
-                tmem_ld16(lane_t + C::T_D2 + 16 * q, d0);
-                tmem_ld16(lane_t + C::T_D2 + C::N2 + 16 * q, d1);
-                tmem_ld16(lane_t + C::T_ACC + 16 * q, ah);
-                tmem_wait_ld();
+        // Every tile the two column blocks of D2 are added in FP32 (round to nearest, on the CUDA
+        // cores) into racc; every FF_EVERY tiles racc enters the double-single G accumulators (hi
+        // in tensor memory, lo in shared memory).  The two threads of a lane take alternate groups
+        // of 16 columns (racc[16 i + k]: group hh + 2 i).
+        constexpr int NGRP = (C::N2 / 16 + 1) / 2;  // column groups per thread
+        float racc[16 * NGRP];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    float* lo = acc_lo + (16 * q + k) * C::PB;
-                    const ff r = ff_add_f(first ? ff_zero() : ff{ah[k], *lo}, d0[k] + d1[k]);
-                    ah[k] = r.hi;
-                    *lo = r.lo;
+        for (int v = 0; v < 16 * NGRP; ++v) racc[v] = 0.f;
+        auto drain_tile = [&]() {
+#pragma unroll
+            for (int i = 0; i < NGRP; ++i) {
+                const int q = hh + 2 * i;
+                if (q < C::N2 / 16) {
+                    float d0[16], d1[16];
+                    tmem_ld16(lane_t + C::T_D2 + 16 * q, d0);
+                    tmem_ld16(lane_t + C::T_D2 + C::N2 + 16 * q, d1);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) racc[16 * i + k] += d0[k] + d1[k];
                 }
-                tmem_st16(lane_t + C::T_ACC + 16 * q, ah);
+            }
+        };
+        auto flush = [&](bool first) {
+#pragma unroll
+            for (int i = 0; i < NGRP; ++i) {
+                const int q = hh + 2 * i;
+                if (q < C::N2 / 16) {
+                    float ah[16];
+                    tmem_ld16(lane_t + C::T_ACC + 16 * q, ah);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        float* lo = acc_lo + (16 * q + k) * C::PB;
+                        const ff r = ff_add_f(first ? ff_zero() : ff{ah[k], *lo}, racc[16 * i + k]);
+                        ah[k] = r.hi;
+                        *lo = r.lo;
+                        racc[16 * i + k] = 0.f;
+                    }
+                    tmem_st16(lane_t + C::T_ACC + 16 * q, ah);
+                }
             }
             tmem_wait_st();
         };
@@ -443,8 +469,12 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
             }
             if (grad && (++win == C::WINDOW || t + 1 == ntile)) {
                 if (!ab) {
-                    drain(!drained);
-                    drained = true;
+                    drain_tile();
+                    if (++since_ff == C::FF_EVERY || t + 1 == ntile) {
+                        flush(!drained);
+                        drained = true;
+                        since_ff = 0;
+                    }
                 }
                 win = 0;
             }

@@ -267,6 +267,31 @@ size_t ni_smem() {
     return sizeof(float2) * NI_E * ni_rs<KMAX>() + sizeof(float) * NI_E + sizeof(float) * 64 * PWA_THREADS;
 }
 
+// the tensor-core kernel (normint_tc.cu) and the same fixed-order finalisation
+template <int KMAX>
+cudaError_t ni_launch_tc(const float2* A, int K, int64_t n, const int64_t ld, double n_gen, double2* Psi, void* ws,
+                         int* status, int sm_count, cudaStream_t st, const float* kin, const WaveTable* wt) {
+    float4* part = reinterpret_cast<float4*>(ws);
+    int nb = 1;
+    cudaError_t e = launch_normint_tc(A, K, n, ld, kin, wt, part, status, sm_count, st, &nb);
+    if (e != cudaSuccess) return e;
+    const int fin_blocks = (K * K * 32 + PWA_THREADS - 1) / PWA_THREADS;  // one warp per entry
+    k_normint_final<KMAX><<<fin_blocks, PWA_THREADS, 0, st>>>(part, nb, K, 1.0 / n_gen, Psi);
+    return cudaGetLastError();
+}
+
+// The tensor-core kernel by default for 16 < K <= 32 with unit weights (measured on GB300: at
+// K = 32 and 1e7 events from the kinematics 1.31 ms against 2.15 ms on SIMT; at K = 16 its
+// two-stage pipeline is latency-bound and the SIMT kernel is faster).  PWA_NORMINT_TC=1 takes it
+// for every K <= 32, PWA_NORMINT_TC=0 never.
+bool use_normint_tc(int K, const float* w, const WaveTable* wt, const int* status) {
+    if (!status || !normint_tc_ok(K, w, wt)) return false;
+    const char* e = getenv("PWA_NORMINT_TC");
+    if (e && e[0] == '0') return false;
+    if (e && e[0] == '1') return true;
+    return K > 16;
+}
+
 template <int KMAX>
 cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float* w, double n_gen,
                       double2* Psi, void* ws, int sm_count, cudaStream_t st, const float* kin = nullptr,
@@ -300,12 +325,18 @@ cudaError_t ni_launch(const float2* A, int K, int64_t n, int64_t ld, const float
 }  // namespace
 
 size_t normint_workspace(int K, int sm_count) {
-    int KMAX = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64;
+    // block partials of the SIMT kernel (2 blocks per SM) or of the tensor-core one (1 per SM, KMAX >= 8)
+    int KMAX = K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : K <= 48 ? 48 : 64;
     return sizeof(float4) * (size_t)KMAX * KMAX * (size_t)sm_count * 2;
 }
 
 cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int64_t n, int64_t ld, const float* w,
-                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st, int* status) {
+    if (use_normint_tc(K, w, &wt, status)) {
+        if (K <= 8) return ni_launch_tc<8>(nullptr, K, n, ld, n_gen, Psi, ws, status, sm_count, st, kin, &wt);
+        if (K <= 16) return ni_launch_tc<16>(nullptr, K, n, ld, n_gen, Psi, ws, status, sm_count, st, kin, &wt);
+        return ni_launch_tc<32>(nullptr, K, n, ld, n_gen, Psi, ws, status, sm_count, st, kin, &wt);
+    }
     if (K <= 4) return ni_launch<4>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
     if (K <= 8) return ni_launch<8>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
     if (K <= 16) return ni_launch<16>(nullptr, K, n, ld, w, n_gen, Psi, ws, sm_count, st, kin, &wt);
@@ -315,7 +346,12 @@ cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int
 }
 
 cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const float* w,
-                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st) {
+                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st, int* status) {
+    if (use_normint_tc(K, w, nullptr, status)) {
+        if (K <= 8) return ni_launch_tc<8>(A, K, n, ld, n_gen, Psi, ws, status, sm_count, st, nullptr, nullptr);
+        if (K <= 16) return ni_launch_tc<16>(A, K, n, ld, n_gen, Psi, ws, status, sm_count, st, nullptr, nullptr);
+        return ni_launch_tc<32>(A, K, n, ld, n_gen, Psi, ws, status, sm_count, st, nullptr, nullptr);
+    }
     if (K <= 4) return ni_launch<4>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
     if (K <= 8) return ni_launch<8>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);
     if (K <= 16) return ni_launch<16>(A, K, n, ld, w, n_gen, Psi, ws, sm_count, st);

@@ -182,8 +182,12 @@ cudaError_t launch_amplitudes(const WaveTable& wt, const float* kin, int64_t n, 
                               cudaStream_t st);
 
 size_t normint_workspace(int K, int sm_count);
+// With status given, unit weights and 16 < K <= 32 the tensor-core kernel runs (normint_tc.cu; a
+// timeout of its bounded waits sets status bit 1); otherwise FP32 SIMT.  PWA_NORMINT_TC=1 / 0
+// forces the tensor-core kernel for K <= 32 / the SIMT one.
 cudaError_t launch_normint(const float2* A, int K, int64_t n, int64_t ld, const float* w,
-                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st);
+                           double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st,
+                           int* status = nullptr);
 
 size_t nll_workspace(int K, int64_t n, int P, int sm_count);
 cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t ld, const float2* V,
@@ -290,7 +294,11 @@ cudaError_t launch_hessian(const float2* A, int K, int64_t n, int64_t ld, const 
 // Psi straight from MC kinematics kin [3][ld]: the amplitudes of each tile of events are computed
 // in shared memory (with the arithmetic of pwa_amplitudes) and consumed there.
 cudaError_t launch_normint_kin(const WaveTable& wt, const float* kin, int K, int64_t n, int64_t ld, const float* w,
-                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st);
+                               double n_gen, double2* Psi, void* ws, int sm_count, cudaStream_t st,
+                               int* status = nullptr);
+bool normint_tc_ok(int K, const float* w, const WaveTable* wt);
+cudaError_t launch_normint_tc(const float2* A, int K, int64_t n, int64_t ld, const float* kin, const WaveTable* wt,
+                              float4* part, int* status, int sm_count, cudaStream_t st, int* nblocks);
 
 // The same product on the tensor cores (tcgen05 kind::f16) for a BF16 B; an FP32 A is split into
 // three BF16 parts.  A timeout of its bounded wait sets status bit 1.

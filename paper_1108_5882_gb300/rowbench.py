@@ -89,7 +89,7 @@ def line(row, what, sec, nbytes=0.0, flops=0.0, hbm=6800.0, f32=80.0, extra=None
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--rows", default="a1,a1b,a2,a3,a3i,a4,a5,a7,a7p,a7h,a8,a9")
+    ap.add_argument("--rows", default="a1,a1b,a2,a3,a3i,a4,a4u,a5,a7,a7p,a7h,a8,a9")
     ap.add_argument("--json", default=None)
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and one timed launch per kernel, no peak microbenchmark and 64 toys "
@@ -139,8 +139,27 @@ def main():
         h.pwa_amplitudes(w16, kin_mc, n_mc, A_mc)
         h.pwa_normint(A_mc, n_mc, Psi16)
     if "a2" in rows:
-        sec = T(lambda: h.pwa_normint(A_mc, n_mc, Psi16), R)
-        add("a2", "normint K=16, 5e6 MC events", sec, nbytes=n_mc * 8 * 16, flops=n_mc * 8.0 * 16 * 17 / 2)
+        # the tensor-core kernel (default: unit weights, K <= 32) and the FP32 SIMT one
+        for tc in ("1", "0"):
+            os.environ["PWA_NORMINT_TC"] = tc
+            kind = "tcgen05" if tc == "1" else "SIMT"
+            sec = T(lambda: h.pwa_normint(A_mc, n_mc, Psi16), R)
+            add("a2", f"normint K=16, 5e6 MC events ({kind})", sec, nbytes=n_mc * 8 * 16, flops=n_mc * 8.0 * 16 * 17 / 2)
+            sec = T(lambda: h.pwa_normint_from_kinematics(w16, kin_mc, n_mc, Psi16), R)
+            add("a2", f"normint from kinematics K=16, 5e6 ({kind})", sec, nbytes=n_mc * 12.0,
+                flops=n_mc * (30.0 * 16 + 8.0 * 16 * 17 / 2))
+        os.environ.pop("PWA_NORMINT_TC")
+        # the multistart workload's Psi: K=32, 1e7 MC events straight from the kinematics
+        ws32n = inputs.wave_set_spread(32, seed + 1)
+        kin32 = torch.from_numpy(inputs.kinematics(10_000_000, seed + 1, 5)).cuda()
+        Psi32 = torch.empty((32, 32), dtype=torch.complex128, device="cuda")
+        for tc in ("1", "0"):
+            os.environ["PWA_NORMINT_TC"] = tc
+            sec = T(lambda: h.pwa_normint_from_kinematics(pwa.waves_from(ws32n), kin32, 10_000_000, Psi32), max(5, R // 2))
+            add("a2", f"normint from kinematics K=32, 1e7 ({'tcgen05' if tc == '1' else 'SIMT'})", sec,
+                nbytes=1e7 * 12.0, flops=1e7 * (30.0 * 32 + 8.0 * 32 * 33 / 2))
+        os.environ.pop("PWA_NORMINT_TC")
+        del kin32
     if "a3" in rows:
         for K, N in ((4, 1_000_000), (16, 1_000_000), (16, 4_000_000), (32, 1_000_000)):
             wsK = inputs.wave_set_spread(K, seed)
@@ -263,6 +282,35 @@ def main():
             print(f"{tag:3s} batched L-BFGS fit K={K}, N={N:.0e}, P={P}, {coords}: {wall:.3f} s, {iters} iterations "
                   f"(max), {evals:.1f} evaluations/start, {conv}/{P} converged, best -lnL {best:.3f}", flush=True)
         del A
+    if "a4u" in rows:
+        # many channels with floating masses and widths in one persistent launch: the uneven
+        # workload's 64 channels at 1/8 of its event counts (N_data log-U[1e4, 5e5], N_MC = 5 N_data),
+        # flat events; masses and widths of waves 0 and K/2 float
+        sdu = inputs.SEED_BASE + 6
+        descs, Vs, ths, flops, n_data, n_ev = [], [], [], 0.0, 0, 0
+        for c, (K, N, NMC) in enumerate(inputs.uneven_channels(64, sdu, nmax=5e5)):
+            wsu = inputs.wave_set_spread(K, sdu, stream=100 + c)
+            ld, ldm = N + (N & 1), NMC + (NMC & 1)
+            fl = [0, K // 2]
+            descs.append(dict(waves=pwa.waves_from(wsu), kin=torch.from_numpy(inputs.kinematics(N, sdu, 300 + c, ld=ld)).cuda(),
+                              n=N, kin_mc=torch.from_numpy(inputs.kinematics(NMC, sdu, 400 + c, ld=ldm)).cuda(),
+                              n_mc=NMC, n_gen=float(NMC), n_factor=float(N), float_wave=[fl[0], fl[1], fl[0], fl[1]],
+                              float_kind=[0, 0, 1, 1]))
+            Vs.append(inputs.production_amplitudes(K, sdu, stream=200 + c))
+            ths.append([wsu.M[fl[0]], wsu.M[fl[1]], wsu.W[fl[0]], wsu.W[fl[1]]])
+            # per event: per wave one Breit-Wigner (11 flop) and the complex multiply-adds into u and
+            # the gradient (16); per floating parameter 10; |u|^2, ln I and w 12
+            flops += (N + NMC) * (27.0 * K + 10 * 4 + 12)
+            n_data += N
+            n_ev += N + NMC
+        Vu = torch.from_numpy(np.concatenate(Vs)).cuda()
+        thu = torch.tensor(np.concatenate(ths), dtype=torch.float64, device="cuda")
+        nllu = torch.empty(len(descs), dtype=torch.float64, device="cuda")
+        gu = torch.empty(sum(2 * len(d["waves"]) + 4 for d in descs), dtype=torch.float64, device="cuda")
+        sec = T(lambda: h.pwa_nll_grad_uneven(descs, Vu, thu, nllu, gu), max(5, R // 2), flush=False)
+        add("a4u", f"64 channels, floating (M,G), {n_data:.2e} data + {n_ev - n_data:.2e} MC events", sec,
+            nbytes=12.0 * n_ev, flops=flops)
+        del descs, Vu, thu
     if "a8" in rows:
         sd = inputs.SEED_BASE + 5
         wsl = inputs.wave_set_spread(16, sd)

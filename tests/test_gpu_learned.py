@@ -9,6 +9,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_1108_5882_gb300 import inputs
+from learned_oracle_judge import judge_toy, summarize_judged
 from problems import fp32_decision_band
 
 pytestmark = pytest.mark.gpu
@@ -199,23 +200,31 @@ def test_learned_proposer_trains_and_competes_with_random_starts():
     hist = learned.train(prop, feats, targets, epochs=8, batch=128, lr=2e-3)
     assert hist[-1] < 0.8 * hist[0], hist
     Vh = learned.random_truths(6, 16, seed + 1)
-    outs = []
-    Psi_np = Psi.cpu().numpy()
+    outs, judged = [], []
+    # the oracle's own Psi over the same flat MC events, and per toy its own FP64 amplitudes
+    kin_mc = inputs.kinematics(500_000, seed, 31)
+    Psi_or = oracle.normint(oracle.amplitudes(ws.J, ws.lam, ws.M, ws.W, kin_mc).astype(np.complex64))
     for t in range(6):
         o = learned.evaluate_toy(hh, waves, Psi, prop, Vh[t], 100_000, seed + 1, 7 + t, P_rand=64, max_seq=16)
         reps, _ = learned.cluster_minima(o["Vs"], o["fs"], o["ok"])
         assert reps and abs(o["fs"][reps[0]] - o["f_best"]) == 0.0
-        if len(reps) >= 2:
-            A = o["A"].cpu().numpy()
-            f_or = [oracle.nll_grad(A, o["Vs"][r].astype(np.complex64)[None, :], Psi_np)[0][0] for r in reps[:4]]
-            assert int(np.argmin(f_or)) == 0 or abs(min(f_or) - f_or[0]) < 1e-3 * abs(f_or[0]) * 1e-3, f_or
+        j = judge_toy(o, ws, Psi_or)
+        judged.append(j)
+        # the minimum the GPU takes as global is one by the oracle's criterion (within 0.01 of
+        # the oracle's best), and its value agrees to the FP32 evaluation's error bound
+        # (1e-6 sum |ln I| + 4e-7 N, under 1 here)
+        assert j["gpu_choice_is_global"], j
+        assert abs(j["f_best_gpu"] - j["f_best_oracle"]) < 1.0, j
         # a sequential method stops at its first fit that reaches the global minimum, or after
         # its last start
         assert o["plain_hit"] or o["n_plain"] == 16
         assert o["learned_seq_hit"] or o["n_learned_seq"] == prop.C + 16
         o.pop("A")
+        o.pop("kin")
         outs.append(o)
     s = learned.summarize(outs)
-    print("learned-vs-random (reduced):", s)
+    so = summarize_judged(outs, judged)
+    print("learned-vs-random (reduced), GPU-decided:", s)
+    print("learned-vs-random (reduced), oracle-decided:", so)
     assert s["toys"] == 6
-    assert s["learned_sequential_reached"] >= 5 / 6 and s["plain_reached"] >= 0.5
+    assert so["learned_sequential_reached"] >= 5 / 6 and so["plain_reached"] >= 0.5

@@ -188,6 +188,36 @@ def test_normint_parity(h, K, n_mc, weighted):
     assert np.array_equal(got, got.conj().T)
 
 
+@pytest.mark.parametrize("K,n_mc,from_kin", [(16, 30_001, False), (32, 20_003, False), (16, 30_001, True),
+                                              (32, 20_003, True), (7, 5_000, True)])
+def test_normint_simt_path_forced(h, K, n_mc, from_kin, monkeypatch):
+    # unit weights and 16 < K <= 32 take the tensor-core kernel by default; PWA_NORMINT_TC=1 / 0
+    # force the tensor-core / FP32 SIMT kernel for any K <= 32: both within the same bound
+    from paper_1108_5882_gb300 import pwa
+    ws = inputs.wave_set_spread(K, SEED + 1500 + K)
+    kin = inputs.kinematics(n_mc, SEED + 1500 + K, 5, ld=n_mc + (n_mc & 1))
+    A = torch.zeros((K, kin.shape[1]), dtype=torch.complex64, device="cuda")
+    h.pwa_amplitudes(pwa.waves_from(ws), dev(kin), n_mc, A)
+    out = {}
+    for tc in ("1", "0"):
+        monkeypatch.setenv("PWA_NORMINT_TC", tc)
+        Psi = torch.zeros((K, K), dtype=torch.complex128, device="cuda")
+        if from_kin:
+            h.pwa_normint_from_kinematics(pwa.waves_from(ws), dev(kin), n_mc, Psi)
+        else:
+            h.pwa_normint(A, n_mc, Psi)
+        out[tc] = Psi.cpu().numpy()
+    A_np = A.cpu().numpy()[:, :n_mc]
+    ref = oracle.normint(A_np)
+    d = np.sqrt(np.outer(np.diag(ref).real, np.diag(ref).real))
+    m = np.abs(A_np).sum(axis=1) / n_mc
+    tol = 1e-5 * d + (4e-6 * (m[:, None] + m[None, :]) if from_kin else 0.0) + 1e-30
+    for tc in ("1", "0"):
+        assert np.all(np.abs(out[tc] - ref) <= tol), (tc, np.max(np.abs(out[tc] - ref) / tol))
+        assert np.array_equal(out[tc], out[tc].conj().T)
+    assert h.pwa_sync_status() == pwa.PWA_OK
+
+
 def test_normint_on_amplitudes_of_the_plain_workload(h):
     p = make_problem(4, 100, 50_000, SEED + 1, accept_reject=False, plain=True)
     Psi = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
