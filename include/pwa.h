@@ -293,7 +293,11 @@ PWA_API void pwa_fit_default_opts(pwa_fit_opts* opts);
 
 /* Run n_fits fits (fits[f].P starts each).  results: HOST array of sum_f fits[f].P entries in
  * (fit, start) order.  opts may be NULL (defaults).  The workspace grows as needed (outside
- * any stream capture).  Returns PWA_OK once every start has stopped (see result.status). */
+ * any stream capture).  Returns PWA_OK once every start has stopped (see result.status).
+ * Evaluation: the autotuned tile shape of each fit; a start whose line search backtracks 10
+ * times in a row pauses, and once no start is running the paused ones resume from their
+ * accepted points with the fastest FP32 SIMT shape (the tensor-core shape's rounding can hide
+ * the decrease the line search looks for near a minimum). */
 PWA_API pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits,
                                  const pwa_fit_opts* opts, pwa_fit_result* results, void* stream);
 

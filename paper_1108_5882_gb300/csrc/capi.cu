@@ -911,6 +911,11 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
         off += fits[f].P;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "fit init");
+    // Two phases.  First every fit evaluates with its autotuned tile shape; a start whose line
+    // search keeps backtracking (the tensor-core shape's rounding, ~1e-8 of the gradient scale,
+    // can hide the decrease near a minimum) pauses.  Then the paused starts resume from their
+    // accepted points with the fastest FP32 SIMT shape, without pausing, until they stop.
+    bool precise = false;
     auto iteration = [&]() -> cudaError_t {
         int p_off = 0;
         for (int f = 0; f < n_fits; ++f) {
@@ -918,10 +923,11 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
             cudaError_t ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
                                              reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll,
                                              eb[f].grad, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
-                                             h->sm_count, s);
+                                             h->sm_count, s, precise);
             if (ee != cudaSuccess) return ee;
             ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
-                                      o.gtol * std::fabs(d.n_factor), fit_mode(o), o.max_iter, s);
+                                      o.gtol * std::fabs(d.n_factor), fit_mode(o) | (precise ? 0 : pwa::FIT_PAUSE),
+                                      o.max_iter, s);
             if (ee != cudaSuccess) return ee;
             p_off += d.P;
         }
@@ -929,6 +935,14 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     };
     e = run_fit_loop(h, s, o, P_tot, m, iteration);
     if (e != cudaSuccess) return cuda_fail(h, e, "fit loop");
+    int n_paused = 0;
+    e = pwa::fit_resume_paused(h->fitws, P_tot, m, &n_paused, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fit resume");
+    if (n_paused > 0) {
+        precise = true;
+        e = run_fit_loop(h, s, o, P_tot, m, iteration);
+        if (e != cudaSuccess) return cuda_fail(h, e, "fit loop (precise evaluation)");
+    }
     off = 0;
     for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
         if (fits[f].V_out)

@@ -61,6 +61,7 @@ struct FitState {
     int* head;      // [P]
     int* status;    // [P]
     int* evals;     // [P]
+    int* nfail;     // [P] line-search backtracks in a row
     int* running;   // [1]
 };
 
@@ -141,6 +142,7 @@ __global__ void k_fit_init(FitState st, const float2* __restrict__ V0, int K, in
         st.head[p] = 0;
         st.status[p] = FIT_RUNNING;
         st.evals[p] = 0;
+        st.nfail[p] = 0;
         st.alpha[p] = 0.0;  // 0: the first evaluation defines the starting point
         st.f[p] = INFINITY;
         st.gtd[p] = 0.0;
@@ -239,10 +241,14 @@ __device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew
             }
             an = fmin(fmax(an, 0.1 * alpha), 0.5 * alpha);
             st.alpha[p] = an;
+            const int nf = st.nfail[p] + 1;
+            st.nfail[p] = nf;
             if (an < 1e-20) st.status[p] = 2;
+            else if ((mode & FIT_PAUSE) && nf >= FIT_PAUSE_BACKTRACKS) st.status[p] = FIT_PAUSED;
         }
         __syncthreads();
-        write_trial(x, d, st.alpha[p], K, F, Vrow, th_row, polar);
+        if (st.status[p] == FIT_PAUSED) write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
+        else write_trial(x, d, st.alpha[p], K, F, Vrow, th_row, polar);
         return;
     }
     // ---- accepted: history update with s = xt - x, y = gt - g
@@ -273,6 +279,7 @@ __device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew
     }
     if (t == 0) {
         st.f[p] = fnew;
+        st.nfail[p] = 0;
         if (alpha != 0.0) st.iter[p] += 1;
     }
     __syncthreads();
@@ -376,6 +383,28 @@ __global__ void __launch_bounds__(128) k_lbfgs_step_multi(FitState st, const Ste
                     a.lb);
 }
 
+// paused -> running with alpha = 0: the next evaluation (at the trial point x, written when the
+// start paused) replaces f and g at x and the line search starts afresh; the count to out
+__global__ void k_fit_resume(FitState st, int P, int* __restrict__ out) {
+    __shared__ int s[256];
+    int c = 0;
+    for (int i = threadIdx.x; i < P; i += 256) {
+        if (st.status[i] == FIT_PAUSED) {
+            st.status[i] = FIT_RUNNING;
+            st.alpha[i] = 0.0;
+            st.nfail[i] = 0;
+            ++c;
+        }
+    }
+    s[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
 __global__ void k_count_running(const int* __restrict__ status, int P, int* __restrict__ out) {
     __shared__ int s[256];
     int c = 0;
@@ -450,6 +479,7 @@ static FitState carve(void* base, int P_tot, int m) {
     s.head = (int*)take(sizeof(int) * p);
     s.status = (int*)take(sizeof(int) * p);
     s.evals = (int*)take(sizeof(int) * p);
+    s.nfail = (int*)take(sizeof(int) * p);
     s.running = (int*)take(sizeof(int) * 16);
     return s;
 }
@@ -459,7 +489,7 @@ size_t fit_workspace(int P_tot, int m) {
     const size_t p = (size_t)P_tot;
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     return 3 * r(sizeof(double) * p * DM) + 2 * r(sizeof(double) * p * m * DM) + r(sizeof(double) * p * m) +
-           3 * r(sizeof(double) * p) + 5 * r(sizeof(int) * p) + r(sizeof(int) * 16);
+           3 * r(sizeof(double) * p) + 6 * r(sizeof(int) * p) + r(sizeof(int) * 16);
 }
 
 // Per-fit device buffers for the evaluation (V trial, nll, grad) live in `evalbuf`.
@@ -507,6 +537,15 @@ cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaS
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(host_out, st.running, sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t fit_resume_paused(void* fitws, int P_tot, int m, int* host_count, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    k_fit_resume<<<1, 256, 0, s>>>(st, P_tot, st.running);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_count, st.running, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
 }
 
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,

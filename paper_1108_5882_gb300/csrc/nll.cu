@@ -956,6 +956,7 @@ struct Shape {
 // shape 4: the tensor-core kernel k_nll_tc (3xTF32, K <= 32)
 const Shape kShapes[] = {{64, 64}, {64, 32}, {128, 32}, {128, 64}, {64, 128}};
 constexpr int kNumShapes = 5;
+constexpr int kTensorShape = 4;
 
 template <int KMAX, int E, int PB>
 bool shape_feasible() {
@@ -1078,15 +1079,18 @@ int tuned_shape(int K, int64_t n, int P) {
     return it != g_tuned.end() ? it->second : -1;
 }
 
+// precise: the fastest of the FP32 SIMT shapes (0-3), whose gradient error at a minimum is ~20x
+// below the tensor-core shape's; the fitter resumes starts whose line search stalled on the
+// tensor-core shape's rounding with it.
 int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const float2* V, void* ws, size_t ws_bytes, int* bad,
-                 int* status, int with_grad, int sm_count, cudaStream_t st) {
+                 int* status, int with_grad, int sm_count, cudaStream_t st, bool precise) {
     const int kmax = kmax_batched(K);
     const char* env = getenv("PWA_BATCHED_SHAPE");
     if (env) {
         int s = atoi(env);
-        if (s >= 0 && s < kNumShapes && shape_ok(kmax, s)) return s;
+        if (s >= 0 && s < kNumShapes && shape_ok(kmax, s) && !(precise && s == kTensorShape)) return s;
     }
-    const auto key = std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), 0);
+    const auto key = std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), precise ? 1 : 0);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -1100,8 +1104,8 @@ int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const flo
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = fallback;
-    float best_ms = 1e30f;
+    int best = fallback, best_p = fallback;
+    float best_ms = 1e30f, best_p_ms = 1e30f;
     for (int s = 0; s < kNumShapes; ++s) {
         if (!shape_ok(kmax, s)) continue;
         int nc;
@@ -1121,14 +1125,19 @@ int choose_shape(int K, int64_t n, int P, const float2* A, int64_t ld, const flo
             best_ms = tot;
             best = s;
         }
+        if (ok && s != kTensorShape && tot < best_p_ms) {
+            best_p_ms = tot;
+            best_p = s;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // clear the non-finite flags the trial launches may have set
     cudaMemsetAsync(bad, 0, sizeof(int) * (size_t)P, st);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = best;
-    return best;
+    g_tuned[std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), 0)] = best;
+    g_tuned[std::make_tuple(kmax, bucket_log2(P), bucket_log2(n), 1)] = best_p;
+    return precise ? best_p : best;
 }
 
 // One parameter set with caller-provided scratch and a cap on the number of blocks (used by
@@ -1180,7 +1189,7 @@ size_t nll_workspace(int K, int64_t n, int P, int sm_count) {
 
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
-                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st) {
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st, bool precise) {
     if (P == 1) {
         // counter[0]: completion ticket, counter[1]: non-finite flag of this evaluation
         int* badw = reinterpret_cast<int*>(counter + 1);
@@ -1189,7 +1198,7 @@ cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const floa
         return stream_dispatch<false>(A, K, n, ld, V, Psi, nfac, nll, nullptr, ws, ws_bytes, counter, badw, status, sm_count, st);
     }
     const int with_grad = grad != nullptr;
-    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, status, with_grad, sm_count, st);
+    const int shape = choose_shape(K, n, P, A, ld, V, ws, ws_bytes, bad, status, with_grad, sm_count, st, precise);
     int nchunk = 1;
     cudaError_t e = batched_dispatch(shape, A, K, n, ld, V, P, ws, ws_bytes, bad, status, with_grad, sm_count, st,
                                      &nchunk);

@@ -399,23 +399,41 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
             tmem_ld16(lane_t + C::T_D1 + E + 16 * q, ui);
             tmem_wait_ld();
             float yrh[16], yrl[16], yih[16], yil[16];
+            if (nvalid >= 16 * q + 16) {
+                // all 16 events inside the chunk: no per-event selects.  A zero or non-finite
+                // intensity makes ln I, and so the group's sum, non-finite: one test per group
+                // flags the set (its Y, and so only its own row of G, may then hold NaN; a
+                // flagged set's results are not used)
+                float lg16 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                // branch-free, so that the 16 events interleave: events past the end or sets past
-                // P contribute nothing; a zero or non-finite intensity flags the set
-                const float I = fmaf(ur[k], ur[k], ui[k] * ui[k]);
-                const bool valid = 16 * q + k < nvalid;
-                const bool ok = intensity_ok(I);
-                mybad |= valid && !ok;
-                const bool use = valid && ok;
-                const float Iu = use ? I : 1.f;
-                // both functions evaluated unconditionally (a select, not a branch, picks the result)
-                const float lgu = __logf(Iu);
-                const float rcu = __fdividef(1.f, Iu);
-                lt += use ? lgu : 0.f;
-                const float rc = use ? rcu : 0.f;
-                tf32_split(use ? ur[k] * rc : 0.f, yrh[k], yrl[k]);
-                tf32_split(use ? ui[k] * rc : 0.f, yih[k], yil[k]);
+                for (int k = 0; k < 16; ++k) {
+                    const float I = fmaf(ur[k], ur[k], ui[k] * ui[k]);
+                    lg16 += __logf(I);
+                    const float rc = __fdividef(1.f, I);
+                    tf32_split(ur[k] * rc, yrh[k], yrl[k]);
+                    tf32_split(ui[k] * rc, yih[k], yil[k]);
+                }
+                mybad |= !(fabsf(lg16) < INFINITY);
+                lt += lg16;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    // branch-free, so that the 16 events interleave: events past the end or sets past
+                    // P contribute nothing; a zero or non-finite intensity flags the set
+                    const float I = fmaf(ur[k], ur[k], ui[k] * ui[k]);
+                    const bool valid = 16 * q + k < nvalid;
+                    const bool ok = intensity_ok(I);
+                    mybad |= valid && !ok;
+                    const bool use = valid && ok;
+                    const float Iu = use ? I : 1.f;
+                    // both functions evaluated unconditionally (a select, not a branch, picks the result)
+                    const float lgu = __logf(Iu);
+                    const float rcu = __fdividef(1.f, Iu);
+                    lt += use ? lgu : 0.f;
+                    const float rc = use ? rcu : 0.f;
+                    tf32_split(use ? ur[k] * rc : 0.f, yrh[k], yrl[k]);
+                    tf32_split(use ? ui[k] * rc : 0.f, yih[k], yil[k]);
+                }
             }
             if (grad) {
                 tmem_st16(lane_t + C::T_D1 + 16 * q, yrh);  // Y hi over U, in place

@@ -194,18 +194,22 @@ cudaError_t launch_nll_grad_scratch(const float2* A, int K, int64_t n, int64_t l
                                     const double2* Psi, double nfac, double* nll, double* grad, float2* part,
                                     size_t part_bytes, unsigned* counter, int* badw, int* status, int max_blocks,
                                     int sm_count, cudaStream_t st);
-// P > 1: the autotuned tile shape
+// P > 1: the autotuned tile shape (precise: the fastest shape other than the tensor-core one)
 cudaError_t launch_nll(const float2* A, int K, int64_t n, int64_t ld, const float2* V, int P,
                        const double2* Psi, double nfac, double* nll, double* grad, void* ws, size_t ws_bytes,
-                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st);
+                       unsigned* counter, int* bad, int* status, int sm_count, cudaStream_t st, bool precise = false);
 
 // record a message for pwa_last_error(NULL) (calls without a handle)
 void record_global_error(const char* msg);
 
 // mode bits of the fit kernels: FIT_GAUGE rotates each start so that V_0 is real >= 0 and
 // freezes the phase component of V_0; FIT_POLAR makes the minimiser's coordinates of wave a
-// (rho_a, phi_a) with V_a = rho_a exp(i phi_a) instead of (Re V_a, Im V_a)
-constexpr int FIT_GAUGE = 1, FIT_POLAR = 2;
+// (rho_a, phi_a) with V_a = rho_a exp(i phi_a) instead of (Re V_a, Im V_a); FIT_PAUSE pauses a
+// start (status FIT_PAUSED) whose line search has backtracked FIT_PAUSE_BACKTRACKS times in a
+// row, a sign that the evaluation's rounding hides the decrease it looks for, so that the
+// caller can resume it (fit_resume_paused) on a more precise evaluation
+constexpr int FIT_GAUGE = 1, FIT_POLAR = 2, FIT_PAUSE = 4;
+constexpr int FIT_PAUSED = 4, FIT_PAUSE_BACKTRACKS = 10;
 
 size_t fit_workspace(int P_tot, int m);
 size_t fit_eval_bytes(int P, int K);
@@ -217,6 +221,9 @@ cudaError_t fit_launch_step(void* fitws, int P_tot, int m, const double* ft, con
                             double* theta_t = nullptr, const double* lb = nullptr);
 cudaError_t fit_export_x(void* fitws, int P_tot, int m, int K, int D, int p, int mode, double* xout, cudaStream_t s);
 cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaStream_t s);
+// paused starts -> running, their next evaluation at their accepted point; *host_count = how
+// many (the stream is synchronised)
+cudaError_t fit_resume_paused(void* fitws, int P_tot, int m, int* host_count, cudaStream_t s);
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
                              std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int D_of_p[],
                              cudaStream_t s);

@@ -375,7 +375,9 @@ def evaluate_toy(h, waves, Psi, prop, V_true, n_events, seed, stream, P_rand=256
                iters_first_learned=iters_learned[0] if iters_learned else 0,
                plain_stop=plain_stop, learned_seq_stop=lseq_stop,
                n_learned=nl, n_random=P_rand, Vs=np.array(Vs), fs=fs_a, ok=ok_a, A=A, kin=kin,
-               evals_learned=sum(r["evaluations"] for r in res_l), evals_random=sum(r["evaluations"] for r in res_r))
+               evals_learned=sum(r["evaluations"] for r in res_l), evals_random=sum(r["evaluations"] for r in res_r),
+               iters_max_random=max(r["iterations"] for r in res_r),
+               unconverged_random=sum(1 for r in res_r if r["status"] != 0))
     return out
 
 
@@ -396,7 +398,11 @@ def summarize(outs):
                time_to_global_plain_s=t_plain,
                time_to_global_learned_sequential_s=m("t_learned_seq"),
                time_to_global_batched_random_s=m("t_random"),
-               time_to_global_batched_learned_s=m("t_learned"))
+               time_to_global_batched_learned_s=m("t_learned"),
+               batched_random_time_median_s=float(np.median([o["t_random"] for o in outs])),
+               batched_random_time_max_s=float(np.max([o["t_random"] for o in outs])),
+               batched_random_iterations_max=int(np.max([o["iters_max_random"] for o in outs])),
+               toys_with_unconverged_random_start=int(sum(o["unconverged_random"] > 0 for o in outs)))
     for k in ("learned_sequential", "batched_random", "batched_learned"):
         res[f"speedup_{k}_vs_plain"] = t_plain / res[f"time_to_global_{k}_s"]
     return res

@@ -351,9 +351,11 @@ def test_normint_from_kinematics(h, K, n, weighted):
     assert np.all(np.abs(Psi_k.cpu().numpy() - Psi_a.cpu().numpy()) <= tol)  # the unfused path
 
 
-@pytest.mark.parametrize("K,n", [(4, 3001), (13, 20_001), (16, 100_000), (32, 9_999), (1, 1)])
+# the last three run several FP32 windows per block (two blocks per SM over whole tiles)
+@pytest.mark.parametrize("K,n", [(4, 3001), (13, 20_001), (16, 100_000), (32, 9_999), (1, 1),
+                                 (16, 1_000_003), (32, 300_001), (4, 5_000_001)])
 def test_hessian_fumili_and_exact(h, K, n):
-    p = make_problem(K, n, max(2 * n, 1000), SEED + 1500 + K, accept_reject=False)
+    p = make_problem(K, n, min(max(2 * n, 1000), 2_000_000), SEED + 1500 + K, accept_reject=False)
     ld = n + 1 if n % 2 else n + 2
     Ad = dev(padded(p.A, ld, fill=np.complex64(np.nan)))
     V = inputs.starts(1, K, SEED + 1600 + K)[0]
