@@ -2,13 +2,13 @@
 // batched evaluation, chosen by the autotuner when it is the fastest): the event x wave x start
 // contraction of Eq. 3 as two real GEMMs per tile of E = 64 events, in FP32-accurate
 // arithmetic emulated with three TF32 products, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
-// (each operand split as x = hi + lo: hi the nearest TF32 value, lo = x - hi exactly, of which the
-// tensor cores use the leading 11 bits; the dropped a_lo b_lo and the truncation of lo leave a
-// relative error below 2^-20 per product, and the products accumulate in FP32 in tensor memory).
+// (each operand split as x = hi + lo, hi the nearest TF32 value and lo the nearest TF32 value of
+// x - hi; the dropped a_lo b_lo and the rounding of lo leave a relative error near 2^-21 per
+// product, and the products accumulate in FP32 in tensor memory).
 //
-// Block: PB = 128 parameter sets (one per tensor-memory lane and per thread) x one chunk of
-// events, one block per SM.  Complex numbers are expanded into real rows and columns so that
-// each GEMM is a plain real product with both operands K-major:
+// Block: PB = 128 parameter sets (one per tensor-memory lane, two threads per set) x one chunk
+// of events, one block per SM.  Complex numbers are expanded into real rows and columns so
+// that each GEMM is a plain real product with both operands K-major:
 //
 //   GEMM1 (U = A V^T, M = 128 sets, N = 2E, contraction 2 KMAX):
 //     D1[p][e + E h] = sum_c V'[p][c] A'[e + E h][c],  V'[p] = (Re V_p | Im V_p),
@@ -22,26 +22,32 @@
 //     X[a, g=1] = (-Im A_a | Re A_a), so D2[p][a] = sum_e Re(conj(A_ea) w_ep) and
 //     D2[p][KMAX + a] = sum_e Im(conj(A_ea) w_ep).
 //
-// Shared memory holds V' (hi, lo), A' and X (hi, lo; both layouts are written from registers,
-// since a transposed TF32 operand is not available) and the low words of the G accumulators;
-// tensor memory holds D1 (Y hi overwrites it), Y lo, D2 and the high words of the G
-// accumulators.  D2 has two column blocks: hi.hi alone, and the small hi.lo + lo.hi.  They
-// accumulate in FP32 in tensor memory over WINDOW tiles (64 events), are added in FP32 (rounded
-// to nearest) into registers, and every FF_EVERY windows into the double-single G
-// accumulators.  The tensor cores' FP32 accumulation does not round to nearest; at a minimum the
-// data sum of the gradient is coherent (about n Psi^T V), so that error adds up over a window
-// instead of averaging out: draining every tile keeps it ~1e-8 of the gradient scale, 10x below
-// the minimiser's convergence threshold at 2e6 events.  At the end they are written to the
-// block's [chunk][P][1 + 2K] partials, the layout of the other tile shapes, so one finalisation
-// serves all.  Sum ln I: FP32 per tile and thread, double-single across tiles.  Every wait on the
-// tensor cores is bounded; a timeout sets status bit 1 and the block's sets' bad flags, waits
-// (bounded) for the MMAs in flight and frees the tensor memory.
+// Every MMA has N >= 128 where the shape allows it (N = 2E for GEMM1; the hi and lo parts of X
+// stacked as one operand of 2 N2 rows for GEMM2): an MMA instruction costs at least ~60 cycles
+// whatever its N, and N = 128 is the smallest that runs at the tensor cores' arithmetic rate.
+// Shared memory holds V', A' and X (hi, lo; both layouts are written from registers, since a
+// transposed TF32 operand is not available).  Tensor memory holds three regions of 2E columns
+// that rotate over the tiles (tile t: U in region 2t mod 3, Y hi written over it in place, Y lo
+// in region 2t + 1 mod 3) and D2, so GEMM1(t + 1) writes the third region while the epilogue of
+// tile t runs, and GEMM2(t) queues behind it.  D2 has two column blocks: hi.hi alone, and the
+// small hi.lo + lo.hi.  They accumulate in FP32 in tensor memory over one tile (64 events), are
+// added in FP32 (rounded to nearest) into registers, and every FF_EVERY tiles into the
+// double-single G accumulators (high words in registers, low words in shared memory).  The tensor cores' FP32 accumulation does not round
+// to nearest; at a minimum the data sum of the gradient is coherent (about n Psi^T V), so that
+// error adds up over the accumulation instead of averaging out: 64 events keep it ~1e-8 of the
+// gradient scale, 10x below the minimiser's convergence threshold at 2e6 events.  At the end
+// the sums are written to the block's [chunk][P][1 + 2K] partials, the layout of the other tile
+// shapes, so one finalisation serves all.  Sum ln I: FP32 per tile and thread, double-single
+// across tiles.
+//
+// The compute warps signal the MMA warp by mbarrier arrivals (they never wait for it to issue,
+// which blocks while the tensor cores' queue is full), the MMA warp signals them by
+// tcgen05.commit.  Every wait is bounded; a timeout sets an abort flag, after which no MMA is
+// issued, no tensor memory is touched and no wait is made, but every arrival and commit is still
+// made, so neither side waits for a phase the other skips.  A timeout sets status bit 1 and the
+// block's sets' bad flags; the tensor memory is freed after a bounded wait for the MMAs in flight.
 #include "nll_common.cuh"
 #include "tc.cuh"
-
-#ifndef PWA_TC_WINDOW
-#define PWA_TC_WINDOW 1
-#endif
 
 namespace pwa {
 
@@ -50,6 +56,7 @@ namespace {
 template <int KMAX>
 struct TcCfg {
     static constexpr int NC = 256, NT = NC + 32, E = 64, PB = 128;  // 8 compute warps + 1 MMA warp
+    static constexpr int NCW = NC / 32;  // compute warps (arrivals per phase)
     static constexpr int C1 = 2 * KMAX;  // GEMM1 contraction
     static constexpr int C2 = 2 * E;     // GEMM2 contraction
     static constexpr int N2 = 2 * KMAX;  // GEMM2 columns
@@ -64,19 +71,17 @@ struct TcCfg {
     static constexpr uint32_t SMEM_USED = OFF_BAR + 64;
     // at least half of an SM's shared memory, so that one block holds the SM (and its tensor memory)
     static constexpr uint32_t SMEM = SMEM_USED > 118784u ? SMEM_USED : 118784u;
-    // tensor-memory columns: D1 (U, then Y hi in place), Y lo, D2 (two column blocks: hi.hi, and
-    // hi.lo + lo.hi), the high words of the G accumulators
-    static constexpr uint32_t T_D1 = 0, T_YL = 2 * E, T_D2 = 4 * E, T_ACC = T_D2 + 2 * N2, TMEM_COLS = 512;
-    // tiles per FP32 accumulation window of G in tensor memory before it is added to the
-    // double-single accumulators (the tensor cores' accumulation is not rounded to nearest, so
-    // its error grows with the window)
-    static constexpr int WINDOW = PWA_TC_WINDOW;
-    // windows per double-single update of the G accumulators (FP32 round-to-nearest in between)
+    // tensor-memory columns: three rotating regions of 2E (U, then Y hi in place; Y lo), D2 (two
+    // column blocks: hi.hi, and hi.lo + lo.hi)
+    static constexpr uint32_t T_REG = 2 * E, T_D2 = 3 * T_REG, TMEM_COLS = 512;
+    // tiles per double-single update of the G accumulators (FP32 round-to-nearest in between)
     static constexpr int FF_EVERY = 4;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
     static constexpr int ITEMS = (ITEMS_TOT + NC - 1) / NC;       // per compute thread
+    static constexpr int NGRP = (N2 / 16 + 1) / 2;               // 16-column groups of G per thread
     static_assert(KMAX % 8 == 0 && KMAX <= 32, "tensor-core batched kernel: K <= 32");
-    static_assert(T_ACC + N2 <= TMEM_COLS, "tensor memory");
+    static_assert(T_D2 + 2 * N2 <= TMEM_COLS, "tensor memory");
+    static_assert(SMEM_USED <= 232448u, "shared memory");
     static_assert(OFF_XL == OFF_XH + X_BYTES, "X hi and lo form one operand of 2 N2 rows");
     static_assert(N2 % 16 == 0 && 2 * E <= 256 && 2 * N2 <= 256, "MMA shape");
     static_assert(A1_BYTES >= 2 * PB * sizeof(float4), "end-of-kernel exchange area");
@@ -84,40 +89,21 @@ struct TcCfg {
 
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 
-// named barriers (id 0 is __syncthreads) between the compute warps and the MMA warp; both
-// sides wait (bar.sync), so neither can run a barrier instance ahead of the other
-constexpr int NB_A = 1;   // A' (and for the first tile X) of the next tile stored
-constexpr int NB_Y0 = 2;  // Y of the first half of the tile's events in tensor memory
-constexpr int NB_Y1 = 3;  // Y of the second half
-constexpr int NB_C = 4;   // compute warps only
-
-__device__ __forceinline__ void nb_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ bool nb_or(int id, int n, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
-}
-
 // Warp roles: warps 0-7 (two threads per set: lane quarter warp % 4, event half warp / 4) load
 // and store the operand tiles and run the epilogue; warp 8 issues every MMA (one lane).
-// Per tile t:
-//   MMA warp:     [A'(t) stored] wait GEMM2(t-1) -> GEMM1(t) -> commit g1
-//                 [Y of events half 0 stored] GEMM2 k-steps of half 0
-//                 [Y of half 1 stored] GEMM2 k-steps of half 1 -> commit g2
-//   compute warps: wait g1 -> epilogue half 0 -> (arrive) -> epilogue half 1 -> (arrive)
-//                 -> store A'(t+1) -> (arrive) -> wait g2 -> store X(t+1), load tile t+2, drain G
-// so GEMM2 of half 0 runs during the epilogue of half 1, and GEMM1(t+1) during the X copy,
-// the loads and the drain.  The epilogue writes Y hi over D1 in place; GEMM1(t+1), which
-// overwrites D1, waits for GEMM2(t), which reads Y hi.  GEMM2 takes X hi and X lo as one
-// operand of 2 N2 rows (hi.hi and hi.lo in one MMA per k-step), then adds lo.hi into the second
-// column block.  Every WINDOW tiles the two column blocks are added to the G accumulators (high
-// words in tensor memory, low words in shared memory).  A wait that times out sets a block flag;
-// from then on no MMA is issued and no mbarrier wait is made, but every named barrier is still
-// passed in the same order by both roles, so neither waits on a barrier that the other skips.
+// Per tile t (u_t = region 2t mod 3 holds U(t), then Y hi(t); l_t = region 2t + 1 mod 3 = u_{t-1}
+// holds Y lo(t)):
+//   MMA warp:      wait a_ready(t + 1) [A'(t + 1) stored], wait g2(t - 1) [u_{t+1} = l_{t-1} free]
+//                  -> GEMM1(t + 1) into u_{t+1} -> commit g1
+//                  wait y_ready(t) [Y(t), X(t) stored, D2 drained] -> GEMM2(t) -> commit g2
+//   compute warps: wait g1(t) -> store A'(t + 1) (GEMM1(t) has read A'(t)) -> arrive a_ready
+//                  -> wait g2(t - 1) (Y lo region, X and D2 free) -> store X(t) -> epilogue and Y
+//                  of the tile in four quarters of 8 events -> drain D2 -> arrive y_ready
+//                  -> load the registers of tiles t + 2 (A') and t + 1 (X)
+// Tensor-core order: ... GEMM2(t - 1), GEMM1(t + 1), GEMM2(t), GEMM1(t + 2) ...; the epilogue of
+// tile t overlaps GEMM1(t + 1).  Phase discipline: every mbarrier completes once per tile, and
+// each waiter waits for the oldest phase it has not seen, which cannot be overtaken (the next
+// completion needs an arrival or an issue that comes after this wait).
 template <int KMAX>
 __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A, int K, int64_t n, int64_t ld,
                                                    const float2* __restrict__ V, int P, int64_t ev_per_chunk,
@@ -140,9 +126,11 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     const int64_t ntile = e_begin < e_end ? (e_end - e_begin + E - 1) / E : 0;
     uint64_t* bar_g1 = reinterpret_cast<uint64_t*>(tsm + C::OFF_BAR);
     uint64_t* bar_g2 = bar_g1 + 1;
-    uint64_t* bar_fin = bar_g1 + 2;
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(tsm + C::OFF_BAR + 24);
-    volatile int* abort_s = reinterpret_cast<volatile int*>(tsm + C::OFF_BAR + 28);
+    uint64_t* bar_a = bar_g1 + 2;  // A' of the next tile stored (one arrival per compute warp)
+    uint64_t* bar_y = bar_g1 + 3;  // Y and X of the tile stored, D2 drained (one arrival per compute warp)
+    uint64_t* bar_fin = bar_g1 + 4;
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(tsm + C::OFF_BAR + 40);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(tsm + C::OFF_BAR + 44);
 
     // V' = (Re V | Im V) per set, split into TF32 hi / lo
     for (int idx = tid; idx < C::PB * KMAX; idx += C::NT) {
@@ -157,10 +145,13 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
         *reinterpret_cast<float*>(tsm + C::OFF_VH + kmaj_off(pp, KMAX + a, C::SBO1)) = h;
         *reinterpret_cast<float*>(tsm + C::OFF_VL + kmaj_off(pp, KMAX + a, C::SBO1)) = l;
     }
+    for (int idx = tid; idx < C::N2 * C::PB; idx += C::NT) reinterpret_cast<float*>(tsm + C::OFF_ACC)[idx] = 0.f;
     if (warp == 0) tmem_alloc(taddr_s, C::TMEM_COLS);
     if (tid == 0) {
         mbar_init(bar_g1, 1);
         mbar_init(bar_g2, 1);
+        mbar_init(bar_a, C::NCW);
+        mbar_init(bar_y, C::NCW);
         mbar_init(bar_fin, 1);
         *abort_s = 0;
         fence_mbar_init();
@@ -173,10 +164,29 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     const uint32_t lane_t = tmem + ((uint32_t)(32 * lq) << 16);  // this warp's 32 lanes
     const uint32_t sbase = smem_u32(tsm);
     const bool grad = with_grad != 0;
+    // bounded wait; after a timeout (here or on the other side) no further wait is made
+    auto wait_or_abort = [&](uint64_t* b, uint32_t parity) {
+        if (*abort_s != 0) return false;
+        if (!mbar_wait_bounded(b, parity, TC_WAIT_NS)) {
+            *abort_s = 1;
+            return false;
+        }
+        tc_fence_after();
+        return true;
+    };
+    auto region = [&](int64_t t, int which) {  // which 0: u_t, 1: l_t
+        return (uint32_t)((2 * t + which) % 3) * C::T_REG;
+    };
 
     ff lsum = ff_zero();
-    bool mybad = false, drained = false;
-    int since_ff = 0;
+    bool mybad = false;
+    // double-single G accumulators of this thread's column groups: high words in registers, low
+    // words in shared memory ([column][PB])
+    float ghi[16 * C::NGRP];
+#pragma unroll
+    for (int v = 0; v < 16 * C::NGRP; ++v) ghi[v] = 0.f;
+    float* acc_lo = reinterpret_cast<float*>(tsm + C::OFF_ACC) + pl;
+    auto glo = [&](int i, int k) -> float& { return acc_lo[(16 * (hh + 2 * i) + k) * C::PB]; };
 
     if (mma_warp) {
         // ================================================================ MMA warp
@@ -185,59 +195,47 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
         const uint64_t dXh = umma_desc(sbase + C::OFF_XH, 128u, C::SBO2);
         constexpr uint32_t id1 = umma_idesc_tf32(128, 2 * E);
         constexpr uint32_t idw = umma_idesc_tf32(128, 2 * C::N2), idn = umma_idesc_tf32(128, C::N2);
-        int win = 0;
-        for (int64_t t = 0; t < ntile; ++t) {
-            nb_sync(NB_A, C::NT);
-            bool ab = *abort_s != 0;
-            if (!ab && grad && t > 0 && !mbar_wait_bounded(bar_g2, (uint32_t)((t - 1) & 1), TC_WAIT_NS)) {
-                ab = true;
-                *abort_s = 1;
+        // U = V' A'^T into region d: the small products (hi, lo) and (lo, hi) first, then (hi, hi),
+        // so that most accumulation steps add to a small running sum (the tensor cores' FP32
+        // accumulation does not round to nearest)
+        auto gemm1 = [&](uint32_t d) {
+            if (*abort_s == 0 && lane == 0) {
+#pragma unroll
+                for (int s = 0; s < C::C1 / 8; ++s) mma_tf32_ss(d, dVh + 16u * s, dAl + 16u * s, id1, s > 0 ? 1u : 0u);
+#pragma unroll
+                for (int s = 0; s < C::C1 / 8; ++s) mma_tf32_ss(d, dVl + 16u * s, dAh + 16u * s, id1, 1u);
+#pragma unroll
+                for (int s = 0; s < C::C1 / 8; ++s) mma_tf32_ss(d, dVh + 16u * s, dAh + 16u * s, id1, 1u);
             }
-            tc_fence_after();
-            if (!ab && lane == 0) {
-                // U = V' A'^T: the small products (hi, lo) and (lo, hi) first, then (hi, hi), so
-                // that most accumulation steps add to a small running sum (the tensor cores'
-                // FP32 accumulation does not round to nearest)
-#pragma unroll
-                for (int s = 0; s < C::C1 / 8; ++s)
-                    mma_tf32_ss(tmem + C::T_D1, dVh + 16u * s, dAl + 16u * s, id1, s > 0 ? 1u : 0u);
-#pragma unroll
-                for (int s = 0; s < C::C1 / 8; ++s) mma_tf32_ss(tmem + C::T_D1, dVl + 16u * s, dAh + 16u * s, id1, 1u);
-#pragma unroll
-                for (int s = 0; s < C::C1 / 8; ++s) mma_tf32_ss(tmem + C::T_D1, dVh + 16u * s, dAh + 16u * s, id1, 1u);
-                umma_commit(bar_g1);
-            }
+            if (lane == 0) umma_commit(bar_g1);
             __syncwarp();
+        };
+        if (ntile > 0) {
+            wait_or_abort(bar_a, 0);  // A'(0)
+            gemm1(tmem + region(0, 0));
+        }
+        for (int64_t t = 0; t < ntile; ++t) {
+            if (t + 1 < ntile) {
+                wait_or_abort(bar_a, (uint32_t)((t + 1) & 1));                // A'(t + 1)
+                if (grad && t >= 1) wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));  // region u_{t+1} = l_{t-1} read
+                gemm1(tmem + region(t + 1, 0));
+            }
             if (grad) {
-                const bool fresh = win == 0;
+                wait_or_abort(bar_y, (uint32_t)(t & 1));  // Y(t), X(t), D2 drained
+                if (*abort_s == 0 && lane == 0) {
+                    // G = Y X^T over the contraction c = (Re | Im) x 64 events: hi.hi and hi.lo in
+                    // one MMA per k-step (X hi and lo as one operand of 2 N2 rows), then lo.hi
+                    // into the second column block; the first k-step overwrites D2
+                    const uint32_t yh = tmem + region(t, 0), yl = tmem + region(t, 1);
 #pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-                    nb_sync(hf == 0 ? NB_Y0 : NB_Y1, C::NT);
-                    ab = ab || *abort_s != 0;
-                    tc_fence_after();
-                    if (!ab && lane == 0) {
-                        // contraction c = (Re | Im) x 64 events; this half's events are 16 hf + 0..15
-                        // and 32 + 16 hf + 0..15, i.e. k-steps 4 j + 2 hf + {0, 1}
+                    for (int s = 0; s < C::C2 / 8; ++s)
+                        mma_tf32_ts(tmem + C::T_D2, yh + 8u * s, dXh + 16u * s, idw, s > 0 ? 1u : 0u);
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-#pragma unroll
-                            for (int d = 0; d < 2; ++d) {
-                                const uint32_t s = 4 * j + 2 * hf + d;
-                                mma_tf32_ts(tmem + C::T_D2, tmem + C::T_D1 + 8u * s, dXh + 16u * s, idw,
-                                            (fresh && hf == 0 && j == 0 && d == 0) ? 0u : 1u);
-                            }
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-#pragma unroll
-                            for (int d = 0; d < 2; ++d) {
-                                const uint32_t s = 4 * j + 2 * hf + d;
-                                mma_tf32_ts(tmem + C::T_D2 + C::N2, tmem + C::T_YL + 8u * s, dXh + 16u * s, idn, 1u);
-                            }
-                        if (hf == 1) umma_commit(bar_g2);
-                    }
-                    __syncwarp();
+                    for (int s = 0; s < C::C2 / 8; ++s)
+                        mma_tf32_ts(tmem + C::T_D2 + C::N2, yl + 8u * s, dXh + 16u * s, idn, 1u);
                 }
-                if (++win == C::WINDOW || t + 1 == ntile) win = 0;
+                if (lane == 0) umma_commit(bar_g2);
+                __syncwarp();
             }
         }
         // every MMA of this warp has completed (bounded) before the tensor memory is released
@@ -248,10 +246,10 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
         // ================================================================ compute warps
         float2 ra[C::ITEMS][4];
         float4 rx[C::ITEMS][2];
-        // two register images of the same K x E tile:
-        //  ra: item (event e, waves 4 aq .. 4 aq + 3) for A'  (a warp reads 32 events of one wave row)
-        //  rx: item (wave a, events 4 eq .. 4 eq + 3) for X   (8 waves x 4 quads per warp)
-        auto load_tile = [&](int64_t e0) {
+        // two register images of K x E tiles: ra for A' (item: event e, waves 4 aq .. 4 aq + 3; a
+        // warp reads 32 events of one wave row), rx for X (item: wave a, events 4 eq .. 4 eq + 3;
+        // 8 waves x 4 quads per warp).  ra holds the tile after the current one, rx the current one.
+        auto load_a = [&](int64_t e0) {
 #pragma unroll
             for (int i = 0; i < C::ITEMS; ++i) {
                 const int j = tid + C::NC * i;
@@ -264,6 +262,12 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
                         ra[i][q] = (a < K && ge < e_end) ? __ldg(A + a * ld + ge) : make_float2(0.f, 0.f);
                     }
                 }
+            }
+        };
+        auto load_x = [&](int64_t e0) {
+#pragma unroll
+            for (int i = 0; i < C::ITEMS; ++i) {
+                const int j = tid + C::NC * i;
                 if (grad && j < C::ITEMS_TOT) {
                     const int blk = j >> 5, ln = j & 31;
                     const int a = (blk % (KMAX / 8)) * 8 + (ln & 7);
@@ -348,18 +352,31 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
                 }
             }
         };
-        float* acc_lo = reinterpret_cast<float*>(tsm + C::OFF_ACC) + pl;  // [column][PB]
         // Every tile the two column blocks of D2 are added in FP32 (round to nearest, on the CUDA
-        // cores) into racc; every FF_EVERY tiles racc enters the double-single G accumulators (hi
-        // in tensor memory, lo in shared memory).  The two threads of a lane take alternate groups
-        // of 16 columns (racc[16 i + k]: group hh + 2 i).
-        constexpr int NGRP = (C::N2 / 16 + 1) / 2;  // column groups per thread
-        float racc[16 * NGRP];
+        // cores) into racc; every FF_EVERY tiles racc enters the double-single G accumulators.
+        // The two threads of a lane take alternate groups of 16 columns (racc[16 i + k]: group
+        // hh + 2 i).
+        float racc[16 * C::NGRP];
 #pragma unroll
-        for (int v = 0; v < 16 * NGRP; ++v) racc[v] = 0.f;
-        auto drain_tile = [&]() {
+        for (int v = 0; v < 16 * C::NGRP; ++v) racc[v] = 0.f;
+        int since_ff = 0;
+        auto flush = [&]() {
 #pragma unroll
-            for (int i = 0; i < NGRP; ++i) {
+            for (int i = 0; i < C::NGRP; ++i) {
+                if (hh + 2 * i < C::N2 / 16) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const ff r = ff_add_f(ff{ghi[16 * i + k], glo(i, k)}, racc[16 * i + k]);
+                        ghi[16 * i + k] = r.hi;
+                        glo(i, k) = r.lo;
+                        racc[16 * i + k] = 0.f;
+                    }
+                }
+            }
+        };
+        auto drain = [&]() {
+#pragma unroll
+            for (int i = 0; i < C::NGRP; ++i) {
                 const int q = hh + 2 * i;
                 if (q < C::N2 / 16) {
                     float d0[16], d1[16];
@@ -370,63 +387,46 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
                     for (int k = 0; k < 16; ++k) racc[16 * i + k] += d0[k] + d1[k];
                 }
             }
-        };
-        auto flush = [&](bool first) {
-#pragma unroll
-            for (int i = 0; i < NGRP; ++i) {
-                const int q = hh + 2 * i;
-                if (q < C::N2 / 16) {
-                    float ah[16];
-                    tmem_ld16(lane_t + C::T_ACC + 16 * q, ah);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        float* lo = acc_lo + (16 * q + k) * C::PB;
-                        const ff r = ff_add_f(first ? ff_zero() : ff{ah[k], *lo}, racc[16 * i + k]);
-                        ah[k] = r.hi;
-                        *lo = r.lo;
-                        racc[16 * i + k] = 0.f;
-                    }
-                    tmem_st16(lane_t + C::T_ACC + 16 * q, ah);
-                }
+            if (++since_ff == C::FF_EVERY) {
+                flush();
+                since_ff = 0;
             }
-            tmem_wait_st();
         };
-        // I, ln I, W = U / I for the 16 events of column group q -> Y (hi over U, lo)
-        auto epilogue = [&](int q, int64_t nvalid, float& lt) {
-            float ur[16], ui[16];
-            tmem_ld16(lane_t + C::T_D1 + 16 * q, ur);
-            tmem_ld16(lane_t + C::T_D1 + E + 16 * q, ui);
+        // I, ln I, W = U / I for the 8 events 32 hh + 8 qq + 0..7 of the tile (U in region u) ->
+        // registers yr / yi (hi, lo); events past the end of the chunk or sets past P give 0
+        auto epi_math = [&](uint32_t u, int qq, int64_t nvalid, float& lt, float (&yrh)[8], float (&yrl)[8],
+                            float (&yih)[8], float (&yil)[8]) {
+            const int c0 = 32 * hh + 8 * qq;
+            float ur[8], ui[8];
+            tmem_ld8(lane_t + u + c0, ur);
+            tmem_ld8(lane_t + u + E + c0, ui);
             tmem_wait_ld();
-            float yrh[16], yrl[16], yih[16], yil[16];
-            if (nvalid >= 16 * q + 16) {
-                // all 16 events inside the chunk: no per-event selects.  A zero or non-finite
+            if (nvalid >= c0 + 8) {
+                // all 8 events inside the chunk: no per-event selects.  A zero or non-finite
                 // intensity makes ln I, and so the group's sum, non-finite: one test per group
                 // flags the set (its Y, and so only its own row of G, may then hold NaN; a
                 // flagged set's results are not used)
-                float lg16 = 0.f;
+                float lg = 0.f;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     const float I = fmaf(ur[k], ur[k], ui[k] * ui[k]);
-                    lg16 += __logf(I);
+                    lg += __logf(I);
                     const float rc = __fdividef(1.f, I);
                     tf32_split(ur[k] * rc, yrh[k], yrl[k]);
                     tf32_split(ui[k] * rc, yih[k], yil[k]);
                 }
-                mybad |= !(fabsf(lg16) < INFINITY);
-                lt += lg16;
+                mybad |= !(fabsf(lg) < INFINITY);
+                lt += lg;
             } else {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    // branch-free, so that the 16 events interleave: events past the end or sets past
-                    // P contribute nothing; a zero or non-finite intensity flags the set
+                for (int k = 0; k < 8; ++k) {
+                    // branch-free: a select, not a branch, picks each result
                     const float I = fmaf(ur[k], ur[k], ui[k] * ui[k]);
-                    const bool valid = 16 * q + k < nvalid;
+                    const bool valid = c0 + k < nvalid;
                     const bool ok = intensity_ok(I);
                     mybad |= valid && !ok;
                     const bool use = valid && ok;
                     const float Iu = use ? I : 1.f;
-                    // both functions evaluated unconditionally (a select, not a branch, picks the result)
                     const float lgu = __logf(Iu);
                     const float rcu = __fdividef(1.f, Iu);
                     lt += use ? lgu : 0.f;
@@ -435,70 +435,72 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
                     tf32_split(use ? ui[k] * rc : 0.f, yih[k], yil[k]);
                 }
             }
-            if (grad) {
-                tmem_st16(lane_t + C::T_D1 + 16 * q, yrh);  // Y hi over U, in place
-                tmem_st16(lane_t + C::T_D1 + E + 16 * q, yih);
-                tmem_st16(lane_t + C::T_YL + 16 * q, yrl);
-                tmem_st16(lane_t + C::T_YL + E + 16 * q, yil);
-                tmem_wait_st();
-            }
         };
-        bool ab = false;
-        // block-uniform (compute warps) wait on an MMA group; a timeout sets the abort flag
-        auto wait_mma = [&](uint64_t* b, uint32_t parity) {
-            const bool ok = ab || mbar_wait_bounded(b, parity, TC_WAIT_NS);
-            if (nb_or(NB_C, C::NC, !ok || *abort_s != 0)) {
-                ab = true;
-                if (tid == 0) *abort_s = 1;
-            }
-            tc_fence_after();
+        auto epi_store = [&](uint32_t u, uint32_t l, int qq, const float (&yrh)[8], const float (&yrl)[8],
+                             const float (&yih)[8], const float (&yil)[8]) {
+            const int c0 = 32 * hh + 8 * qq;
+            tmem_st8(lane_t + u + c0, yrh);  // Y hi over U, in place
+            tmem_st8(lane_t + u + E + c0, yih);
+            tmem_st8(lane_t + l + c0, yrl);
+            tmem_st8(lane_t + l + E + c0, yil);
         };
-        int win = 0;
+        auto arrive = [&](uint64_t* b) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive_one(b);
+        };
         if (ntile > 0) {
-            load_tile(e_begin);
+            load_a(e_begin);
+            load_x(e_begin);
             store_a1();
-            if (grad) store_x();
             fence_proxy_async_smem();
-            nb_sync(NB_A, C::NT);
-            if (ntile > 1) load_tile(e_begin + E);
+            arrive(bar_a);  // A'(0)
+            if (ntile > 1) load_a(e_begin + E);
         }
         for (int64_t t = 0; t < ntile; ++t) {
             const int64_t e0 = e_begin + t * E;
-            wait_mma(bar_g1, (uint32_t)(t & 1));  // GEMM1(t)
-            const int64_t nvalid = (pvalid && !ab) ? (e_end - e0) : 0;
+            const uint32_t u = region(t, 0), l = region(t, 1);
+            const bool ok1 = wait_or_abort(bar_g1, (uint32_t)(t & 1));  // GEMM1(t): U(t) in u, A' read
+            if (t + 1 < ntile) {
+                if (ok1) store_a1();  // A'(t + 1)
+                fence_proxy_async_smem();
+                arrive(bar_a);
+            }
+            const int64_t nvalid = (pvalid && ok1) ? (e_end - e0) : 0;
             float lt = 0.f;
+            float yrh[8], yrl[8], yih[8], yil[8];
+            if (grad) {
+                // GEMM2(t - 1) has read Y(t - 1) (region l = u_{t-1} may take Y lo(t)) and X(t - 1),
+                // and its sums are complete in D2
+                const bool ok2 = t == 0 || wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));
+                if (ok2) store_x();  // X(t)
+                if (ok1 && ok2) {
 #pragma unroll 1
-            for (int hf = 0; hf < 2; ++hf) {
-                if (!ab) epilogue(2 * hh + hf, nvalid, lt);
-                tc_fence_before();
-                if (grad) nb_sync(hf == 0 ? NB_Y0 : NB_Y1, C::NT);
-            }
-            lsum = ff_add_f(lsum, lt);
-            if (t + 1 < ntile) {
-                if (!ab) store_a1();  // A'(t + 1): GEMM1(t) has completed
-                fence_proxy_async_smem();
-                nb_sync(NB_A, C::NT);
-            }
-            if (grad) wait_mma(bar_g2, (uint32_t)(t & 1));  // GEMM2(t)
-            if (t + 1 < ntile) {
-                if (grad && !ab) store_x();  // X(t + 1): GEMM2(t) has completed
-                if (t + 2 < ntile) load_tile(e0 + 2 * E);
-                fence_proxy_async_smem();
-            }
-            if (grad && (++win == C::WINDOW || t + 1 == ntile)) {
-                if (!ab) {
-                    drain_tile();
-                    if (++since_ff == C::FF_EVERY || t + 1 == ntile) {
-                        flush(!drained);
-                        drained = true;
-                        since_ff = 0;
+                    for (int qq = 0; qq < 4; ++qq) {
+                        epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
+                        epi_store(u, l, qq, yrh, yrl, yih, yil);
                     }
                 }
-                win = 0;
+                if (ok2 && t > 0) drain();
+                if (ok1 && ok2) tmem_wait_st();
+                fence_proxy_async_smem();
+                tc_fence_before();
+                arrive(bar_y);
+            } else if (ok1) {
+#pragma unroll 1
+                for (int qq = 0; qq < 4; ++qq) epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
             }
+            lsum = ff_add_f(lsum, lt);
+            if (t + 2 < ntile) load_a(e0 + 2 * E);
+            if (t + 1 < ntile) load_x(e0 + E);
+        }
+        if (grad && ntile > 0 && wait_or_abort(bar_g2, (uint32_t)((ntile - 1) & 1))) {  // the last GEMM2
+            drain();
+            flush();
         }
     }
-    // ---- results: combine the two threads of each set (the A' area is free now)
+    // ---- results: combine the two threads of each set (the A' area is free now: every MMA has
+    // completed)
     tc_fence_before();
     __syncthreads();
     const bool timeout = *abort_s != 0;
@@ -506,29 +508,28 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     float4* xch = reinterpret_cast<float4*>(tsm + C::OFF_AH);
     if (!mma_warp && hh == 1) xch[pl] = make_float4(lsum.hi, lsum.lo, mybad ? 1.f : 0.f, 0.f);
     __syncthreads();
-    float2* prow = part + ((int64_t)blockIdx.x * P + p) * NV;  // this set's partials (valid if pvalid)
-    if (!mma_warp && hh == 0 && pvalid) {
-        const float4 o = xch[pl];
-        lsum = ff_add(lsum, ff{o.x, o.y});
-        prow[0] = make_float2(lsum.hi, lsum.lo);
-        if (mybad || o.z != 0.f || timeout) bad[p] = 1;
-    }
-    // G: both threads of a set write their column groups
-    if (!mma_warp && grad) {
-        const float* acc_lo = reinterpret_cast<const float*>(tsm + C::OFF_ACC) + pl;
-#pragma unroll 1
-        for (int q = hh; q < C::N2 / 16; q += 2) {
-            float ah[16];
-            tmem_ld16(lane_t + C::T_ACC + 16 * q, ah);
-            tmem_wait_ld();
-            if (pvalid) {
+    if (!mma_warp) {
+        float2* prow = part + ((int64_t)blockIdx.x * P + p) * NV;  // this set's partials (valid if pvalid)
+        if (hh == 0 && pvalid) {
+            const float4 o = xch[pl];
+            lsum = ff_add(lsum, ff{o.x, o.y});
+            prow[0] = make_float2(lsum.hi, lsum.lo);
+            if (mybad || o.z != 0.f || timeout) bad[p] = 1;
+        }
+        // G: both threads of a set write their column groups
+        if (grad && pvalid) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int col = 16 * q + k;
-                    const int a = col % KMAX, g = col / KMAX;
-                    if (a < K)
-                        prow[1 + 2 * a + g] =
-                            (drained && !timeout) ? make_float2(ah[k], acc_lo[col * C::PB]) : make_float2(0.f, 0.f);
+            for (int i = 0; i < C::NGRP; ++i) {
+                const int q = hh + 2 * i;
+                if (q < C::N2 / 16) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int col = 16 * q + k;
+                        const int a = col % KMAX, g = col / KMAX;
+                        if (a < K)
+                            prow[1 + 2 * a + g] =
+                                (ntile > 0 && !timeout) ? make_float2(ghi[16 * i + k], glo(i, k)) : make_float2(0.f, 0.f);
+                    }
                 }
             }
         }
