@@ -55,8 +55,9 @@ namespace {
 
 template <int KMAX>
 struct TcCfg {
-    static constexpr int NC = 256, NT = NC + 32, E = 64, PB = 128;  // 8 compute warps + 1 MMA warp
-    static constexpr int NCW = NC / 32;  // compute warps (arrivals per phase)
+    // 8 epilogue warps, 1 MMA warp, 3 operand warps
+    static constexpr int NC = 256, NL = 96, NT = NC + 32 + NL, E = 64, PB = 128;
+    static constexpr int NCW = NC / 32, NLW = NL / 32;  // arrivals per phase
     static constexpr int C1 = 2 * KMAX;  // GEMM1 contraction
     static constexpr int C2 = 2 * E;     // GEMM2 contraction
     static constexpr int N2 = 2 * KMAX;  // GEMM2 columns
@@ -77,7 +78,7 @@ struct TcCfg {
     // tiles per double-single update of the G accumulators (FP32 round-to-nearest in between)
     static constexpr int FF_EVERY = 4;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
-    static constexpr int ITEMS = (ITEMS_TOT + NC - 1) / NC;       // per compute thread
+    static constexpr int ITEMS = (ITEMS_TOT + NL - 1) / NL;       // per operand thread
     static constexpr int NGRP = (N2 / 16 + 1) / 2;               // 16-column groups of G per thread
     static_assert(KMAX % 8 == 0 && KMAX <= 32, "tensor-core batched kernel: K <= 32");
     static_assert(T_D2 + 2 * N2 <= TMEM_COLS, "tensor memory");
@@ -89,23 +90,27 @@ struct TcCfg {
 
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 
-// Warp roles: warps 0-7 (two threads per set: lane quarter warp % 4, event half warp / 4) load
-// and store the operand tiles and run the epilogue; warp 8 issues every MMA (one lane).
+// Warp roles: warps 0-7 (two threads per set: lane quarter warp % 4, event half warp / 4) run
+// the epilogue; warp 8 issues every MMA (one lane); warps 9-11 load the amplitude tiles and store
+// the operands A' and X (hi, lo) into shared memory.
 // Per tile t (u_t = region 2t mod 3 holds U(t), then Y hi(t); l_t = region 2t + 1 mod 3 = u_{t-1}
 // holds Y lo(t)):
-//   MMA warp:      wait a_ready(t + 1) [A'(t + 1) stored], wait g2(t - 1) [u_{t+1} = l_{t-1} free]
+//   MMA warp:      wait a_ready(t + 1), wait g2(t - 1) [u_{t+1} = l_{t-1} free]
 //                  -> GEMM1(t + 1) into u_{t+1} -> commit g1
 //                  wait y_ready(t) [Y(t), X(t) stored, D2 drained] -> GEMM2(t) -> commit g2
-//   compute warps: wait g1(t) -> store A'(t + 1) (GEMM1(t) has read A'(t)) -> arrive a_ready
-//                  -> wait g2(t - 1) (Y lo region, X and D2 free) -> store X(t) -> epilogue and Y
-//                  of the tile in four quarters of 8 events -> drain D2 -> arrive y_ready
-//                  -> load the registers of tiles t + 2 (A') and t + 1 (X)
+//   operand warps: wait g1(t) -> store A'(t + 1) (GEMM1(t) has read A'(t)) -> arrive a_ready
+//                  -> wait g2(t - 1) (GEMM2(t - 1) has read X(t - 1)) -> store X(t) -> arrive
+//                  y_ready -> load the registers of tiles t + 2 (A') and t + 1 (X)
+//   epilogue warps: wait g1(t) -> arrive a_ready -> wait g2(t - 1) (Y lo region free, D2
+//                  complete) -> epilogue and Y of the tile in four quarters of 8 events -> drain
+//                  D2 -> arrive y_ready
 // Tensor-core order: ... GEMM2(t - 1), GEMM1(t + 1), GEMM2(t), GEMM1(t + 2) ...; the epilogue of
 // tile t overlaps GEMM1(t + 1).  Phase discipline: every mbarrier completes once per tile, and
-// each waiter waits for the oldest phase it has not seen, which cannot be overtaken (the next
-// completion needs an arrival or an issue that comes after this wait).
+// each waiter waits for the oldest phase it has not seen, which cannot be overtaken: the next
+// completion needs an arrival or an issue that comes after this wait (every warp that waits on
+// g1 arrives on a_ready afterwards, every warp that waits on g2 arrives on y_ready afterwards).
 template <int KMAX>
-__global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A, int K, int64_t n, int64_t ld,
+__global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A, int K, int64_t n, int64_t ld,
                                                    const float2* __restrict__ V, int P, int64_t ev_per_chunk,
                                                    float2* __restrict__ part, int* __restrict__ bad, int with_grad,
                                                    int* __restrict__ status) {
@@ -113,12 +118,12 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     constexpr int E = C::E;
     extern __shared__ __align__(1024) unsigned char tsm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool mma_warp = warp == 8;
+    const bool compute = warp < 8, mma_warp = warp == 8;  // warps 9 to 11 stage the operands
     const int lq = warp & 3, hh = (warp >> 2) & 1;  // tensor-memory lane quarter; event / column half
     const int pl = 32 * lq + lane;                  // this thread's set within the block (its lane)
     const int p0 = blockIdx.y * C::PB;
     const int p = p0 + pl;
-    const bool pvalid = !mma_warp && p < P;
+    const bool pvalid = compute && p < P;
     const int NV = 1 + 2 * K;
     const int64_t e_begin = (int64_t)blockIdx.x * ev_per_chunk;
     int64_t e_end = e_begin + ev_per_chunk;
@@ -126,8 +131,10 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     const int64_t ntile = e_begin < e_end ? (e_end - e_begin + E - 1) / E : 0;
     uint64_t* bar_g1 = reinterpret_cast<uint64_t*>(tsm + C::OFF_BAR);
     uint64_t* bar_g2 = bar_g1 + 1;
-    uint64_t* bar_a = bar_g1 + 2;  // A' of the next tile stored (one arrival per compute warp)
-    uint64_t* bar_y = bar_g1 + 3;  // Y and X of the tile stored, D2 drained (one arrival per compute warp)
+    // A' of the next tile stored (operand warps), the epilogue warps past their wait for the
+    // current GEMM1 (one arrival per warp)
+    uint64_t* bar_a = bar_g1 + 2;
+    uint64_t* bar_y = bar_g1 + 3;  // Y and X of the tile stored, D2 drained (one arrival per epilogue and operand warp)
     uint64_t* bar_fin = bar_g1 + 4;
     uint32_t* taddr_s = reinterpret_cast<uint32_t*>(tsm + C::OFF_BAR + 40);
     volatile int* abort_s = reinterpret_cast<volatile int*>(tsm + C::OFF_BAR + 44);
@@ -150,8 +157,8 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     if (tid == 0) {
         mbar_init(bar_g1, 1);
         mbar_init(bar_g2, 1);
-        mbar_init(bar_a, C::NCW);
-        mbar_init(bar_y, C::NCW);
+        mbar_init(bar_a, C::NCW + C::NLW);
+        mbar_init(bar_y, C::NCW + C::NLW);
         mbar_init(bar_fin, 1);
         *abort_s = 0;
         fence_mbar_init();
@@ -242,116 +249,8 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
         if (lane == 0) umma_commit(bar_fin);
         __syncwarp();
         if (!mbar_wait_bounded(bar_fin, 0, TC_WAIT_NS)) *abort_s = 1;
-    } else {
-        // ================================================================ compute warps
-        float2 ra[C::ITEMS][4];
-        float4 rx[C::ITEMS][2];
-        // two register images of K x E tiles: ra for A' (item: event e, waves 4 aq .. 4 aq + 3; a
-        // warp reads 32 events of one wave row), rx for X (item: wave a, events 4 eq .. 4 eq + 3;
-        // 8 waves x 4 quads per warp).  ra holds the tile after the current one, rx the current one.
-        auto load_a = [&](int64_t e0) {
-#pragma unroll
-            for (int i = 0; i < C::ITEMS; ++i) {
-                const int j = tid + C::NC * i;
-                if (j < C::ITEMS_TOT) {
-                    const int e = j % E, aq = j / E;
-                    const int64_t ge = e0 + e;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int a = 4 * aq + q;
-                        ra[i][q] = (a < K && ge < e_end) ? __ldg(A + a * ld + ge) : make_float2(0.f, 0.f);
-                    }
-                }
-            }
-        };
-        auto load_x = [&](int64_t e0) {
-#pragma unroll
-            for (int i = 0; i < C::ITEMS; ++i) {
-                const int j = tid + C::NC * i;
-                if (grad && j < C::ITEMS_TOT) {
-                    const int blk = j >> 5, ln = j & 31;
-                    const int a = (blk % (KMAX / 8)) * 8 + (ln & 7);
-                    const int eq = (blk / (KMAX / 8)) * 4 + (ln >> 3);
-                    const int64_t ge = e0 + 4 * eq;
-                    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-                    if (a < K) {
-                        const float2* src = A + a * ld + ge;
-                        if (ge + 3 < e_end) {
-                            x0 = __ldg(reinterpret_cast<const float4*>(src));
-                            x1 = __ldg(reinterpret_cast<const float4*>(src + 2));
-                        } else {
-                            float2 tq[4];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) tq[k] = ge + k < e_end ? __ldg(src + k) : make_float2(0.f, 0.f);
-                            x0 = make_float4(tq[0].x, tq[0].y, tq[1].x, tq[1].y);
-                            x1 = make_float4(tq[2].x, tq[2].y, tq[3].x, tq[3].y);
-                        }
-                    }
-                    rx[i][0] = x0;
-                    rx[i][1] = x1;
-                }
-            }
-        };
-        auto st4 = [&](uint32_t off, float a, float b, float c, float d) {
-            *reinterpret_cast<float4*>(tsm + off) = make_float4(a, b, c, d);
-        };
-        // registers -> A' or X (hi and lo).  Each 16-byte store of a warp phase (8 lanes) hits 8
-        // different rows of one core-matrix column: A' rows e = 8 consecutive events, X rows a =
-        // 8 consecutive waves.
-        auto store_a1 = [&]() {
-#pragma unroll
-            for (int i = 0; i < C::ITEMS; ++i) {
-                const int j = tid + C::NC * i;
-                if (j < C::ITEMS_TOT) {
-                    const int e = j % E, aq = j / E;
-                    float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        tf32_split(ra[i][q].x, rh[q], rl[q]);
-                        tf32_split(ra[i][q].y, ih[q], il[q]);
-                    }
-                    const uint32_t re0 = kmaj_off(e, 4 * aq, C::SBO1), im0 = kmaj_off(e, KMAX + 4 * aq, C::SBO1);
-                    const uint32_t re1 = kmaj_off(E + e, 4 * aq, C::SBO1), im1 = kmaj_off(E + e, KMAX + 4 * aq, C::SBO1);
-                    st4(C::OFF_AH + re0, rh[0], rh[1], rh[2], rh[3]);
-                    st4(C::OFF_AH + im0, -ih[0], -ih[1], -ih[2], -ih[3]);
-                    st4(C::OFF_AH + re1, ih[0], ih[1], ih[2], ih[3]);
-                    st4(C::OFF_AH + im1, rh[0], rh[1], rh[2], rh[3]);
-                    st4(C::OFF_AL + re0, rl[0], rl[1], rl[2], rl[3]);
-                    st4(C::OFF_AL + im0, -il[0], -il[1], -il[2], -il[3]);
-                    st4(C::OFF_AL + re1, il[0], il[1], il[2], il[3]);
-                    st4(C::OFF_AL + im1, rl[0], rl[1], rl[2], rl[3]);
-                }
-            }
-        };
-        auto store_x = [&]() {
-#pragma unroll
-            for (int i = 0; i < C::ITEMS; ++i) {
-                const int j = tid + C::NC * i;
-                if (j < C::ITEMS_TOT) {
-                    const int blk = j >> 5, ln = j & 31;
-                    const int a = (blk % (KMAX / 8)) * 8 + (ln & 7);
-                    const int eq = (blk / (KMAX / 8)) * 4 + (ln >> 3);
-                    const float xr[4] = {rx[i][0].x, rx[i][0].z, rx[i][1].x, rx[i][1].z};
-                    const float xi[4] = {rx[i][0].y, rx[i][0].w, rx[i][1].y, rx[i][1].w};
-                    float rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        tf32_split(xr[q], rh[q], rl[q]);
-                        tf32_split(xi[q], ih[q], il[q]);
-                    }
-                    const uint32_t g0r = kmaj_off(a, 4 * eq, C::SBO2), g0i = kmaj_off(a, E + 4 * eq, C::SBO2);
-                    const uint32_t g1r = kmaj_off(KMAX + a, 4 * eq, C::SBO2), g1i = kmaj_off(KMAX + a, E + 4 * eq, C::SBO2);
-                    st4(C::OFF_XH + g0r, rh[0], rh[1], rh[2], rh[3]);
-                    st4(C::OFF_XH + g0i, ih[0], ih[1], ih[2], ih[3]);
-                    st4(C::OFF_XH + g1r, -ih[0], -ih[1], -ih[2], -ih[3]);
-                    st4(C::OFF_XH + g1i, rh[0], rh[1], rh[2], rh[3]);
-                    st4(C::OFF_XL + g0r, rl[0], rl[1], rl[2], rl[3]);
-                    st4(C::OFF_XL + g0i, il[0], il[1], il[2], il[3]);
-                    st4(C::OFF_XL + g1r, -il[0], -il[1], -il[2], -il[3]);
-                    st4(C::OFF_XL + g1i, rl[0], rl[1], rl[2], rl[3]);
-                }
-            }
-        };
+    } else if (compute) {
+        // ================================================================ epilogue warps
         // Every tile the two column blocks of D2 are added in FP32 (round to nearest, on the CUDA
         // cores) into racc; every FF_EVERY tiles racc enters the double-single G accumulators.
         // The two threads of a lane take alternate groups of 16 columns (racc[16 i + k]: group
@@ -449,31 +348,22 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
             __syncwarp();
             if (lane == 0) mbarrier_arrive_one(b);
         };
-        if (ntile > 0) {
-            load_a(e_begin);
-            load_x(e_begin);
-            store_a1();
-            fence_proxy_async_smem();
-            arrive(bar_a);  // A'(0)
-            if (ntile > 1) load_a(e_begin + E);
-        }
+        // The epilogue warps also arrive on a_ready, once before the first tile and once after
+        // each wait for GEMM1(t), so that GEMM1(t + 1) cannot complete before every epilogue warp
+        // has seen GEMM1(t) complete (a parity wait must not fall two phases behind)
+        if (ntile > 0) arrive(bar_a);
         for (int64_t t = 0; t < ntile; ++t) {
             const int64_t e0 = e_begin + t * E;
             const uint32_t u = region(t, 0), l = region(t, 1);
-            const bool ok1 = wait_or_abort(bar_g1, (uint32_t)(t & 1));  // GEMM1(t): U(t) in u, A' read
-            if (t + 1 < ntile) {
-                if (ok1) store_a1();  // A'(t + 1)
-                fence_proxy_async_smem();
-                arrive(bar_a);
-            }
+            const bool ok1 = wait_or_abort(bar_g1, (uint32_t)(t & 1));  // GEMM1(t): U(t) in u
+            if (t + 1 < ntile) arrive(bar_a);
             const int64_t nvalid = (pvalid && ok1) ? (e_end - e0) : 0;
             float lt = 0.f;
             float yrh[8], yrl[8], yih[8], yil[8];
             if (grad) {
-                // GEMM2(t - 1) has read Y(t - 1) (region l = u_{t-1} may take Y lo(t)) and X(t - 1),
-                // and its sums are complete in D2
+                // GEMM2(t - 1) has read Y(t - 1) (region l = u_{t-1} may take Y lo(t)), and its sums
+                // are complete in D2
                 const bool ok2 = t == 0 || wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));
-                if (ok2) store_x();  // X(t)
                 if (ok1 && ok2) {
 #pragma unroll 1
                     for (int qq = 0; qq < 4; ++qq) {
@@ -483,20 +373,155 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
                 }
                 if (ok2 && t > 0) drain();
                 if (ok1 && ok2) tmem_wait_st();
-                fence_proxy_async_smem();
-                tc_fence_before();
                 arrive(bar_y);
             } else if (ok1) {
 #pragma unroll 1
                 for (int qq = 0; qq < 4; ++qq) epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
             }
             lsum = ff_add_f(lsum, lt);
-            if (t + 2 < ntile) load_a(e0 + 2 * E);
-            if (t + 1 < ntile) load_x(e0 + E);
         }
         if (grad && ntile > 0 && wait_or_abort(bar_g2, (uint32_t)((ntile - 1) & 1))) {  // the last GEMM2
             drain();
             flush();
+        }
+    } else {
+        // ================================================================ operand warps
+        const int lt = tid - (C::NC + 32);
+        auto arrive = [&](uint64_t* b) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive_one(b);
+        };
+        float2 ra[C::ITEMS][4];
+        float4 rx[C::ITEMS][2];
+        // two register images of K x E tiles: ra for A' (item: event e, waves 4 aq .. 4 aq + 3; a
+        // warp reads 32 events of one wave row), rx for X (item: wave a, events 4 eq .. 4 eq + 3;
+        // 8 waves x 4 quads per warp).  ra holds the tile after the current one, rx the current one.
+        auto load_a = [&](int64_t e0) {
+#pragma unroll
+            for (int i = 0; i < C::ITEMS; ++i) {
+                const int j = lt + C::NL * i;
+                if (j < C::ITEMS_TOT) {
+                    const int e = j % E, aq = j / E;
+                    const int64_t ge = e0 + e;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int a = 4 * aq + q;
+                        ra[i][q] = (a < K && ge < e_end) ? __ldg(A + a * ld + ge) : make_float2(0.f, 0.f);
+                    }
+                }
+            }
+        };
+        auto load_x = [&](int64_t e0) {
+#pragma unroll
+            for (int i = 0; i < C::ITEMS; ++i) {
+                const int j = lt + C::NL * i;
+                if (grad && j < C::ITEMS_TOT) {
+                    const int blk = j >> 5, ln = j & 31;
+                    const int a = (blk % (KMAX / 8)) * 8 + (ln & 7);
+                    const int eq = (blk / (KMAX / 8)) * 4 + (ln >> 3);
+                    const int64_t ge = e0 + 4 * eq;
+                    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+                    if (a < K) {
+                        const float2* src = A + a * ld + ge;
+                        if (ge + 3 < e_end) {
+                            x0 = __ldg(reinterpret_cast<const float4*>(src));
+                            x1 = __ldg(reinterpret_cast<const float4*>(src + 2));
+                        } else {
+                            float2 tq[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) tq[k] = ge + k < e_end ? __ldg(src + k) : make_float2(0.f, 0.f);
+                            x0 = make_float4(tq[0].x, tq[0].y, tq[1].x, tq[1].y);
+                            x1 = make_float4(tq[2].x, tq[2].y, tq[3].x, tq[3].y);
+                        }
+                    }
+                    rx[i][0] = x0;
+                    rx[i][1] = x1;
+                }
+            }
+        };
+        auto st4 = [&](uint32_t off, float a, float b, float c, float d) {
+            *reinterpret_cast<float4*>(tsm + off) = make_float4(a, b, c, d);
+        };
+        // registers -> A' or X (hi and lo).  Each 16-byte store of a warp phase (8 lanes) hits 8
+        // different rows of one core-matrix column: A' rows e = 8 consecutive events, X rows a =
+        // 8 consecutive waves.
+        auto store_a1 = [&]() {
+#pragma unroll
+            for (int i = 0; i < C::ITEMS; ++i) {
+                const int j = lt + C::NL * i;
+                if (j < C::ITEMS_TOT) {
+                    const int e = j % E, aq = j / E;
+                    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        tf32_split(ra[i][q].x, rh[q], rl[q]);
+                        tf32_split(ra[i][q].y, ih[q], il[q]);
+                    }
+                    const uint32_t re0 = kmaj_off(e, 4 * aq, C::SBO1), im0 = kmaj_off(e, KMAX + 4 * aq, C::SBO1);
+                    const uint32_t re1 = kmaj_off(E + e, 4 * aq, C::SBO1), im1 = kmaj_off(E + e, KMAX + 4 * aq, C::SBO1);
+                    st4(C::OFF_AH + re0, rh[0], rh[1], rh[2], rh[3]);
+                    st4(C::OFF_AH + im0, -ih[0], -ih[1], -ih[2], -ih[3]);
+                    st4(C::OFF_AH + re1, ih[0], ih[1], ih[2], ih[3]);
+                    st4(C::OFF_AH + im1, rh[0], rh[1], rh[2], rh[3]);
+                    st4(C::OFF_AL + re0, rl[0], rl[1], rl[2], rl[3]);
+                    st4(C::OFF_AL + im0, -il[0], -il[1], -il[2], -il[3]);
+                    st4(C::OFF_AL + re1, il[0], il[1], il[2], il[3]);
+                    st4(C::OFF_AL + im1, rl[0], rl[1], rl[2], rl[3]);
+                }
+            }
+        };
+        auto store_x = [&]() {
+#pragma unroll
+            for (int i = 0; i < C::ITEMS; ++i) {
+                const int j = lt + C::NL * i;
+                if (j < C::ITEMS_TOT) {
+                    const int blk = j >> 5, ln = j & 31;
+                    const int a = (blk % (KMAX / 8)) * 8 + (ln & 7);
+                    const int eq = (blk / (KMAX / 8)) * 4 + (ln >> 3);
+                    const float xr[4] = {rx[i][0].x, rx[i][0].z, rx[i][1].x, rx[i][1].z};
+                    const float xi[4] = {rx[i][0].y, rx[i][0].w, rx[i][1].y, rx[i][1].w};
+                    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        tf32_split(xr[q], rh[q], rl[q]);
+                        tf32_split(xi[q], ih[q], il[q]);
+                    }
+                    const uint32_t g0r = kmaj_off(a, 4 * eq, C::SBO2), g0i = kmaj_off(a, E + 4 * eq, C::SBO2);
+                    const uint32_t g1r = kmaj_off(KMAX + a, 4 * eq, C::SBO2), g1i = kmaj_off(KMAX + a, E + 4 * eq, C::SBO2);
+                    st4(C::OFF_XH + g0r, rh[0], rh[1], rh[2], rh[3]);
+                    st4(C::OFF_XH + g0i, ih[0], ih[1], ih[2], ih[3]);
+                    st4(C::OFF_XH + g1r, -ih[0], -ih[1], -ih[2], -ih[3]);
+                    st4(C::OFF_XH + g1i, rh[0], rh[1], rh[2], rh[3]);
+                    st4(C::OFF_XL + g0r, rl[0], rl[1], rl[2], rl[3]);
+                    st4(C::OFF_XL + g0i, il[0], il[1], il[2], il[3]);
+                    st4(C::OFF_XL + g1r, -il[0], -il[1], -il[2], -il[3]);
+                    st4(C::OFF_XL + g1i, rl[0], rl[1], rl[2], rl[3]);
+                }
+            }
+        };
+        if (ntile > 0) {
+            load_a(e_begin);
+            load_x(e_begin);
+            store_a1();
+            arrive(bar_a);  // A'(0)
+            if (ntile > 1) load_a(e_begin + E);
+        }
+        for (int64_t t = 0; t < ntile; ++t) {
+            const int64_t e0 = e_begin + t * E;
+            const bool ok1 = wait_or_abort(bar_g1, (uint32_t)(t & 1));  // GEMM1(t) has read A'(t)
+            if (t + 1 < ntile) {
+                if (ok1) store_a1();  // A'(t + 1)
+                arrive(bar_a);
+            }
+            if (grad) {
+                // GEMM2(t - 1) has read X(t - 1)
+                const bool ok2 = t == 0 || wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));
+                if (ok2) store_x();  // X(t)
+                arrive(bar_y);
+            }
+            if (t + 2 < ntile) load_a(e0 + 2 * E);
+            if (grad && t + 1 < ntile) load_x(e0 + E);
         }
     }
     // ---- results: combine the two threads of each set (the A' area is free now: every MMA has
@@ -506,9 +531,9 @@ __global__ void __launch_bounds__(288, 1) k_nll_tc(const float2* __restrict__ A,
     const bool timeout = *abort_s != 0;
     if (timeout && tid == 0) atomicOr(status, 2);
     float4* xch = reinterpret_cast<float4*>(tsm + C::OFF_AH);
-    if (!mma_warp && hh == 1) xch[pl] = make_float4(lsum.hi, lsum.lo, mybad ? 1.f : 0.f, 0.f);
+    if (compute && hh == 1) xch[pl] = make_float4(lsum.hi, lsum.lo, mybad ? 1.f : 0.f, 0.f);
     __syncthreads();
-    if (!mma_warp) {
+    if (compute) {
         float2* prow = part + ((int64_t)blockIdx.x * P + p) * NV;  // this set's partials (valid if pvalid)
         if (hh == 0 && pvalid) {
             const float4 o = xch[pl];
