@@ -76,7 +76,7 @@ struct TcCfg {
     // column blocks: hi.hi, and hi.lo + lo.hi)
     static constexpr uint32_t T_REG = 2 * E, T_D2 = 3 * T_REG, TMEM_COLS = 512;
     // tiles per double-single update of the G accumulators (FP32 round-to-nearest in between)
-    static constexpr int FF_EVERY = 4;
+    static constexpr int FF_EVERY = 8;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
     static constexpr int ITEMS = (ITEMS_TOT + NL - 1) / NL;       // per operand thread
     static constexpr int NGRP = (N2 / 16 + 1) / 2;               // 16-column groups of G per thread
