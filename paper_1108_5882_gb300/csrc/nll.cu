@@ -1180,10 +1180,13 @@ int batched_shape(int K, int64_t n, int P) { return tuned_shape(K, n, P); }
 size_t nll_workspace(int K, int64_t n, int P, int sm_count) {
     const size_t NV = 1 + 2 * (size_t)K;
     if (P == 1) return sizeof(float2) * NV * (size_t)sm_count * 8;
-    // batched: the (E = 64, PB = 64) geometry has the most chunks of all shapes
-    int nchunk;
+    // batched: the most chunks of all shapes, the SIMT ones (at most those of (E = 64, PB = 64),
+    // two blocks per SM) and the tensor-core one (E = 48, PB = 128, one block per SM)
+    int nchunk, nchunk_tc;
     int64_t epc;
     batched_geometry(n, P, 64, 64, sm_count, &nchunk, &epc);
+    batched_geometry(n, P, 128, 48, sm_count, &nchunk_tc, &epc, 1);
+    if (nchunk_tc > nchunk) nchunk = nchunk_tc;
     return sizeof(float2) * NV * (size_t)P * (size_t)nchunk;
 }
 

@@ -1,6 +1,6 @@
 // Batched -lnL and gradient for P parameter sets on the tensor cores (one tile shape of the
 // batched evaluation, chosen by the autotuner when it is the fastest): the event x wave x start
-// contraction of Eq. 3 as two real GEMMs per tile of E = 64 events, in FP32-accurate
+// contraction of Eq. 3 as two real GEMMs per tile of E = 48 events, in FP32-accurate
 // arithmetic emulated with three TF32 products, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
 // (each operand split as x = hi + lo, hi the nearest TF32 value and lo the nearest TF32 value of
 // x - hi; the dropped a_lo b_lo and the rounding of lo leave a relative error near 2^-21 per
@@ -22,23 +22,25 @@
 //     X[a, g=1] = (-Im A_a | Re A_a), so D2[p][a] = sum_e Re(conj(A_ea) w_ep) and
 //     D2[p][KMAX + a] = sum_e Im(conj(A_ea) w_ep).
 //
-// Every MMA has N >= 128 where the shape allows it (N = 2E for GEMM1; the hi and lo parts of X
-// stacked as one operand of 2 N2 rows for GEMM2): an MMA instruction costs at least ~60 cycles
-// whatever its N, and N = 128 is the smallest that runs at the tensor cores' arithmetic rate.
-// Shared memory holds V', A' and X (hi, lo; both layouts are written from registers, since a
-// transposed TF32 operand is not available).  Tensor memory holds three regions of 2E columns
-// that rotate over the tiles (tile t: U in region 2t mod 3, Y hi written over it in place, Y lo
-// in region 2t + 1 mod 3) and D2, so GEMM1(t + 1) writes the third region while the epilogue of
-// tile t runs, and GEMM2(t) queues behind it.  D2 has two column blocks: hi.hi alone, and the
-// small hi.lo + lo.hi.  They accumulate in FP32 in tensor memory over one tile (64 events), are
-// added in FP32 (rounded to nearest) into registers, and every FF_EVERY tiles into the
-// double-single G accumulators (high words in registers, low words in shared memory).  The tensor cores' FP32 accumulation does not round
+// GEMM2's MMAs have N = 2 N2 >= 128 (the hi and lo parts of X stacked as one operand) where K
+// allows it; GEMM1's have N = 2E = 96, a compromise: an MMA instruction costs at least ~60
+// cycles whatever its N (N = 128 is the smallest at the tensor cores' arithmetic rate), but
+// 48-event tiles let tensor memory hold four regions of 2E columns beside D2.  Shared memory
+// holds V', A' and X (hi, lo; both layouts are written from registers, since a transposed TF32
+// operand is not available).  The four regions rotate over the tiles (tile t: U in region
+// 2t mod 4, Y hi written over it in place, Y lo in region 2t + 1 mod 4), so GEMM1(t + 1) writes
+// the regions of tile t - 1 while the epilogue of tile t runs, and the epilogue writes Y lo(t)
+// into a region whose last reader, GEMM2(t - 2), has completed: it waits for GEMM2(t - 1) only
+// to drain D2.  D2 has two column blocks: hi.hi alone, and the small hi.lo + lo.hi.  They
+// accumulate in FP32 in tensor memory over one tile, are added in FP32 (rounded to nearest)
+// into registers, and every FF_EVERY tiles into the double-single G accumulators (high words in
+// registers, low words in shared memory).  The tensor cores' FP32 accumulation does not round
 // to nearest; at a minimum the data sum of the gradient is coherent (about n Psi^T V), so that
-// error adds up over the accumulation instead of averaging out: 64 events keep it ~1e-8 of the
-// gradient scale, 10x below the minimiser's convergence threshold at 2e6 events.  At the end
-// the sums are written to the block's [chunk][P][1 + 2K] partials, the layout of the other tile
-// shapes, so one finalisation serves all.  Sum ln I: FP32 per tile and thread, double-single
-// across tiles.
+// error adds up over the accumulation instead of averaging out: draining every tile keeps it
+// ~1e-8 of the gradient scale, 10x below the minimiser's convergence threshold at 2e6 events.
+// At the end the sums are written to the block's [chunk][P][1 + 2K] partials, the layout of the
+// other tile shapes, so one finalisation serves all.  Sum ln I: FP32 per tile and thread,
+// double-single across tiles.
 //
 // The compute warps signal the MMA warp by mbarrier arrivals (they never wait for it to issue,
 // which blocks while the tensor cores' queue is full), the MMA warp signals them by
@@ -56,7 +58,7 @@ namespace {
 template <int KMAX>
 struct TcCfg {
     // 8 epilogue warps, 1 MMA warp, 3 operand warps
-    static constexpr int NC = 256, NL = 96, NT = NC + 32 + NL, E = 64, PB = 128;
+    static constexpr int NC = 256, NL = 96, NT = NC + 32 + NL, E = 48, PB = 128;
     static constexpr int NCW = NC / 32, NLW = NL / 32;  // arrivals per phase
     static constexpr int C1 = 2 * KMAX;  // GEMM1 contraction
     static constexpr int C2 = 2 * E;     // GEMM2 contraction
@@ -72,9 +74,10 @@ struct TcCfg {
     static constexpr uint32_t SMEM_USED = OFF_BAR + 64;
     // at least half of an SM's shared memory, so that one block holds the SM (and its tensor memory)
     static constexpr uint32_t SMEM = SMEM_USED > 118784u ? SMEM_USED : 118784u;
-    // tensor-memory columns: three rotating regions of 2E (U, then Y hi in place; Y lo), D2 (two
+    // tensor-memory columns: four rotating regions of 2E (U, then Y hi in place; Y lo), D2 (two
     // column blocks: hi.hi, and hi.lo + lo.hi)
-    static constexpr uint32_t T_REG = 2 * E, T_D2 = 3 * T_REG, TMEM_COLS = 512;
+    static constexpr uint32_t NREG = 4, T_REG = 2 * E, T_D2 = NREG * T_REG, TMEM_COLS = 512;
+    static constexpr int NQ = E / 16;  // epilogue quarters of 8 events per thread
     // tiles per double-single update of the G accumulators (FP32 round-to-nearest in between)
     static constexpr int FF_EVERY = 8;
     static constexpr int ITEMS_TOT = E * KMAX / 4;                // load items per tile and layout
@@ -84,7 +87,8 @@ struct TcCfg {
     static_assert(T_D2 + 2 * N2 <= TMEM_COLS, "tensor memory");
     static_assert(SMEM_USED <= 232448u, "shared memory");
     static_assert(OFF_XL == OFF_XH + X_BYTES, "X hi and lo form one operand of 2 N2 rows");
-    static_assert(N2 % 16 == 0 && 2 * E <= 256 && 2 * N2 <= 256, "MMA shape");
+    static_assert(N2 % 16 == 0 && (2 * E) % 16 == 0 && 2 * E <= 256 && 2 * N2 <= 256, "MMA shape");
+    static_assert(E % 16 == 0 && (E * KMAX / 4) % 32 == 0, "whole 8-event quarters; whole warps of load items");
     static_assert(A1_BYTES >= 2 * PB * sizeof(float4), "end-of-kernel exchange area");
 };
 
@@ -93,19 +97,19 @@ constexpr uint64_t TC_WAIT_NS = 1000000000ull;
 // Warp roles: warps 0-7 (two threads per set: lane quarter warp % 4, event half warp / 4) run
 // the epilogue; warp 8 issues every MMA (one lane); warps 9-11 load the amplitude tiles and store
 // the operands A' and X (hi, lo) into shared memory.
-// Per tile t (u_t = region 2t mod 3 holds U(t), then Y hi(t); l_t = region 2t + 1 mod 3 = u_{t-1}
-// holds Y lo(t)):
-//   MMA warp:      wait a_ready(t + 1), wait g2(t - 1) [u_{t+1} = l_{t-1} free]
+// Per tile t (u_t = region 2t mod 4 holds U(t), then Y hi(t); l_t = region 2t + 1 mod 4 holds
+// Y lo(t); u_{t+2} = u_t, l_{t+2} = l_t):
+//   MMA warp:      wait a_ready(t + 1), wait g2(t - 1) [u_{t+1} = u_{t-1} free]
 //                  -> GEMM1(t + 1) into u_{t+1} -> commit g1
 //                  wait y_ready(t) [Y(t), X(t) stored, D2 drained] -> GEMM2(t) -> commit g2
 //   operand warps: wait g1(t) -> store A'(t + 1) (GEMM1(t) has read A'(t)) -> arrive a_ready
 //                  -> wait g2(t - 1) (GEMM2(t - 1) has read X(t - 1)) -> store X(t) -> arrive
 //                  y_ready -> load the registers of tiles t + 2 (A') and t + 1 (X)
-//   epilogue warps: wait g1(t) -> arrive a_ready -> wait g2(t - 1) (Y lo region free, D2
-//                  complete) -> epilogue and Y of the tile in four quarters of 8 events -> drain
-//                  D2 -> arrive y_ready
+//   epilogue warps: wait g1(t) -> arrive a_ready -> epilogue and Y of the tile in three quarters
+//                  of 8 events (l_t = l_{t-2}: GEMM1(t) was issued after GEMM2(t - 2) completed)
+//                  -> wait g2(t - 1) (D2 complete) -> drain D2 -> arrive y_ready
 // Tensor-core order: ... GEMM2(t - 1), GEMM1(t + 1), GEMM2(t), GEMM1(t + 2) ...; the epilogue of
-// tile t overlaps GEMM1(t + 1).  Phase discipline: every mbarrier completes once per tile, and
+// tile t overlaps GEMM2(t - 1) and GEMM1(t + 1).  Phase discipline: every mbarrier completes once per tile, and
 // each waiter waits for the oldest phase it has not seen, which cannot be overtaken: the next
 // completion needs an arrival or an issue that comes after this wait (every warp that waits on
 // g1 arrives on a_ready afterwards, every warp that waits on g2 arrives on y_ready afterwards).
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
         return true;
     };
     auto region = [&](int64_t t, int which) {  // which 0: u_t, 1: l_t
-        return (uint32_t)((2 * t + which) % 3) * C::T_REG;
+        return (uint32_t)((2 * t + which) % C::NREG) * C::T_REG;
     };
 
     ff lsum = ff_zero();
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
         for (int64_t t = 0; t < ntile; ++t) {
             if (t + 1 < ntile) {
                 wait_or_abort(bar_a, (uint32_t)((t + 1) & 1));                // A'(t + 1)
-                if (grad && t >= 1) wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));  // region u_{t+1} = l_{t-1} read
+                if (grad && t >= 1) wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));  // region u_{t+1} = u_{t-1} read
                 gemm1(tmem + region(t + 1, 0));
             }
             if (grad) {
@@ -291,11 +295,11 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
                 since_ff = 0;
             }
         };
-        // I, ln I, W = U / I for the 8 events 32 hh + 8 qq + 0..7 of the tile (U in region u) ->
+        // I, ln I, W = U / I for the 8 events (E/2) hh + 8 qq + 0..7 of the tile (U in region u) ->
         // registers yr / yi (hi, lo); events past the end of the chunk or sets past P give 0
         auto epi_math = [&](uint32_t u, int qq, int64_t nvalid, float& lt, float (&yrh)[8], float (&yrl)[8],
                             float (&yih)[8], float (&yil)[8]) {
-            const int c0 = 32 * hh + 8 * qq;
+            const int c0 = (E / 2) * hh + 8 * qq;
             float ur[8], ui[8];
             tmem_ld8(lane_t + u + c0, ur);
             tmem_ld8(lane_t + u + E + c0, ui);
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
         };
         auto epi_store = [&](uint32_t u, uint32_t l, int qq, const float (&yrh)[8], const float (&yrl)[8],
                              const float (&yih)[8], const float (&yil)[8]) {
-            const int c0 = 32 * hh + 8 * qq;
+            const int c0 = (E / 2) * hh + 8 * qq;
             tmem_st8(lane_t + u + c0, yrh);  // Y hi over U, in place
             tmem_st8(lane_t + u + E + c0, yih);
             tmem_st8(lane_t + l + c0, yrl);
@@ -361,22 +365,23 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
             float lt = 0.f;
             float yrh[8], yrl[8], yih[8], yil[8];
             if (grad) {
-                // GEMM2(t - 1) has read Y(t - 1) (region l = u_{t-1} may take Y lo(t)), and its sums
-                // are complete in D2
-                const bool ok2 = t == 0 || wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));
-                if (ok1 && ok2) {
+                // region l = l_{t-2} is free: GEMM1(t), which has completed, was issued after
+                // GEMM2(t - 2), its last reader
+                if (ok1) {
 #pragma unroll 1
-                    for (int qq = 0; qq < 4; ++qq) {
+                    for (int qq = 0; qq < C::NQ; ++qq) {
                         epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
                         epi_store(u, l, qq, yrh, yrl, yih, yil);
                     }
                 }
+                // GEMM2(t - 1) complete: its sums in D2, drained before GEMM2(t) overwrites them
+                const bool ok2 = t == 0 || wait_or_abort(bar_g2, (uint32_t)((t - 1) & 1));
                 if (ok2 && t > 0) drain();
-                if (ok1 && ok2) tmem_wait_st();
+                if (ok1) tmem_wait_st();
                 arrive(bar_y);
             } else if (ok1) {
 #pragma unroll 1
-                for (int qq = 0; qq < 4; ++qq) epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
+                for (int qq = 0; qq < C::NQ; ++qq) epi_math(u, qq, nvalid, lt, yrh, yrl, yih, yil);
             }
             lsum = ff_add_f(lsum, lt);
         }

@@ -303,13 +303,14 @@ def test_nll_grad_batched_pipelined_shape(h, K, P, n, monkeypatch):
 
 @pytest.mark.parametrize("K,P,n", [(4, 3, 3001), (8, 64, 40_001), (13, 130, 9_999), (16, 64, 20_000),
                                    (32, 256, 200_001), (32, 7, 1), (29, 300, 70_001), (24, 129, 33),
-                                   (16, 100, 4_900), (8, 90, 14_500)])
+                                   (16, 100, 14_500), (8, 90, 21_800), (16, 64, 6_400)])
 def test_nll_grad_batched_tensor_core_shape(h, K, P, n, monkeypatch):
     # the tensor-core kernel (shape 4: 3xTF32 products accumulated in FP32 in tensor memory,
-    # 64-event tiles over three rotating tensor-memory regions, 128 sets per block) forced by the
+    # 48-event tiles over four rotating tensor-memory regions, 128 sets per block) forced by the
     # tuning override: ragged odd tails (NaN in the padding column), one, two, three and many
     # tiles per block (the pipeline's start-up and end), more tiles than the double-single flush
-    # interval, several blocks of sets with a partial last one, K padded to 8, 16 or 32 waves
+    # interval, several blocks of sets with a partial last one, K padded to 8, 16 or 32 waves, and
+    # more event chunks than the SIMT shapes' geometry (the workspace is sized for both)
     monkeypatch.setenv("PWA_BATCHED_SHAPE", "4")
     p = make_problem(K, n, max(2 * n, 1000), SEED + 900 + K, accept_reject=False)
     V = inputs.starts(P, K, SEED + P + 2)
