@@ -297,7 +297,9 @@ PWA_API void pwa_fit_default_opts(pwa_fit_opts* opts);
  * Evaluation: the autotuned tile shape of each fit; a start whose line search backtracks 10
  * times in a row pauses, and once no start is running the paused ones resume from their
  * accepted points with the fastest FP32 SIMT shape (the tensor-core shape's rounding can hide
- * the decrease the line search looks for near a minimum). */
+ * the decrease the line search looks for near a minimum); only the resumed starts are then
+ * evaluated, gathered into one dense batch per fit.  PWA_FIT_PAUSE_BACKTRACKS=b (1..255)
+ * overrides the 10. */
 PWA_API pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits,
                                  const pwa_fit_opts* opts, pwa_fit_result* results, void* stream);
 

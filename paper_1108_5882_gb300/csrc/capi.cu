@@ -875,16 +875,22 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     const int m = o.history;
     pwa_status st = ensure_workspace(h, ws_need, P_tot);
     if (st != PWA_OK) return st;
-    // fit state + per-fit evaluation buffers (V trial, nll, grad)
+    // fit state + per-fit evaluation buffers (V trial, nll, grad; twice: the second set holds the
+    // dense batch of the starts resumed in the precise phase, with their indices)
     size_t state_b = pwa::fit_workspace(P_tot, m);
     size_t need = state_b;
-    for (int f = 0; f < n_fits; ++f) need += pwa::fit_eval_bytes(fits[f].P, fits[f].K);
+    for (int f = 0; f < n_fits; ++f) need += 2 * pwa::fit_eval_bytes(fits[f].P, fits[f].K) + 256 + sizeof(int) * fits[f].P;
     st = grow_fitws(h, need);
     if (st != PWA_OK) return st;
     struct EvalBuf {
         float2* Vt;
         double* nll;
         double* grad;
+        float2* Vc;  // the resumed starts' V, their results and indices into the fit
+        double* nll_c;
+        double* grad_c;
+        int* idx;
+        int n_c;
     };
     std::vector<EvalBuf> eb(n_fits);
     std::vector<int> K_of_p(P_tot);
@@ -900,6 +906,15 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
             c += r(sizeof(double) * P);
             eb[f].grad = reinterpret_cast<double*>(c);
             c += r(sizeof(double) * (size_t)P * 2 * K);
+            eb[f].Vc = reinterpret_cast<float2*>(c);
+            c += r(sizeof(float2) * (size_t)P * K);
+            eb[f].nll_c = reinterpret_cast<double*>(c);
+            c += r(sizeof(double) * P);
+            eb[f].grad_c = reinterpret_cast<double*>(c);
+            c += r(sizeof(double) * (size_t)P * 2 * K);
+            eb[f].idx = reinterpret_cast<int*>(c);
+            c += r(sizeof(int) * (size_t)P);
+            eb[f].n_c = 0;
             for (int p = 0; p < P; ++p) K_of_p[q++] = 2 * K;  // components per start
         }
     }
@@ -914,19 +929,39 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     // Two phases.  First every fit evaluates with its autotuned tile shape; a start whose line
     // search keeps backtracking (the tensor-core shape's rounding, ~1e-8 of the gradient scale,
     // can hide the decrease near a minimum) pauses.  Then the paused starts resume from their
-    // accepted points with the fastest FP32 SIMT shape, without pausing, until they stop.
+    // accepted points with the fastest FP32 SIMT shape, without pausing, until they stop; only
+    // they are evaluated, as one dense batch per fit (the step skips every other start).
     bool precise = false;
+    // PWA_FIT_PAUSE_BACKTRACKS=b (1..255) overrides the pause limit (a test takes it to 1 so that
+    // many starts pause and resume)
+    int pause_mode = pwa::FIT_PAUSE;
+    if (const char* pb = getenv("PWA_FIT_PAUSE_BACKTRACKS")) {
+        const int b = atoi(pb);
+        if (b >= 1 && b <= 255) pause_mode |= b << pwa::FIT_PAUSE_SHIFT;
+    }
     auto iteration = [&]() -> cudaError_t {
         int p_off = 0;
         for (int f = 0; f < n_fits; ++f) {
             const pwa_fit_desc& d = fits[f];
-            cudaError_t ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
-                                             reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll,
-                                             eb[f].grad, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
-                                             h->sm_count, s, precise);
+            cudaError_t ee = cudaSuccess;
+            if (!precise) {
+                ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vt, d.P,
+                                     reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll, eb[f].grad,
+                                     h->ws, h->ws_bytes, h->counters, h->bad, h->status, h->sm_count, s, false);
+            } else if (eb[f].n_c > 0) {
+                ee = pwa::fit_gather_sets(eb[f].Vt, eb[f].idx, eb[f].n_c, d.K, eb[f].Vc, s);
+                if (ee == cudaSuccess)
+                    ee = pwa::launch_nll(reinterpret_cast<const float2*>(d.A), d.K, d.n, d.ld, eb[f].Vc, eb[f].n_c,
+                                         reinterpret_cast<const double2*>(d.Psi), d.n_factor, eb[f].nll_c,
+                                         eb[f].grad_c, h->ws, h->ws_bytes, h->counters, h->bad, h->status,
+                                         h->sm_count, s, true);
+                if (ee == cudaSuccess)
+                    ee = pwa::fit_scatter_sets(eb[f].nll_c, eb[f].grad_c, eb[f].idx, eb[f].n_c, 2 * d.K, eb[f].nll,
+                                               eb[f].grad, s);
+            }
             if (ee != cudaSuccess) return ee;
             ee = pwa::fit_launch_step(h->fitws, P_tot, m, eb[f].nll, eb[f].grad, eb[f].Vt, d.K, d.P, p_off,
-                                      o.gtol * std::fabs(d.n_factor), fit_mode(o) | (precise ? 0 : pwa::FIT_PAUSE),
+                                      o.gtol * std::fabs(d.n_factor), fit_mode(o) | (precise ? 0 : pause_mode),
                                       o.max_iter, s);
             if (ee != cudaSuccess) return ee;
             p_off += d.P;
@@ -939,6 +974,31 @@ pwa_status pwa_fit_batch(pwa_handle* h, const pwa_fit_desc* fits, int n_fits, co
     e = pwa::fit_resume_paused(h->fitws, P_tot, m, &n_paused, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "fit resume");
     if (n_paused > 0) {
+        std::vector<int> run;
+        e = pwa::fit_running_list(h->fitws, P_tot, m, run, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "fit resume");
+        std::vector<int> loc;
+        int p_off = 0;
+        size_t r = 0;
+        for (int f = 0; f < n_fits && e == cudaSuccess; ++f) {
+            loc.clear();
+            for (; r < run.size() && run[r] < p_off + fits[f].P; ++r) loc.push_back(run[r] - p_off);
+            eb[f].n_c = (int)loc.size();
+            if (!loc.empty())
+                e = cudaMemcpyAsync(eb[f].idx, loc.data(), sizeof(int) * loc.size(), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            p_off += fits[f].P;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "fit resume");
+        // a smaller batch may take more event chunks per set than the full one
+        size_t ws_c = 0;
+        for (int f = 0; f < n_fits; ++f)
+            if (eb[f].n_c > 0) {
+                const size_t w = pwa::nll_workspace(fits[f].K, fits[f].n, eb[f].n_c, h->sm_count);
+                if (w > ws_c) ws_c = w;
+            }
+        st = ensure_workspace(h, ws_c, P_tot);
+        if (st != PWA_OK) return st;
         precise = true;
         e = run_fit_loop(h, s, o, P_tot, m, iteration);
         if (e != cudaSuccess) return cuda_fail(h, e, "fit loop (precise evaluation)");

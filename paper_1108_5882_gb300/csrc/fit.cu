@@ -244,7 +244,7 @@ __device__ __forceinline__ void lbfgs_step_body(FitState& st, int p, double fnew
             const int nf = st.nfail[p] + 1;
             st.nfail[p] = nf;
             if (an < 1e-20) st.status[p] = 2;
-            else if ((mode & FIT_PAUSE) && nf >= FIT_PAUSE_BACKTRACKS) st.status[p] = FIT_PAUSED;
+            else if ((mode & FIT_PAUSE) && nf >= fit_pause_backtracks(mode)) st.status[p] = FIT_PAUSED;
         }
         __syncthreads();
         if (st.status[p] == FIT_PAUSED) write_trial(x, x, 0.0, K, F, Vrow, th_row, polar);
@@ -546,6 +546,48 @@ cudaError_t fit_resume_paused(void* fitws, int P_tot, int m, int* host_count, cu
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_count, st.running, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
+}
+
+cudaError_t fit_running_list(void* fitws, int P_tot, int m, std::vector<int>& idx, cudaStream_t s) {
+    FitState st = carve(fitws, P_tot, m);
+    std::vector<int> status(P_tot);
+    cudaError_t e = cudaMemcpyAsync(status.data(), st.status, sizeof(int) * P_tot, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    idx.clear();
+    for (int p = 0; p < P_tot; ++p)
+        if (status[p] == FIT_RUNNING) idx.push_back(p);
+    return e;
+}
+
+__global__ void k_gather_sets(const float2* __restrict__ Vt, const int* __restrict__ idx, int n, int K,
+                              float2* __restrict__ Vc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * K; i += gridDim.x * blockDim.x)
+        Vc[i] = Vt[(int64_t)idx[i / K] * K + i % K];
+}
+
+__global__ void k_scatter_sets(const double* __restrict__ nll_c, const double* __restrict__ grad_c,
+                               const int* __restrict__ idx, int n, int D, double* __restrict__ nll,
+                               double* __restrict__ grad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * D; i += gridDim.x * blockDim.x) {
+        const int r = i / D, c = i % D;
+        grad[(int64_t)idx[r] * D + c] = grad_c[i];
+        if (c == 0) nll[idx[r]] = nll_c[r];
+    }
+}
+
+cudaError_t fit_gather_sets(const float2* Vt, const int* idx, int n, int K, float2* Vc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n * K + 255) / 256;
+    k_gather_sets<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(Vt, idx, n, K, Vc);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_scatter_sets(const double* nll_c, const double* grad_c, const int* idx, int n, int D, double* nll,
+                             double* grad, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n * D + 255) / 256;
+    k_scatter_sets<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(nll_c, grad_c, idx, n, D, nll, grad);
+    return cudaGetLastError();
 }
 
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,

@@ -210,6 +210,12 @@ void record_global_error(const char* msg);
 // caller can resume it (fit_resume_paused) on a more precise evaluation
 constexpr int FIT_GAUGE = 1, FIT_POLAR = 2, FIT_PAUSE = 4;
 constexpr int FIT_PAUSED = 4, FIT_PAUSE_BACKTRACKS = 10;
+// the pause limit travels in bits 8..15 of the mode (0: FIT_PAUSE_BACKTRACKS)
+constexpr int FIT_PAUSE_SHIFT = 8;
+__host__ __device__ __forceinline__ int fit_pause_backtracks(int mode) {
+    const int b = (mode >> FIT_PAUSE_SHIFT) & 255;
+    return b > 0 ? b : FIT_PAUSE_BACKTRACKS;
+}
 
 size_t fit_workspace(int P_tot, int m);
 size_t fit_eval_bytes(int P, int K);
@@ -224,6 +230,14 @@ cudaError_t fit_launch_count(void* fitws, int P_tot, int m, int* host_out, cudaS
 // paused starts -> running, their next evaluation at their accepted point; *host_count = how
 // many (the stream is synchronised)
 cudaError_t fit_resume_paused(void* fitws, int P_tot, int m, int* host_count, cudaStream_t s);
+// the starts whose status is running, in increasing order (the stream is synchronised)
+cudaError_t fit_running_list(void* fitws, int P_tot, int m, std::vector<int>& idx, cudaStream_t s);
+// a subset of the parameter sets of one fit as a dense batch: Vc[i] = Vt[idx[i]] (K waves each),
+// and the results of that batch back into the fit's rows: nll[idx[i]] = nll_c[i], grad[idx[i]]
+// = grad_c[i] (D components each)
+cudaError_t fit_gather_sets(const float2* Vt, const int* idx, int n, int K, float2* Vc, cudaStream_t s);
+cudaError_t fit_scatter_sets(const double* nll_c, const double* grad_c, const int* idx, int n, int D, double* nll,
+                             double* grad, cudaStream_t s);
 cudaError_t fit_read_results(void* fitws, int P_tot, int m, std::vector<double>& f, std::vector<double>& gmax,
                              std::vector<int>& iter, std::vector<int>& evals, std::vector<int>& status, int D_of_p[],
                              cudaStream_t s);

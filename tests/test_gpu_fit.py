@@ -184,6 +184,30 @@ def test_multistart_and_uneven_fits_in_one_call(h):
                 assert gmax < 1e-5 and abs(S - 1) < 1e-4
 
 
+def test_paused_starts_resume_as_a_dense_batch(h, monkeypatch):
+    # a start pauses after its first backtrack (PWA_FIT_PAUSE_BACKTRACKS=1 instead of 10), so most
+    # starts of three fits (tensor-core shape forced for the K=16 and K=32 fits) finish in the
+    # precise phase, where only the resumed starts are evaluated: gathered from the fits' rows into
+    # one dense batch per fit, on the FP32 SIMT shapes, and scattered back.  Every start must still
+    # end at an oracle-stationary point with S = 1, the other fits' rows untouched by the batch.
+    monkeypatch.setenv("PWA_FIT_PAUSE_BACKTRACKS", "1")
+    monkeypatch.setenv("PWA_BATCHED_SHAPE", "4")
+    pa = make_problem(4, 5_000, 20_000, SEED + 50, accept_reject=True, plain=True)
+    pb = make_problem(16, 40_000, 80_000, SEED + 51, accept_reject=False)
+    pc = make_problem(32, 60_000, 120_000, SEED + 52, accept_reject=False)
+    jobs = [(pa, inputs.starts(5, 4, 11)), (pb, inputs.starts(23, 16, 12)), (pc, inputs.starts(70, 32, 13))]
+    res, Vs = run_fits(h, jobs, max_iter=3000)
+    q = 0
+    for (p, V0), V in zip(jobs, Vs):
+        for i in range(V0.shape[0]):
+            r = res[q]
+            q += 1
+            assert r["status"] == 0, (q, r)
+            f, gmax, S = stationary(p, V[i])
+            assert gmax < 1e-5 and abs(S - 1) < 1e-4, (q, gmax, S)
+            assert abs(f - r["nll"]) <= 1e-5 * max(abs(f), p.n)
+
+
 def test_graph_and_eager_are_identical(h):
     p = make_problem(8, 8_000, 16_000, SEED + 30, accept_reject=False)
     V0 = inputs.starts(5, 8, 9)
