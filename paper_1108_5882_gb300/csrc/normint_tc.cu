@@ -13,23 +13,25 @@
 // The A operand is the tile itself and the B operand its first 2 KMAX rows (one shared-memory
 // tile, read twice by the tensor cores).
 //
-// Pipeline (one block per SM, 8 compute warps + 1 MMA warp): two shared-memory stages of 128
+// Pipeline (one block per SM, 16 compute warps + 1 MMA warp): two shared-memory stages of 128
 // events and two tensor-memory accumulators.  For tile s the compute warps fill stage s % 2 (the
 // amplitudes, computed from the kinematics or loaded, split into TF32 hi / lo), the MMA warp
 // issues the 16 MMAs of the tile into accumulator s % 2 (a fresh sum each tile), and the compute
-// warps add the accumulator of tile s - 1 into FP32 registers (round to nearest; warps w and
-// w + 4 share lane quarter w % 4 and take half of the columns each), which enter double-single
-// sums in shared memory every 4 tiles.  The tensor memory's FP32 accumulation does not round to
+// warps add the accumulator of tile s - 1 into FP32 registers (round to nearest; warps w, w + 4,
+// w + 8 and w + 12 share lane quarter w % 4 and take a quarter of the columns each, at least 8),
+// which enter double-single sums in shared memory every 4 tiles.  The fill, not the MMAs, bounds
+// a tile (an MMA of N = 2K <= 64 costs ~60 cycles; computing and splitting 128 x K amplitudes
+// costs several thousand), hence the 16 warps.  The tensor memory's FP32 accumulation does not round to
 // nearest and the diagonal of G is a sum of squares (coherent), so the sums leave tensor memory
 // every tile: their error stays ~1e-6 of the entry.  Every wait is bounded; a timeout sets status bit 1,
 // skips the remaining waits and MMAs, and the tensor memory is freed only after the MMAs issued
 // have completed (bounded).
 //
 // Work split of a fill: thread (warp w, lane l) takes the 4 consecutive events 4 q .. 4 q + 3,
-// q = 4 w + l / 8, and the waves s = 8 m + (l % 8); the 8 threads of a quarter-warp store the 8
-// rows of one 16-byte column of core matrices, so every shared-memory store is conflict-free.
+// q = 2 w + l / 16, and the waves s = 16 m + (l % 16); the 8 threads of a quarter-warp store the
+// 8 rows of one 16-byte column of core matrices, so every shared-memory store is conflict-free.
 // From kinematics, each thread first computes the angular factor P_J(cos theta) exp(i lambda phi)
-// of every (J, lambda) group for one event of its quarter-warp into a per-tile table.
+// of every fourth (J, lambda) group for one event of its half-warp into a per-tile table.
 #include "amp_model.cuh"
 #include "tc.cuh"
 
@@ -38,7 +40,8 @@ namespace pwa {
 namespace {
 
 constexpr int NT_E = 128;                  // events per tile (16 k-steps of 8)
-constexpr int NT_THREADS = 288;            // 8 compute warps + 1 MMA warp
+constexpr int NT_CW = 16;                  // compute warps
+constexpr int NT_THREADS = 32 * NT_CW + 32;  // + 1 MMA warp
 constexpr int NT_NG = 16;                  // (J, lambda) groups, at most (from kinematics)
 constexpr uint32_t NT_SBO = 32u * NT_E;    // bytes between groups of 8 rows of a K-major tile
 constexpr uint32_t NT_STAGE = 16u * NT_SBO;  // 128 rows
@@ -56,7 +59,8 @@ struct NtCfg {
     static constexpr uint32_t OFF_Y = OFF_ACC + 2u * N * 128u * 4u;         // float2 [NT_NG][NT_E]
     static constexpr uint32_t OFF_BAR = OFF_Y + (uint32_t)NT_NG * NT_E * 8u;
     static constexpr uint32_t SMEM = OFF_BAR + 128;
-    static constexpr int MW = KMAX / 8;                        // waves per thread
+    static constexpr int MW = (KMAX + 15) / 16;                // waves per thread
+    static constexpr int NH = N / 4 > 8 ? N / 4 : 8;           // drained columns per thread
     static_assert(KMAX % 8 == 0 && KMAX <= 32, "tensor-core normalisation integral: K <= 32");
     static_assert(N % 16 == 0 && N <= 256, "MMA shape");
 };
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
     constexpr int N = C::N;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool mma_warp = warp == 8;
+    const bool mma_warp = warp == NT_CW;
     const uint32_t sbase = smem_u32(sm);
     float* acc_hi = reinterpret_cast<float*>(sm + C::OFF_ACC);
     float* acc_lo = acc_hi + N * 128;
@@ -131,9 +135,9 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
     if (warp == 0) tmem_alloc(taddr_s, C::TCOLS);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            mbar_init(bar_fill + b, 8);
+            mbar_init(bar_fill + b, NT_CW);
             mbar_init(bar_mma + b, 1);
-            mbar_init(bar_drain + b, 8);
+            mbar_init(bar_drain + b, NT_CW);
         }
         mbar_init(bar_fin, 1);
         *abort_s = 0;
@@ -174,19 +178,22 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
         if (!mbar_wait_bounded(bar_fin, 0, NT_WAIT_NS)) *abort_s = 1;
     } else {
         // ================================================================ compute warps
-        const int q = 4 * warp + (lane >> 3);  // event quad of the tile
-        const int j = lane & 7;                // wave residue
+        const int q = 2 * warp + (lane >> 4);  // event quad of the tile
+        const int j = lane & 15;               // wave residue
         const uint32_t lane_t = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        // Drain of the accumulator of tile s: warps w and w + 4 share lane quarter w % 4 and take
-        // one half of the columns each; the tile's values are added in FP32 (round to nearest)
-        // into registers, and every NT_FF tiles into the double-single sums in shared memory.
-        constexpr int NH = N / 2;
+        // Drain of the accumulator of tile s: warps w, w + 4, w + 8, w + 12 share lane quarter
+        // w % 4 and take NH columns each (the warps past N columns take none); the tile's values
+        // are added in FP32 (round to nearest) into registers, and every NT_FF tiles into the
+        // double-single sums in shared memory.
+        constexpr int NH = C::NH;
         float racc[NH];
 #pragma unroll
         for (int v = 0; v < NH; ++v) racc[v] = 0.f;
         const int c_half = (warp >> 2) * NH;
+        const bool drains = c_half < N;
         const int row = 32 * (warp & 3) + lane;
         auto flush = [&]() {
+            if (!drains) return;
 #pragma unroll
             for (int v = 0; v < NH; ++v) {
                 const int idx = (c_half + v) * 128 + row;
@@ -205,13 +212,26 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                 return;
             }
             tc_fence_after();
+            if (drains) {
+                if constexpr (NH % 16 == 0) {
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 16) {
-                float d[16];
-                tmem_ld16(lane_t + (uint32_t)(b * N + c_half + c0), d);
-                tmem_wait_ld();
+                    for (int c0 = 0; c0 < NH; c0 += 16) {
+                        float d[16];
+                        tmem_ld16(lane_t + (uint32_t)(b * N + c_half + c0), d);
+                        tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) racc[c0 + k] += d[k];
+                        for (int k = 0; k < 16; ++k) racc[c0 + k] += d[k];
+                    }
+                } else {
+#pragma unroll
+                    for (int c0 = 0; c0 < NH; c0 += 8) {
+                        float d[8];
+                        tmem_ld8(lane_t + (uint32_t)(b * N + c_half + c0), d);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) racc[c0 + k] += d[k];
+                    }
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
             } else {
 #pragma unroll
                 for (int mm = 0; mm < C::MW; ++mm) {
-                    const int a = 8 * mm + j;
+                    const int a = 16 * mm + j;
                     if (s < ntile && a < K && e0 + 3 < e_end) {
                         const float4* src = reinterpret_cast<const float4*>(A + (int64_t)a * ld + e0);
                         const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
@@ -263,14 +283,14 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
             const uint32_t st = sbase + (b ? C::OFF_ST1 : C::OFF_ST0);
             const int64_t e0 = e_begin + (int64_t)s * NT_E + 4 * q;
             if (FROM_KIN) {
-                // angular factors of the groups for event e0 + (j % 4) (groups j / 4, j / 4 + 2, ...)
+                // angular factors of the groups for event e0 + (j % 4) (groups j / 4, j / 4 + 4, ...)
                 {
                     float s1, c1;
                     sincosf(pph, &s1, &c1);
                     const float ct = pct;
                     float pcur = 1.f, pprev = 0.f;
                     int jc = 0;
-                    for (int g = (j >> 2); g < wt.ng; g += 2) {
+                    for (int g = (j >> 2); g < wt.ng; g += 4) {
                         const int J = s_gJ[g], lam = s_glam[g];
                         for (; jc < J; ++jc) {
                             const float pn = ((2.f * jc + 1.f) * ct * pcur - (float)jc * pprev) * c_nt_inv_int[jc];
@@ -295,7 +315,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                 __syncwarp();
 #pragma unroll
                 for (int mm = 0; mm < C::MW; ++mm) {
-                    const int a = 8 * mm + j;
+                    const int a = 16 * mm + j;
+                    if (a >= KMAX) continue;  // KMAX = 8: half of the residues have no wave
                     const float4 p = s_prm[a];
                     const int g = s_grp[a];
                     float re[4], im[4];
@@ -317,7 +338,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
             } else {
 #pragma unroll
                 for (int mm = 0; mm < C::MW; ++mm) {
-                    const int a = 8 * mm + j;
+                    const int a = 16 * mm + j;
+                    if (a >= KMAX) continue;
                     float re[4], im[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {

@@ -189,7 +189,8 @@ def test_normint_parity(h, K, n_mc, weighted):
 
 
 @pytest.mark.parametrize("K,n_mc,from_kin", [(16, 30_001, False), (32, 20_003, False), (16, 30_001, True),
-                                              (32, 20_003, True), (7, 5_000, True)])
+                                              (32, 20_003, True), (7, 5_000, True), (8, 4_001, False),
+                                              (24, 9_001, True)])
 def test_normint_simt_path_forced(h, K, n_mc, from_kin, monkeypatch):
     # unit weights and 16 < K <= 32 take the tensor-core kernel by default; PWA_NORMINT_TC=1 / 0
     # force the tensor-core / FP32 SIMT kernel for any K <= 32: both within the same bound
