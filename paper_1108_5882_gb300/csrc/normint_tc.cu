@@ -43,6 +43,7 @@ constexpr int NT_E = 128;                  // events per tile (16 k-steps of 8)
 constexpr int NT_CW = 16;                  // compute warps
 constexpr int NT_THREADS = 32 * NT_CW + 32;  // + 1 MMA warp
 constexpr int NT_NG = 16;                  // (J, lambda) groups, at most (from kinematics)
+constexpr int NT_YS = NT_NG + 1;           // row stride of the angular table (float2)
 constexpr uint32_t NT_SBO = 32u * NT_E;    // bytes between groups of 8 rows of a K-major tile
 constexpr uint32_t NT_STAGE = 16u * NT_SBO;  // 128 rows
 constexpr uint64_t NT_WAIT_NS = 1000000000ull;
@@ -56,8 +57,10 @@ struct NtCfg {
     static constexpr uint32_t TCOLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators (power of 2 >= 32)
     static constexpr uint32_t OFF_ST0 = 0, OFF_ST1 = NT_STAGE;
     static constexpr uint32_t OFF_ACC = 2 * NT_STAGE;                       // ff sums [N][128 lanes] hi, then lo
-    static constexpr uint32_t OFF_Y = OFF_ACC + 2u * N * 128u * 4u;         // float2 [NT_NG][NT_E]
-    static constexpr uint32_t OFF_BAR = OFF_Y + (uint32_t)NT_NG * NT_E * 8u;
+    // angular table float2 [NT_E][NT_YS]: event-major with an odd row stride, so that the 16 lanes
+    // of a half-warp (one event, the groups of 16 waves) read distinct banks or broadcast
+    static constexpr uint32_t OFF_Y = OFF_ACC + 2u * N * 128u * 4u;
+    static constexpr uint32_t OFF_BAR = OFF_Y + (uint32_t)NT_YS * NT_E * 8u;
     static constexpr uint32_t SMEM = OFF_BAR + 128;
     static constexpr int MW = (KMAX + 15) / 16;                // waves per thread
     static constexpr int NH = N / 4 > 8 ? N / 4 : 8;           // drained columns per thread
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                             er = tr;
                         }
                         if (lam < 0) ei = -ei;
-                        sY[g * NT_E + 4 * q + (j & 3)] = make_float2(pcur * er, pcur * ei);
+                        sY[(4 * q + (j & 3)) * NT_YS + g] = make_float2(pcur * er, pcur * ei);
                     }
                 }
                 float m4[4];
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                         const float inv = __fdividef(1.f, fmaf(dr, dr, p.w));
                         const float t1 = p.z * inv;
                         const float br = dr * t1, bi = p.z * t1;
-                        const float2 y = sY[g * NT_E + 4 * q + k];
+                        const float2 y = sY[(4 * q + k) * NT_YS + g];
                         const bool in = a < K && e0 + k < e_end;
                         re[k] = in ? br * y.x - bi * y.y : 0.f;
                         im[k] = in ? br * y.y + bi * y.x : 0.f;
