@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(384, 1) k_nll_tc(const float2* __restrict__ A,
             if (grad) {
                 wait_or_abort(bar_y, (uint32_t)(t & 1));  // Y(t), X(t), D2 drained
                 if (*abort_s == 0 && lane == 0) {
-                    // G = Y X^T over the contraction c = (Re | Im) x 64 events: hi.hi and hi.lo in
+                    // G = Y X^T over the contraction c = (Re | Im) x E events: hi.hi and hi.lo in
                     // one MMA per k-step (X hi and lo as one operand of 2 N2 rows), then lo.hi
                     // into the second column block; the first k-step overwrites D2
                     const uint32_t yh = tmem + region(t, 0), yl = tmem + region(t, 1);
