@@ -19,7 +19,7 @@
 // issues the 16 MMAs of the tile into accumulator s % 2 (a fresh sum each tile), and the compute
 // warps add the accumulator of tile s - 1 into FP32 registers (round to nearest; warps w, w + 4,
 // w + 8 and w + 12 share lane quarter w % 4 and take a quarter of the columns each, at least 8),
-// which enter double-single sums in shared memory every 4 tiles.  The fill, not the MMAs, bounds
+// which enter double-single sums in shared memory every 8 tiles.  The fill, not the MMAs, bounds
 // a tile (an MMA of N = 2K <= 64 costs ~60 cycles; computing and splitting 128 x K amplitudes
 // costs several thousand), hence the 16 warps.  The tensor memory's FP32 accumulation does not round to
 // nearest and the diagonal of G is a sum of squares (coherent), so the sums leave tensor memory
@@ -47,7 +47,7 @@ constexpr int NT_YS = NT_NG + 1;           // row stride of the angular table (f
 constexpr uint32_t NT_SBO = 32u * NT_E;    // bytes between groups of 8 rows of a K-major tile
 constexpr uint32_t NT_STAGE = 16u * NT_SBO;  // 128 rows
 constexpr uint64_t NT_WAIT_NS = 1000000000ull;
-constexpr int NT_FF = 4;                   // tiles per double-single update of the sums
+constexpr int NT_FF = 8;                   // tiles per double-single update of the sums
 
 __constant__ float c_nt_inv_int[9] = {1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9};
 
@@ -288,8 +288,12 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
             if (FROM_KIN) {
                 // angular factors of the groups for event e0 + (j % 4) (groups j / 4, j / 4 + 4, ...)
                 {
-                    float s1, c1;
-                    sincosf(pph, &s1, &c1);
+                    // sin and cos of the event's phi once per event (the four lanes j = e, e + 4,
+                    // e + 8, e + 12 of a half-warp share event e), passed by shuffle
+                    float s1 = 0.f, c1 = 1.f;
+                    if ((j >> 2) == 0) sincosf(pph, &s1, &c1);
+                    s1 = __shfl_sync(0xffffffffu, s1, lane & ~12);
+                    c1 = __shfl_sync(0xffffffffu, c1, lane & ~12);
                     const float ct = pct;
                     float pcur = 1.f, pprev = 0.f;
                     int jc = 0;
@@ -323,6 +327,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                     const float4 p = s_prm[a];
                     const int g = s_grp[a];
                     float re[4], im[4];
+                    // whole quads of events of a wave that exists need no per-event selects
+                    const bool full = a < K && e0 + 3 < e_end;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float dr = ((p.x - m4[k]) + p.y) * ((p.x + m4[k]) + p.y);
@@ -330,9 +336,16 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_normint_tc(const float2* __re
                         const float t1 = p.z * inv;
                         const float br = dr * t1, bi = p.z * t1;
                         const float2 y = sY[(4 * q + k) * NT_YS + g];
-                        const bool in = a < K && e0 + k < e_end;
-                        re[k] = in ? br * y.x - bi * y.y : 0.f;
-                        im[k] = in ? br * y.y + bi * y.x : 0.f;
+                        re[k] = br * y.x - bi * y.y;
+                        im[k] = br * y.y + bi * y.x;
+                    }
+                    if (!full) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const bool in = a < K && e0 + k < e_end;
+                            re[k] = in ? re[k] : 0.f;
+                            im[k] = in ? im[k] : 0.f;
+                        }
                     }
                     store_row4<KMAX>(st, a, q, re);
                     store_row4<KMAX>(st, KMAX + a, q, im);
