@@ -243,13 +243,14 @@ def test_nll_grad_single_set(h, K):
 
 
 @pytest.mark.parametrize("variant", ["PWA_STREAM_HOLD=0", "PWA_STREAM_FUSED=0", "PWA_STREAM_TMA=1",
-                                     "PWA_STREAM_HOLD=0,PWA_STREAM_FUSED=0"])
+                                     "PWA_STREAM_TMA=0", "PWA_STREAM_HOLD=0,PWA_STREAM_FUSED=0"])
 @pytest.mark.parametrize("K", [4, 16, 32, 64])
 def test_nll_grad_single_set_variants(h, K, variant, monkeypatch):
-    # the non-default single-set kernels, forced: the amplitudes reloaded for the gradient pass
-    # instead of held in registers (HOLD=0), the grid reduction finalised by a second launch
-    # instead of the last block (FUSED=0), and the bulk-copy staged kernel (TMA=1); ragged tail,
-    # NaN padding never read, several blocks
+    # the single-set kernels besides the default, forced: the amplitudes reloaded for the
+    # gradient pass instead of held in registers (HOLD=0), the grid reduction finalised by a
+    # second launch instead of the last block (FUSED=0), the bulk-copy staged kernel (TMA=1, the
+    # default for 16 < K <= 32) and the register kernel (TMA=0); ragged tail, NaN padding never
+    # read, several blocks
     for kv in variant.split(","):
         k, v = kv.split("=")
         monkeypatch.setenv(k, v)
@@ -398,7 +399,7 @@ def _incoherent_problem(K, H, n, n_mc, seed):
 
 
 @pytest.mark.parametrize("K,H,n,P", [(4, 2, 3001, 1), (13, 3, 9_999, 3), (16, 2, 20_000, 2), (32, 4, 5001, 1),
-                                     (7, 1, 1, 1), (64, 2, 2001, 1)])
+                                     (7, 1, 1, 1), (64, 2, 2001, 1), (16, 4, 70_001, 1)])
 def test_nll_grad_incoherent(h, K, H, n, P):
     A, Psi = _incoherent_problem(K, H, n, max(2 * n, 1000), SEED + 1100 + K)
     V = inputs.starts(P, K, SEED + 1200 + K)
