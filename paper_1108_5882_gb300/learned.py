@@ -370,7 +370,7 @@ def evaluate_toy(h, waves, Psi, prop, V_true, n_events, seed, stream, P_rand=256
     reached = ok_a & (fs_a < f_best + dlnl)
     out.update(f_best=f_best, reached_learned=reached[:nl], reached_random=reached[nl:nl + P_rand],
                t_plain=t_plain, n_plain=n_plain, plain_hit=plain_hit,
-               t_learned_seq=t_lseq, n_learned_seq=n_lseq, learned_seq_hit=lseq_hit,
+               t_learned_seq=t_lseq, t_rank=t_rank, n_learned_seq=n_lseq, learned_seq_hit=lseq_hit,
                iters_first_random=iters_rand[0] if iters_rand else 0,
                iters_first_learned=iters_learned[0] if iters_learned else 0,
                plain_stop=plain_stop, learned_seq_stop=lseq_stop,
@@ -383,7 +383,9 @@ def evaluate_toy(h, waves, Psi, prop, V_true, n_events, seed, stream, P_rand=256
 
 def summarize(outs):
     """Per method: fraction of toys that reached the global minimum, per-start success rates,
-    and the measured wall time to the global minimum per fit (mean over toys)."""
+    and the measured wall time to the global minimum per fit (mean over toys, and the median and
+    maximum of the one-at-a-time methods, whose means a few slow toys can carry; the learned
+    ranking step, the network's forward pass and the 32-set evaluation, is also given alone)."""
     m = lambda k: float(np.mean([o[k] for o in outs]))
     t_plain = m("t_plain")
     res = dict(toys=len(outs),
@@ -399,6 +401,12 @@ def summarize(outs):
                time_to_global_learned_sequential_s=m("t_learned_seq"),
                time_to_global_batched_random_s=m("t_random"),
                time_to_global_batched_learned_s=m("t_learned"),
+               time_to_global_plain_median_s=float(np.median([o["t_plain"] for o in outs])),
+               time_to_global_learned_sequential_median_s=float(np.median([o["t_learned_seq"] for o in outs])),
+               learned_ranking_time_mean_s=m("t_rank"),
+               learned_ranking_time_max_s=float(np.max([o["t_rank"] for o in outs])),
+               learned_sequential_time_max_s=float(np.max([o["t_learned_seq"] for o in outs])),
+               plain_time_max_s=float(np.max([o["t_plain"] for o in outs])),
                batched_random_time_median_s=float(np.median([o["t_random"] for o in outs])),
                batched_random_time_max_s=float(np.max([o["t_random"] for o in outs])),
                batched_random_iterations_max=int(np.max([o["iters_max_random"] for o in outs])),

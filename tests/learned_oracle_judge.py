@@ -136,7 +136,10 @@ def main():
     t_eval = time.perf_counter() - t0
     gpu = learned.summarize(outs)
     orc = summarize_judged(outs, judged)
-    res = dict(gpu_decided=gpu, oracle_decided=orc, train_toys=args.train_toys, train_events=args.train_events,
+    per_toy = {k: [float(o[k]) for o in outs] for k in ("t_plain", "t_learned_seq", "t_rank", "t_random", "t_learned",
+                                                         "n_plain", "n_learned_seq", "iters_first_learned")}
+    res = dict(gpu_decided=gpu, oracle_decided=orc, per_toy=per_toy, train_toys=args.train_toys,
+               train_events=args.train_events,
                eval_toys=args.eval_toys, eval_events=args.eval_events, epochs=args.epochs, loss_first=hist[0],
                loss_last=hist[-1], t_generate_s=t_gen, t_train_s=t_train, t_eval_and_judge_s=t_eval)
     print(json.dumps(res))
